@@ -1,0 +1,55 @@
+"""Replay of the paper's 1D top-hat experiment (Sec. 3.1) with the oracle,
+against the error measures the paper prints (tests/golden/paper_1d_tophat.json).
+Pins the whole oracle loop (delta, FLIP, exact mass RHS, mass solve, G2P)
+against numbers that do not come from this code."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_1d_tophat.json")))
+
+
+def _run(method, jitter):
+    n = N = 200
+    L, h = 1.0, 1.0 / 200
+    dt, steps = 0.1 * h, 2000
+    g = np.random.default_rng(0)
+    x0 = np.mod(np.arange(N) * h + (g.uniform(-jitter, jitter, N) * h if jitter else 0.0), L)
+    a0 = ((x0 > 0.25) & (x0 < 0.75)).astype(float)
+    x, a = x0.copy(), a0.copy()
+    v0 = oracle.particle_volumes(1, L, x0.astype(np.float32))
+    for _ in range(steps):
+        px = x.astype(np.float32)
+        if method == "delta":
+            m = oracle.delta(1, n, L, px, None, a)
+        elif method == "flip":
+            m = oracle.flip(1, n, L, px, None, a)[0]
+        else:
+            m = oracle.assign_mass(1, n, L, px, None, a)
+        x = np.mod(x + dt, L)
+        a = oracle.interpolate(1, n, L, m, x.astype(np.float32))[0]
+    v = oracle.particle_volumes(1, L, x.astype(np.float32))
+    return {"E1": 100 * ((v * a).sum() / (v0 * a0).sum() - 1),
+            "E2": 100 * ((v * a * a).sum() / (v0 * a0 * a0).sum() - 1),
+            "L2": 100 * np.sqrt(((v * a - v0 * a0) ** 2).sum() / ((v0 * a0) ** 2).sum())}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("case,jitter", [("regular", 0.0), ("distorted", 0.4)])
+def test_paper_1d_table(case, jitter):
+    tol = GOLD["tolerance_percentage_points"]
+    for key, meth in [("delta", "delta"), ("flip", "flip"), ("mass_delta", "mass")]:
+        want = GOLD[case].get(key)
+        if not want:
+            continue
+        got = _run(meth, jitter)
+        for k, w in want.items():
+            assert abs(got[k] - w) <= tol, (case, key, k, got[k], w)
+    if case == "regular":
+        # Sec. 3.1: for the regular arrangement FLIP is equivalent to delta
+        d, f = _run("delta", 0.0), _run("flip", 0.0)
+        assert abs(d["E2"] - f["E2"]) < 1e-4 and abs(d["L2"] - f["L2"]) < 1e-4  # float32 positions

@@ -1,0 +1,497 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed
+forms, invariants the paper states, textbook special cases, an independent
+library routine (scipy's Qhull Delaunay), exact big-integer predicates, or
+brute force on tiny inputs.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1610_05258_gb300 import workloads as W
+
+TWO32 = 2 ** 32
+
+
+# --------------------------------------------------------------------------
+# fixed-point positions
+# --------------------------------------------------------------------------
+def test_fixed_coords_definition():
+    """X = floor(frac(x/L) 2^32), checked with exact rationals."""
+    g = np.random.default_rng(1)
+    L = 2 * math.pi
+    x = np.concatenate([g.uniform(-20, 20, 500), [0.0, -0.0, L, -L, 1e-30, -1e-30, 3 * L]]).astype(np.float32)
+    X = oracle.fixed_coords(x, L)
+    for xi, Xi in zip(x.astype(np.float64), X):
+        t = Fraction(float(xi)) / Fraction(L)
+        fr = t - math.floor(t)
+        want = math.floor(fr * TWO32) % TWO32
+        # the oracle rounds x/L once in double; allow that single rounding
+        assert abs(int(Xi) - want) <= 2 or abs(abs(int(Xi) - want) - TWO32) <= 2
+
+
+# --------------------------------------------------------------------------
+# quadrature used by the exact right-hand side
+# --------------------------------------------------------------------------
+def test_triangle_rule_exact_to_degree_three():
+    """int over the unit right triangle of x^a y^b = a! b! / (a+b+2)!."""
+    x, y = [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]
+    for a in range(4):
+        for b in range(4 - a):
+            want = math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
+            assert oracle.tri_monomial(x, y, a, b) == pytest.approx(want, rel=1e-13, abs=1e-15)
+    # not exact at degree 4: the rule is what it claims, no more
+    assert abs(oracle.tri_monomial(x, y, 4, 0) - 1.0 / 30.0) > 1e-4
+
+
+def test_triangle_rule_general_triangle_sympy():
+    sp = pytest.importorskip("sympy")
+    X, Y, u, v = sp.symbols("X Y u v")
+    P = [(sp.Rational(3, 10), sp.Rational(1, 5)), (sp.Rational(17, 10), sp.Rational(1, 2)), (sp.Rational(4, 5), sp.Rational(9, 5))]
+    jac = abs((P[1][0] - P[0][0]) * (P[2][1] - P[0][1]) - (P[2][0] - P[0][0]) * (P[1][1] - P[0][1]))
+    mx = P[0][0] + u * (P[1][0] - P[0][0]) + v * (P[2][0] - P[0][0])
+    my = P[0][1] + u * (P[1][1] - P[0][1]) + v * (P[2][1] - P[0][1])
+    for a, b in [(0, 0), (1, 2), (2, 1), (3, 0), (0, 3), (1, 1)]:
+        want = sp.integrate(sp.integrate(mx ** a * my ** b * jac, (v, 0, 1 - u)), (u, 0, 1))
+        got = oracle.tri_monomial([float(p[0]) for p in P], [float(p[1]) for p in P], a, b)
+        assert got == pytest.approx(float(want), rel=1e-12)
+
+
+# --------------------------------------------------------------------------
+# mesh mass matrix m_ij = int psi_i psi_j  (Sec. 2.4)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,n", [(1, 16), (1, 5), (2, 8), (2, 12)])
+def test_mass_apply_fourier_eigenvalues(dim, n):
+    """Pure periodic modes are eigenvectors: lambda = h (2+cos th)/3 in 1D and
+    h^2 (2+cos th)(2+cos ph)/9 in 2D (closed form of the linear/bilinear FE
+    mass matrix on a uniform periodic mesh)."""
+    L = 1.7
+    h = L / n
+    i = np.arange(n)
+    for k in range(n):
+        th = 2 * math.pi * k / n
+        if dim == 1:
+            x = np.cos(th * i + 0.3)
+            lam = h * (2 + math.cos(th)) / 3
+        else:
+            l = (k * 3 + 1) % n
+            ph = 2 * math.pi * l / n
+            x = np.cos(th * i[None, :] + ph * i[:, None] + 0.3).ravel()
+            lam = h * h * (2 + math.cos(th)) * (2 + math.cos(ph)) / 9
+        y = oracle.mass_apply(dim, n, L, x)[0]
+        np.testing.assert_allclose(y, lam * x, rtol=0, atol=1e-14 * max(1, np.abs(x).max()))
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_mass_row_sums_are_mesh_volumes(dim):
+    """sum_j m_ij = v_i = h^d (Sec. 2.4, remark on lumping)."""
+    n, L = 9, 3.0
+    y = oracle.mass_apply(dim, n, L, np.ones(n ** dim))[0]
+    np.testing.assert_allclose(y, (L / n) ** dim, rtol=1e-14)
+
+
+@pytest.mark.parametrize("dim,n", [(1, 7), (1, 64), (2, 6), (2, 40)])
+def test_direct_solve_matches_cg_and_inverts(dim, n):
+    L = 2.0
+    b = W.mesh_field(dim, n, L, F=2, seed=3, kind="noise")
+    x = oracle.mass_solve(dim, n, L, b)
+    np.testing.assert_allclose(oracle.mass_apply(dim, n, L, x), b, rtol=0, atol=1e-12 * np.abs(b).max())
+    xc, it, res = oracle.mass_solve_cg(dim, n, L, b, rtol=1e-13)
+    np.testing.assert_allclose(x, xc, rtol=0, atol=1e-9 * np.abs(x).max())
+    # CG convergence bound with kappa = 3 (1D) / 9 (2D): rate (sqrt k -1)/(sqrt k +1)
+    kappa = 3.0 if dim == 1 else 9.0
+    rate = (math.sqrt(kappa) - 1) / (math.sqrt(kappa) + 1)
+    assert it.max() <= math.ceil(math.log(2 * math.sqrt(kappa) / 1e-13) / math.log(1 / rate)) + 2
+
+
+def test_preservation_on_mesh():
+    """int phi_i psi_j = delta_ij (Eq. ortho): solving M x = M e_j gives e_j."""
+    n, L = 10, 1.0
+    for j in [0, 3, 57]:
+        e = np.zeros(n * n)
+        e[j] = 1.0
+        x = oracle.mass_solve(2, n, L, oracle.mass_apply(2, n, L, e))
+        np.testing.assert_allclose(x[0], e, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# G2P (Eq. delta2)
+# --------------------------------------------------------------------------
+def _hat(d, h):
+    return np.maximum(0.0, 1.0 - np.abs(d) / h)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_interpolate_brute_force(dim):
+    """sum over ALL nodes of Ab_i psi_i(r_mu), hats by their definition with
+    periodic distance, on a tiny mesh."""
+    n, L = 6, 1.3
+    h = L / n
+    g = np.random.default_rng(4)
+    npart = 40
+    px = g.uniform(-L, 2 * L, npart).astype(np.float32)
+    py = g.uniform(-L, 2 * L, npart).astype(np.float32)
+    mesh = g.standard_normal((2, n ** dim))
+    got = oracle.interpolate(dim, n, L, mesh, px, py)
+    X = oracle.fixed_coords(px, L).astype(np.float64) * (L / TWO32)
+    Y = oracle.fixed_coords(py, L).astype(np.float64) * (L / TWO32)
+    want = np.zeros((2, npart))
+    for i in range(n ** dim):
+        ix, iy = i % n, i // n
+        dx = np.mod(X - ix * h + L / 2, L) - L / 2
+        w = _hat(dx, h)
+        if dim == 2:
+            dy = np.mod(Y - iy * h + L / 2, L) - L / 2
+            w = w * _hat(dy, h)
+        want += mesh[:, i : i + 1] * w[None, :]
+    np.testing.assert_allclose(got, want, atol=1e-12)
+
+
+def test_interpolate_partition_of_unity_and_bilinear():
+    n, L = 16, 1.0
+    g = np.random.default_rng(5)
+    px = g.uniform(0.2, 0.7, 300).astype(np.float32)
+    py = g.uniform(0.2, 0.7, 300).astype(np.float32)
+    one = oracle.interpolate(2, n, L, np.ones(n * n), px, py)
+    np.testing.assert_allclose(one, 1.0, atol=1e-14)
+    i = np.arange(n) * (L / n)
+    xx, yy = np.meshgrid(i, i, indexing="xy")
+    f = lambda x, y: 0.3 + 1.1 * x - 0.7 * y + 2.3 * x * y
+    mesh = f(xx, yy).ravel()
+    X = oracle.fixed_coords(px, L) * (L / TWO32)
+    Y = oracle.fixed_coords(py, L) * (L / TWO32)
+    # the bilinear interpolant reproduces a field that is bilinear in each cell
+    # only cell-wise; a globally bilinear f is cell-wise bilinear
+    np.testing.assert_allclose(oracle.interpolate(2, n, L, mesh, px, py)[0], f(X, Y), atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# 1D particle functions, delta, FLIP, mass
+# --------------------------------------------------------------------------
+def test_1d_volumes():
+    inst = W.tophat_1d(64, 50, seed=2)
+    v = oracle.particle_volumes(1, inst.L, inst.px)
+    assert v.sum() == pytest.approx(inst.L, rel=1e-14)
+    reg = W.tophat_1d(64, 32, regular=True)
+    np.testing.assert_allclose(oracle.particle_volumes(1, reg.L, reg.px), reg.L / 32, rtol=1e-8)
+
+
+def test_1d_delta_particles_at_nodes():
+    """Particles sitting on nodes: A(x_i) = A_mu (Eq. delta)."""
+    n, L = 32, 1.0
+    x = (np.arange(n) * (L / n)).astype(np.float32)
+    # add particles between nodes so that the set is a superset
+    g = np.random.default_rng(7)
+    extra = g.uniform(0, L, 17).astype(np.float32)
+    px = np.concatenate([x, extra])
+    a = g.standard_normal(px.shape[0])
+    d = oracle.delta(1, n, L, px, None, a)[0]
+    np.testing.assert_allclose(d, a[:n], atol=1e-12)
+
+
+def test_1d_flip_equals_delta_on_regular_lattice():
+    """Regular particle arrangement with a uniform shift: FLIP == delta
+    (Sec. 3.1: "in the former case the FLIP method is equivalent")."""
+    n, L = 32, 1.0  # positions exactly representable in float32 and in fixed point
+    for shift in [0.0, 0.25, 0.5, 0.8125]:
+        px = ((np.arange(n) + shift) * (L / n)).astype(np.float32)
+        a = np.random.default_rng(3).standard_normal(n)
+        fl, vol, e = oracle.flip(1, n, L, px, None, a)
+        de = oracle.delta(1, n, L, px, None, a)
+        np.testing.assert_allclose(fl, de, atol=1e-9)
+        assert e == 0
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_flip_conservation_and_jensen(dim):
+    """sum_i v_i Ab_i = sum_mu v_mu A_mu (Eqs. cons, FLIP_vol) and
+    sum v_i Ab_i^2 <= sum v_mu A_mu^2 (stability, Eq. stab)."""
+    inst = W.tophat_1d(64, 50, seed=9) if dim == 1 else W.uniform_instance(16, 2, F=2, seed=5)
+    a = inst.vals.astype(np.float64)
+    v = oracle.particle_volumes(dim, inst.L, inst.px, inst.py)
+    m, vol, e = oracle.flip(dim, inst.n, inst.L, inst.px, inst.py, a, v)
+    np.testing.assert_allclose((vol[None, :] * m).sum(1), (v[None, :] * a).sum(1), rtol=1e-12, atol=1e-15)
+    assert np.all((vol[None, :] * m * m).sum(1) <= (v[None, :] * a * a).sum(1) * (1 + 1e-12))
+    assert vol.sum() == pytest.approx(v.sum(), rel=1e-12)
+
+
+def test_1d_rhs_exact_properties():
+    inst = W.tophat_1d(48, 70, seed=11)
+    h = inst.L / inst.n
+    one = oracle.rhs(1, inst.n, inst.L, inst.px, None, np.ones(inst.np))[0]
+    np.testing.assert_allclose(one, h, rtol=1e-12)
+    v = oracle.particle_volumes(1, inst.L, inst.px)
+    b = oracle.rhs(1, inst.n, inst.L, inst.px, None, inst.vals)[0]
+    assert b.sum() == pytest.approx((v * inst.vals[0]).sum(), rel=1e-12)
+
+
+def test_1d_rhs_brute_force():
+    """b_j = int A psi_j by a fine midpoint rule on the explicit piecewise-
+    linear A (numpy interp over unwrapped ordered particles)."""
+    n, L = 12, 1.0
+    g = np.random.default_rng(12)
+    px = g.uniform(0, L, 9).astype(np.float32)
+    a = g.standard_normal(9)
+    X = oracle.fixed_coords(px, L).astype(np.float64) * (L / TWO32)
+    o = np.argsort(X, kind="stable")
+    xs = np.concatenate([X[o] - L, X[o], X[o] + L])
+    av = np.concatenate([a[o]] * 3)
+    m = 400000
+    q = (np.arange(m) + 0.5) * (L / m)
+    A = np.interp(q, xs, av)
+    h = L / n
+    want = np.array([(A * _hat(np.mod(q - j * h + L / 2, L) - L / 2, h)).sum() * (L / m) for j in range(n)])
+    got = oracle.rhs(1, n, L, px, None, a)[0]
+    np.testing.assert_allclose(got, want, atol=2e-6)
+
+
+def test_1d_preservation_through_particles():
+    """Particles include every node and carry the mesh interpolant's values
+    (G2P): then A(x) == Ab(x), b = M Ab and mass assignment returns Ab
+    (the "preservation of information" requirement, Eq. ortho)."""
+    n, L = 32, 1.0  # node positions exact in float32
+    g = np.random.default_rng(13)
+    px = np.concatenate([np.arange(n) * (L / n), g.uniform(0, L, 31)]).astype(np.float32)
+    mesh = g.standard_normal((1, n))
+    a = oracle.interpolate(1, n, L, mesh, px)
+    b = oracle.rhs(1, n, L, px, None, a)
+    np.testing.assert_allclose(b, oracle.mass_apply(1, n, L, mesh), atol=1e-13)
+    np.testing.assert_allclose(oracle.assign_mass(1, n, L, px, None, a), mesh, atol=1e-11)
+
+
+def test_1d_appendix_b_quadrature_exact_without_particles_inside():
+    """App. B: on an element with no particle strictly inside, A is linear there
+    and the parabola fit is exact; with particles exactly at the nodes the
+    quadrature RHS equals the exact one."""
+    n, L = 16, 1.0
+    px = (np.arange(n) * (L / n)).astype(np.float32)
+    a = np.random.default_rng(2).standard_normal(n)
+    np.testing.assert_allclose(oracle.rhs(1, n, L, px, None, a, mode=1), oracle.rhs(1, n, L, px, None, a, mode=0), atol=1e-14)
+
+
+def test_1d_mass_conservation_and_stability():
+    """Mass assignment is conservative (Eq. cons with v_i = h) and stable in
+    the integral form int Ab^2 <= int A^2 (L2 projection is a contraction)."""
+    inst = W.tophat_1d(64, 90, seed=21)
+    a = inst.vals[0].astype(np.float64)
+    v = oracle.particle_volumes(1, inst.L, inst.px)
+    m = oracle.assign_mass(1, inst.n, inst.L, inst.px, None, a)[0]
+    h = inst.L / inst.n
+    assert (h * m).sum() == pytest.approx((v * a).sum(), rel=1e-12)
+    e_mesh = m @ oracle.mass_apply(1, inst.n, inst.L, m)[0]
+    X = oracle.fixed_coords(inst.px, inst.L).astype(np.float64) * (inst.L / TWO32)
+    o = np.argsort(X, kind="stable")
+    xs, av = X[o], a[o]
+    gaps = np.diff(np.concatenate([xs, [xs[0] + inst.L]]))
+    a1 = np.roll(av, -1)
+    e_part = (gaps * (av * av + av * a1 + a1 * a1) / 3.0).sum()
+    assert e_mesh <= e_part * (1 + 1e-12)
+
+
+# --------------------------------------------------------------------------
+# 2D periodic Delaunay triangulation of the particles
+# --------------------------------------------------------------------------
+def _canon(tri, off):
+    out = set()
+    for (p, a, b), (ax, ay, bx, by) in zip(tri.tolist(), off.tolist()):
+        out.add((p, a, ax, ay, b, bx, by))
+    return out
+
+
+def _scipy_canonical(px, py, L):
+    spatial = pytest.importorskip("scipy.spatial")
+    X = oracle.fixed_coords(px, L).astype(np.float64)
+    Y = oracle.fixed_coords(py, L).astype(np.float64)
+    N = X.shape[0]
+    pts, ids = [], []
+    for oy in (-1, 0, 1):
+        for ox in (-1, 0, 1):
+            pts.append(np.stack([X + ox * TWO32, Y + oy * TWO32], 1))
+            ids.append(np.stack([np.arange(N), np.full(N, ox), np.full(N, oy)], 1))
+    pts = np.concatenate(pts) / TWO32
+    ids = np.concatenate(ids)
+    d = spatial.Delaunay(pts)
+    out = set()
+    for s in d.simplices:
+        v = [tuple(ids[k]) for k in s]
+        # counter-clockwise
+        P = pts[s]
+        if (P[1, 0] - P[0, 0]) * (P[2, 1] - P[0, 1]) - (P[2, 0] - P[0, 0]) * (P[1, 1] - P[0, 1]) < 0:
+            v = [v[0], v[2], v[1]]
+        k = min(range(3), key=lambda i: v[i][0])
+        v = v[k:] + v[:k]
+        (p, px0, py0), (a, ax, ay), (b, bx, by) = v
+        if px0 != 0 or py0 != 0:
+            continue  # anchor must be the canonical copy
+        out.add((p, a, ax - px0, ay - py0, b, bx - px0, by - py0))
+    return out
+
+
+@pytest.mark.parametrize("seed,npart", [(1, 300), (2, 1200)])
+def test_delaunay_matches_qhull(seed, npart):
+    """Generic random points: the oracle's triangles equal those of scipy's
+    Qhull Delaunay on the 3x3 periodic cover (an independent library)."""
+    g = np.random.default_rng(seed)
+    L = 1.0
+    px = g.uniform(0, L, npart).astype(np.float32)
+    py = g.uniform(0, L, npart).astype(np.float32)
+    tri, off, v = oracle.triangulate(L, px, py)
+    assert tri.shape[0] == 2 * npart  # Euler on the torus: F = 2V
+    assert v.sum() == pytest.approx(L * L, rel=1e-12)
+    assert _canon(tri, off) == _scipy_canonical(px, py, L)
+
+
+def _incircle_exact(p, a, b, s):
+    """Exact sign of the in-circle determinant (Python integers): >0 if s is
+    inside the circle through p, a, b (counter-clockwise)."""
+    rows = []
+    for q in (p, a, b):
+        dx, dy = q[0] - s[0], q[1] - s[1]
+        rows.append((dx, dy, dx * dx + dy * dy))
+    (a0, a1, a2), (b0, b1, b2), (c0, c1, c2) = rows
+    return a0 * (b1 * c2 - b2 * c1) - a1 * (b0 * c2 - b2 * c0) + a2 * (b0 * c1 - b1 * c0)
+
+
+def test_delaunay_empty_circles_exact():
+    """Every triangle's circumcircle contains no particle image strictly
+    inside, checked with exact integer arithmetic over all 9 images."""
+    g = np.random.default_rng(5)
+    L = 1.0
+    N = 150
+    px = g.uniform(0, L, N).astype(np.float32)
+    py = g.uniform(0, L, N).astype(np.float32)
+    tri, off, _ = oracle.triangulate(L, px, py)
+    X = [int(v) for v in oracle.fixed_coords(px, L)]
+    Y = [int(v) for v in oracle.fixed_coords(py, L)]
+    imgs = [(X[q] + ox * TWO32, Y[q] + oy * TWO32) for q in range(N) for ox in (-1, 0, 1) for oy in (-1, 0, 1)]
+    for (p, a, b), (ax, ay, bx, by) in zip(tri.tolist(), off.tolist()):
+        P = (X[p], Y[p])
+        A = (X[a] + ax * TWO32, Y[a] + ay * TWO32)
+        B = (X[b] + bx * TWO32, Y[b] + by * TWO32)
+        assert (A[0] - P[0]) * (B[1] - P[1]) - (A[1] - P[1]) * (B[0] - P[0]) > 0
+        for s in imgs:
+            if s in (P, A, B):
+                continue
+            assert _incircle_exact(P, A, B, s) <= 0
+
+
+def test_delaunay_degenerate_lattice():
+    """A perfect square lattice: every cell's four corners are cocircular; the
+    symbolic perturbation still yields a valid triangulation (2N triangles,
+    each half of a lattice square, areas summing to L^2)."""
+    m = 32  # exact in float32 and in fixed point: a truly degenerate lattice
+    L = 1.0
+    i = (np.arange(m) + 0.5) / m
+    xx, yy = np.meshgrid(i, i, indexing="xy")
+    px, py = xx.ravel().astype(np.float32), yy.ravel().astype(np.float32)
+    tri, off, v = oracle.triangulate(L, px, py)
+    assert tri.shape[0] == 2 * m * m
+    assert v.sum() == pytest.approx(1.0, rel=1e-9)
+    X = oracle.fixed_coords(px, L).astype(np.int64)
+    Y = oracle.fixed_coords(py, L).astype(np.int64)
+    for (p, a, b), (ax, ay, bx, by) in zip(tri.tolist(), off.tolist()):
+        ar = ((X[a] + ax * TWO32 - X[p]) * (Y[b] + by * TWO32 - Y[p]) - (Y[a] + ay * TWO32 - Y[p]) * (X[b] + bx * TWO32 - X[p]))
+        assert ar == TWO32 * TWO32 // (m * m)
+
+
+def test_stars_consistent_with_triangulation():
+    inst = W.uniform_instance(16, 3, F=1, seed=8)
+    tri, off, _ = oracle.triangulate(inst.L, inst.px, inst.py)
+    deg = np.zeros(inst.np, dtype=int)
+    for t in tri:
+        for q in t:
+            deg[q] += 1
+    st = oracle.stars(inst.L, inst.px, inst.py, np.arange(0, inst.np, 37))
+    for k, (nb, _) in zip(range(0, inst.np, 37), st):
+        assert len(nb) == deg[k]
+
+
+# --------------------------------------------------------------------------
+# 2D delta, RHS, mass
+# --------------------------------------------------------------------------
+def test_2d_delta_constant_and_affine():
+    inst = W.uniform_instance(16, 4, F=1, seed=31)
+    tri = oracle.triangulate(inst.L, inst.px, inst.py)
+    d = oracle.delta(2, inst.n, inst.L, inst.px, inst.py, np.full(inst.np, 2.5), tri=tri)
+    np.testing.assert_allclose(d, 2.5, atol=1e-13)
+    X = oracle.fixed_coords(inst.px, inst.L) * (inst.L / TWO32)
+    Y = oracle.fixed_coords(inst.py, inst.L) * (inst.L / TWO32)
+    f = lambda x, y: 0.4 - 1.3 * x + 0.8 * y
+    d = oracle.delta(2, inst.n, inst.L, inst.px, inst.py, f(X, Y), tri=tri)[0].reshape(inst.n, inst.n)
+    h = inst.L / inst.n
+    # P1 reproduces affine fields away from the periodic seam
+    for j in range(4, 12):
+        for i in range(4, 12):
+            assert d[j, i] == pytest.approx(f(i * h, j * h), abs=1e-12)
+
+
+def test_2d_rhs_exact_properties():
+    inst = W.uniform_instance(12, 3, F=2, seed=41)
+    tri = oracle.triangulate(inst.L, inst.px, inst.py)
+    h = inst.L / inst.n
+    b1 = oracle.rhs(2, inst.n, inst.L, inst.px, inst.py, np.ones(inst.np), tri=tri)
+    np.testing.assert_allclose(b1, h * h, rtol=1e-12)
+    b = oracle.rhs(2, inst.n, inst.L, inst.px, inst.py, inst.vals, tri=tri)
+    np.testing.assert_allclose(b.sum(1), (tri[2][None, :] * inst.vals).sum(1), rtol=1e-12)
+
+
+def test_2d_rhs_brute_force_fine_grid():
+    """b_j = int A psi_j against a fine-grid product rule: A evaluated on a
+    refined grid by its definition (P1 on the triangulation), psi_j by its
+    definition, second-order convergence to the oracle's exact value."""
+    inst = W.uniform_instance(6, 4, F=1, seed=51)
+    tri = oracle.triangulate(inst.L, inst.px, inst.py)
+    b = oracle.rhs(2, inst.n, inst.L, inst.px, inst.py, inst.vals, tri=tri)[0]
+    h = inst.L / inst.n
+    errs = []
+    for r in (8, 16, 32):
+        m = inst.n * r
+        A = oracle.delta(2, m, inst.L, inst.px, inst.py, inst.vals, tri=tri)[0].reshape(m, m)
+        q = np.arange(m) * (inst.L / m)
+        est = np.zeros(inst.n * inst.n)
+        for j in range(inst.n * inst.n):
+            jx, jy = j % inst.n, j // inst.n
+            wx = _hat(np.mod(q - jx * h + inst.L / 2, inst.L) - inst.L / 2, h)
+            wy = _hat(np.mod(q - jy * h + inst.L / 2, inst.L) - inst.L / 2, h)
+            est[j] = (A * wy[:, None] * wx[None, :]).sum() * (inst.L / m) ** 2
+        errs.append(np.abs(est - b).max())
+    # second-order convergence to the oracle's value: a wrong exact value would
+    # make the error stall at a constant instead of dropping ~4x per halving
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5 and errs[2] < 1e-3 * h * h
+
+
+def test_2d_mass_conservation_and_stability():
+    inst = W.uniform_instance(12, 4, F=1, seed=61)
+    tri, off, v = oracle.triangulate(inst.L, inst.px, inst.py)
+    a = inst.vals[0].astype(np.float64)
+    m = oracle.assign_mass(2, inst.n, inst.L, inst.px, inst.py, a, tri=(tri, off, v))[0]
+    h = inst.L / inst.n
+    assert (h * h * m).sum() == pytest.approx((v * a).sum(), rel=1e-11, abs=1e-14)
+    e_mesh = m @ oracle.mass_apply(2, inst.n, inst.L, m)[0]
+    X = oracle.fixed_coords(inst.px, inst.L).astype(np.float64)
+    Y = oracle.fixed_coords(inst.py, inst.L).astype(np.float64)
+    e_part = 0.0
+    for (p, q, r), (ax, ay, bx, by) in zip(tri.tolist(), off.tolist()):
+        area = 0.5 * ((X[q] + ax * TWO32 - X[p]) * (Y[r] + by * TWO32 - Y[p]) - (Y[q] + ay * TWO32 - Y[p]) * (X[r] + bx * TWO32 - X[p]))
+        area *= (inst.L / TWO32) ** 2
+        A = (a[p], a[q], a[r])
+        e_part += area / 6.0 * (A[0] ** 2 + A[1] ** 2 + A[2] ** 2 + A[0] * A[1] + A[1] * A[2] + A[0] * A[2])
+    assert e_mesh <= e_part * (1 + 1e-12)
+
+
+def test_2d_appendix_b_reading_exact_for_affine_particles():
+    """The 2D App. B analogue is exact wherever A is affine (no particle in the
+    cell breaks the parabola fit): with an affine A the two modes agree away
+    from the seam."""
+    inst = W.uniform_instance(12, 4, F=1, seed=71)
+    tri = oracle.triangulate(inst.L, inst.px, inst.py)
+    X = oracle.fixed_coords(inst.px, inst.L) * (inst.L / TWO32)
+    Y = oracle.fixed_coords(inst.py, inst.L) * (inst.L / TWO32)
+    a = 0.3 + 0.9 * X - 0.4 * Y
+    b0 = oracle.rhs(2, inst.n, inst.L, inst.px, inst.py, a, 0, tri=tri)[0].reshape(12, 12)
+    b1 = oracle.rhs(2, inst.n, inst.L, inst.px, inst.py, a, 1, tri=tri)[0].reshape(12, 12)
+    np.testing.assert_allclose(b1[3:9, 3:9], b0[3:9, 3:9], atol=1e-13)
