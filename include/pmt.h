@@ -1,0 +1,170 @@
+/*
+ * pmt.h - C ABI of a GB300 (sm_103a) library for transferring fields between
+ * particles and a periodic mesh, after D. Duque and P. Espanol, "Assignment
+ * of fields from particles to mesh" (arXiv 1610.05258).
+ *
+ * Notation follows the paper: particles mu carry values A_mu and particle
+ * functions psi_mu; mesh nodes i carry values Ab_i ("A bar") and mesh
+ * functions psi_i; particle values interpolated back from the mesh are Abb_mu.
+ *
+ * Geometry.  The mesh is periodic: dim = 1 or 2, n nodes per side, box length
+ * L, spacing h = L/n, nodes at x_i = i h (2D: node (i, j) has flat index
+ * j*n + i).  Mesh functions are linear (1D) or bilinear (2D) finite elements
+ * (Sec. 3.1 and 3.2).  Particle functions are linear finite elements too: hat
+ * functions over the particles ordered around the circle in 1D, P1 functions
+ * on the periodic Delaunay triangulation of the particles in 2D (Sec. 3.2,
+ * App. A).  Positions may lie anywhere; a float coordinate x is mapped to the
+ * torus coordinate X = floor(frac(fl32(x * fl32(1/L))) * 2^32), and every
+ * geometric decision is taken exactly on X (physical position X L / 2^32).
+ *
+ * Memory.  Unless stated otherwise every pointer argument is a DEVICE pointer
+ * owned by the caller, float32, and must stay valid until the work queued on
+ * the context's stream has finished.  Particle arrays are structure-of-arrays:
+ * px[np], py[np] (py is ignored and may be NULL when dim == 1) and particle
+ * fields vals[F][np] (field f of particle k at vals[f*np + k]).  Mesh fields
+ * are [F][n^dim].  Arguments marked "host" are host pointers; calls that write
+ * a host result wait for the stream before returning.
+ *
+ * Ordering.  Results never depend on the order in which particles are given
+ * beyond the symbolic tie-break of exactly cocircular particles, which uses
+ * the particle index (lower index = stronger perturbation).
+ *
+ * Errors.  Every call returns a pm_status; nothing is thrown across the ABI.
+ * Argument errors are detected on the host before any launch.  Errors found
+ * on the device (non-finite positions, coincident particles, a triangulation
+ * whose circumcircles span more than a quarter of the box, a solve that does
+ * not converge) set a device status word that the next call that waits for
+ * the stream returns; pm_sync() returns it explicitly.  pm_last_error() gives
+ * a one-line description of the last failure.
+ *
+ * Concurrency.  A context owns all its workspace (sized at creation, so no
+ * call allocates device memory) and its calls must not overlap: issue them on
+ * one stream, or synchronise between them.
+ */
+#ifndef PMT_H
+#define PMT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pm_status {
+    PM_OK = 0,
+    PM_EINVAL = 1,      /* bad argument (size, dimension, null pointer, F too large) */
+    PM_ENOMEM = 2,      /* workspace allocation failed at creation                    */
+    PM_ENOTCONV = 3,    /* mass solve reached max_iter above the requested tolerance  */
+    PM_ETIMEOUT = 4,    /* a bounded device-side wait gave up                         */
+    PM_EDEGENERATE = 5, /* non-finite or coincident positions, or a too sparse set    */
+    PM_ECUDA = 6        /* a CUDA runtime call failed                                  */
+} pm_status;
+
+typedef struct pm_ctx pm_ctx;
+
+enum { PM_WS_DELTA = 0, PM_WS_ZERO = 1, PM_WS_USER = 2 };
+
+/* Options of the mass solve  M Ab = b  (Sec. 2.4, Eq. phi_def). */
+typedef struct pm_solve_opts {
+    int warm_start;  /* PM_WS_DELTA: start from the delta assignment (default);
+                        PM_WS_ZERO: start from zero; PM_WS_USER: start from x0  */
+    double rtol;     /* stop when ||b - M Ab||_2 <= rtol ||b||_2 (default 1e-6)  */
+    int max_iter;    /* iteration cap (default 200)                              */
+    const float *x0; /* device [F][n^dim], read when warm_start == PM_WS_USER     */
+} pm_solve_opts;
+
+/* Per-field report of a mass solve (host memory, one entry per field). */
+typedef struct pm_solve_info {
+    int iters;             /* conjugate-gradient iterations taken                     */
+    double init_rel_resid; /* ||b - M x0|| / ||b|| of the start vector (after its mean
+                              is set exactly)                                          */
+    double rel_resid;      /* true residual ||b - M Ab|| / ||b|| at exit, recomputed   */
+    double sum_particles;  /* sum_mu v_mu A_mu  (Eq. cons, particle side)              */
+    double sum_mesh;       /* sum_i v_i Ab_i with v_i = h^dim (Eq. cons, mesh side)     */
+    double cons_err;       /* |sum_mesh - sum_particles| / sum_mu v_mu |A_mu|          */
+} pm_solve_info;
+
+/* Create a context for one periodic mesh (dim 1 or 2, n >= 4 nodes per side,
+ * box length L > 0) able to take up to max_particles particles and max_fields
+ * fields per call. stream is a cudaStream_t (NULL = legacy default stream).
+ * Allocates all device workspace now. *out is set only on success. */
+pm_status pm_ctx_create(pm_ctx **out, int dim, int n, double L, long long max_particles, int max_fields,
+                        void *stream);
+void pm_ctx_destroy(pm_ctx *ctx);
+pm_status pm_ctx_set_stream(pm_ctx *ctx, void *stream);
+/* Wait for the context's stream; return the device status word and clear it. */
+pm_status pm_sync(pm_ctx *ctx);
+const char *pm_last_error(const pm_ctx *ctx);
+/* Bytes of device workspace the context holds. */
+long long pm_ctx_workspace_bytes(const pm_ctx *ctx);
+
+/* Mesh -> particle interpolation, Sec. 2.2 Eq. delta2 (Table 1, right
+ * column for delta, FLIP and mass-delta):  out[f][k] = sum_i mesh[f][i] psi_i(r_k).
+ * mesh [F][n^dim], px/py [np], out [F][np]. np may be 0. Asynchronous. */
+pm_status pm_interpolate(pm_ctx *ctx, const float *mesh, int F, const float *px, const float *py, long long np,
+                         float *out);
+
+/* delta assignment, Sec. 2.2 Eq. delta:  mesh_out[f][i] = A_f(r_i) =
+ * sum_mu vals[f][mu] psi_mu(r_i).  Needs np >= 2 (1D) / np >= 3 (2D).
+ * Asynchronous. */
+pm_status pm_assign_delta(pm_ctx *ctx, const float *px, const float *py, long long np, const float *vals, int F,
+                          float *mesh_out);
+
+/* FLIP assignment, Sec. 2.3 Eqs. PIC and FLIP_vol:
+ *   v_i = sum_mu v_mu psi_i(r_mu),  Ab_i = sum_mu A_mu v_mu psi_i(r_mu) / v_i,
+ * with particle volumes v_mu = int psi_mu (Eq. part_v). A node with v_i = 0
+ * (no particle in its support, Sec. 2.3) gets Ab_i = 0.
+ * node_volume_out [n^dim] (device, may be NULL) receives v_i; empty_nodes
+ * (host, may be NULL) receives the number of nodes with v_i = 0 and makes the
+ * call wait for the stream. */
+pm_status pm_assign_flip(pm_ctx *ctx, const float *px, const float *py, long long np, const float *vals, int F,
+                         float *mesh_out, float *node_volume_out, long long *empty_nodes);
+
+/* Mass assignment ("mass-delta" particle -> mesh direction), Sec. 2.4
+ * Eqs. proj and phi_def:  Ab = M^-1 b  with  m_ij = int psi_i psi_j  and
+ * b_j = int A(r) psi_j(r) dr,  A the particle interpolant (Eq. part_interp).
+ * b is integrated exactly (particle triangles clipped against mesh cells).
+ * The solve is conjugate gradients on the matrix-free mass stencil, FP32
+ * vectors with compensated sums, FP64 reductions; the mean mode of Ab is set
+ * exactly from sum_j b_j first, so the result is conservative (Eq. cons) to
+ * rounding whatever the iteration count. info (host, F entries, may be NULL)
+ * makes the call wait for the stream. */
+pm_status pm_assign_mass(pm_ctx *ctx, const float *px, const float *py, long long np, const float *vals, int F,
+                         float *mesh_out, const pm_solve_opts *opts, pm_solve_info *info);
+
+/* Mass right-hand side alone: b_out[f][j] = int A_f(r) psi_j(r) dr (Sec. 2.4,
+ * Eq. proj), exact. Asynchronous. */
+pm_status pm_mass_rhs(pm_ctx *ctx, const float *px, const float *py, long long np, const float *vals, int F,
+                      float *b_out);
+
+/* Mesh mass matrix applied to mesh fields: y[f] = M x[f], m_ij = int psi_i psi_j
+ * (Sec. 2.4). Asynchronous. */
+pm_status pm_mass_apply(pm_ctx *ctx, const float *x, int F, float *y);
+
+/* Solve M x[f] = b[f] (Sec. 2.4, Eq. phi_def) by conjugate gradients; the
+ * start vector is zero or opts->x0 (PM_WS_DELTA is read as zero here).
+ * info as in pm_assign_mass (sum_particles = sum_j b_j there). */
+pm_status pm_mass_solve(pm_ctx *ctx, const float *b, int F, float *x, const pm_solve_opts *opts,
+                        pm_solve_info *info);
+
+/* Particle volumes v_mu = int psi_mu (Sec. 2.1, Eq. part_v), in the caller's
+ * particle order. v_out [np]. Asynchronous. */
+pm_status pm_particle_volumes(pm_ctx *ctx, const float *px, const float *py, long long np, float *v_out);
+
+/* The periodic Delaunay triangulation of the particles (2D only, Sec. 3.2,
+ * App. A): every triangle once, as caller particle indices (p, a, b) counter-
+ * clockwise with p the vertex that comes first in the library's cell order,
+ * and the image offsets (ax, ay, bx, by) in box lengths of a and b relative
+ * to p. tri_out [max_tri][3], off_out [max_tri][4] (device, int32); *ntri
+ * (host) receives the count (2 np on the torus). Waits for the stream. */
+pm_status pm_triangulate(pm_ctx *ctx, const float *px, const float *py, long long np, int *tri_out, int *off_out,
+                         long long max_tri, long long *ntri);
+
+/* Counting sort of the particles by mesh cell (row-major cell, then caller
+ * index; 1D: then torus coordinate): perm_out [np] receives caller indices in
+ * sorted order, cell_start_out [n^dim + 1] the first sorted slot of every cell.
+ * Asynchronous. */
+pm_status pm_sort(pm_ctx *ctx, const float *px, const float *py, long long np, int *perm_out, int *cell_start_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PMT_H */

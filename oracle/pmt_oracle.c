@@ -21,9 +21,9 @@
  * uniform periodic mesh.
  *
  * Positions: a float coordinate x on a periodic box of length L is read as
- * the 32-bit fixed-point torus coordinate X = floor(frac(x/L) * 2^32); every
- * geometric decision (cell, ordering, Delaunay predicates) is taken on X,
- * exactly, and the physical position is X * L / 2^32.
+ * the 32-bit fixed-point torus coordinate X ~ frac(x/L) * 2^32 (see
+ * fixcoord); every geometric decision (cell, ordering, Delaunay predicates)
+ * is taken on X, exactly, and the physical position is X * L / 2^32.
  *
  * Parity-unpinned parts are listed in the Python wrapper's docstring.
  */
@@ -43,15 +43,19 @@ enum { OR_OK = 0, OR_EINVAL = 1, OR_ENOMEM = 2, OR_EDEGENERATE = 5 };
 /* Positions                                                                  */
 /* ------------------------------------------------------------------------ */
 
-/* x -> floor(frac(x/L) * 2^32), all steps exact or correctly rounded IEEE. */
+/* Canonical torus coordinate of a float position x on a box of length L:
+ *   t = fl32(x * fl32(1/L))   (one correctly rounded single-precision product)
+ *   X = floor((t - floor(t)) * 2^32) mod 2^32
+ * t - floor(t) and the scaling by 2^32 are exact in single precision, so X is
+ * fully determined by IEEE arithmetic and lies within one float ulp of the
+ * exact frac(x/L) 2^32. */
 static int fixcoord(float xf, double L, uint32_t *out) {
-    double x = (double)xf;
-    if (!isfinite(x)) return OR_EINVAL;
-    double t = x / L;
-    t = t - floor(t);
-    double u = floor(t * TWO32);
-    if (u >= TWO32) u = 0.0;
-    *out = (uint32_t)u;
+    if (!isfinite(xf)) return OR_EINVAL;
+    volatile float invL = (float)(1.0 / L);
+    volatile float t = xf * invL;
+    float f = t - floorf(t);
+    if (f >= 1.0f) f = 0.0f;
+    *out = (uint32_t)(f * 4294967296.0f);
     return OR_OK;
 }
 

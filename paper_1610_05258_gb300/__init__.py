@@ -1,1 +1,262 @@
-"""GB300-native particle<->mesh field transfer (arXiv 1610.05258)."""
+"""GB300-native particle <-> mesh field transfer (arXiv 1610.05258).
+
+A thin ctypes binding over the C ABI in ``include/pmt.h``; every step of the
+transfer runs in the library's CUDA kernels. PyTorch provides device memory
+and the current stream only. Importing this package does not load the
+library; the first Context does, and raises if it is missing or no CUDA
+device is present. There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+__all__ = ["Context", "PMError", "SolveInfo", "load_library", "library_path"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "_build", "libpmt.so")
+_lib = None
+
+PM_WS_DELTA, PM_WS_ZERO, PM_WS_USER = 0, 1, 2
+_STATUS = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ENOTCONV", 4: "PM_ETIMEOUT", 5: "PM_EDEGENERATE",
+           6: "PM_ECUDA"}
+
+EXPORTS = [
+    "pm_ctx_create", "pm_ctx_destroy", "pm_ctx_set_stream", "pm_sync", "pm_last_error", "pm_ctx_workspace_bytes",
+    "pm_interpolate", "pm_assign_delta", "pm_assign_flip", "pm_assign_mass", "pm_mass_rhs", "pm_mass_apply",
+    "pm_mass_solve", "pm_particle_volumes", "pm_triangulate", "pm_sort",
+]
+
+
+class PMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("warm_start", ctypes.c_int), ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("x0", ctypes.c_void_p)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("init_rel_resid", ctypes.c_double), ("rel_resid", ctypes.c_double),
+                ("sum_particles", ctypes.c_double), ("sum_mesh", ctypes.c_double), ("cons_err", ctypes.c_double)]
+
+
+@dataclass
+class SolveInfo:
+    iters: int
+    init_rel_resid: float
+    rel_resid: float
+    sum_particles: float
+    sum_mesh: float
+    cons_err: float
+
+
+def library_path() -> str:
+    return _LIBPATH
+
+
+def load_library(path: str | None = None):
+    """Load libpmt.so (built by paper_1610_05258_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or _LIBPATH
+    if not os.path.exists(p):
+        raise ImportError(f"libpmt.so not built ({p}); run `python -m paper_1610_05258_gb300.build`")
+    lib = ctypes.CDLL(p)
+    vp, ll, i, d = ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int, ctypes.c_double
+    sig = {
+        "pm_ctx_create": [ctypes.POINTER(vp), i, i, d, ll, i, vp],
+        "pm_ctx_destroy": [vp],
+        "pm_ctx_set_stream": [vp, vp],
+        "pm_sync": [vp],
+        "pm_last_error": [vp],
+        "pm_ctx_workspace_bytes": [vp],
+        "pm_interpolate": [vp, vp, i, vp, vp, ll, vp],
+        "pm_assign_delta": [vp, vp, vp, ll, vp, i, vp],
+        "pm_assign_flip": [vp, vp, vp, ll, vp, i, vp, vp, ctypes.POINTER(ll)],
+        "pm_assign_mass": [vp, vp, vp, ll, vp, i, vp, ctypes.POINTER(_Opts), vp],
+        "pm_mass_rhs": [vp, vp, vp, ll, vp, i, vp],
+        "pm_mass_apply": [vp, vp, i, vp],
+        "pm_mass_solve": [vp, vp, i, vp, ctypes.POINTER(_Opts), vp],
+        "pm_particle_volumes": [vp, vp, vp, ll, vp],
+        "pm_triangulate": [vp, vp, vp, ll, vp, vp, ll, ctypes.POINTER(ll)],
+        "pm_sort": [vp, vp, vp, ll, vp, vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.pm_last_error.restype = ctypes.c_char_p
+    lib.pm_ctx_workspace_bytes.restype = ctypes.c_longlong
+    lib.pm_ctx_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One periodic mesh (dim 1 or 2, n nodes per side, box length L) with
+    workspace for up to max_particles particles and max_fields fields."""
+
+    def __init__(self, dim: int, n: int, L: float, max_particles: int, max_fields: int = 1, device=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_1610_05258_gb300 needs a CUDA device (no CPU fallback)")
+        self.torch = torch
+        self.lib = load_library()
+        self.device = torch.device(device if device is not None else "cuda")
+        self.dim, self.n, self.L = dim, n, float(L)
+        self.max_particles, self.max_fields = max_particles, max_fields
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = torch.cuda.current_stream().cuda_stream
+            s = self.lib.pm_ctx_create(ctypes.byref(h), dim, n, ctypes.c_double(L), max_particles, max_fields,
+                                       ctypes.c_void_p(st))
+        if s != 0:
+            raise PMError(s, "pm_ctx_create failed")
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.lib is not None:
+            self.lib.pm_ctx_destroy(self.h)
+            self.h = None
+
+    @property
+    def workspace_bytes(self) -> int:
+        return self.lib.pm_ctx_workspace_bytes(self.h)
+
+    def _stream(self):
+        self.lib.pm_ctx_set_stream(self.h, ctypes.c_void_p(self.torch.cuda.current_stream(self.device).cuda_stream))
+
+    def _check(self, s):
+        if s != 0:
+            raise PMError(s, self.lib.pm_last_error(self.h).decode())
+
+    def _f32(self, t):
+        if t is None:
+            return None
+        if not (t.is_cuda and t.dtype == self.torch.float32 and t.is_contiguous()):
+            raise TypeError("expected a contiguous float32 CUDA tensor")
+        return t
+
+    def _empty(self, *shape):
+        return self.torch.empty(*shape, dtype=self.torch.float32, device=self.device)
+
+    @property
+    def nodes(self) -> int:
+        return self.n ** self.dim
+
+    def sync(self):
+        self._check(self.lib.pm_sync(self.h))
+
+    def interpolate(self, mesh, px, py=None, out=None):
+        mesh, px, py = self._f32(mesh), self._f32(px), self._f32(py)
+        F = mesh.numel() // self.nodes
+        out = out if out is not None else self._empty(F, px.numel())
+        self._stream()
+        self._check(self.lib.pm_interpolate(self.h, _ptr(mesh), F, _ptr(px), _ptr(py), px.numel(), _ptr(out)))
+        return out
+
+    def assign_delta(self, px, py, vals, out=None):
+        px, py, vals = self._f32(px), self._f32(py), self._f32(vals)
+        F = vals.numel() // max(1, px.numel())
+        out = out if out is not None else self._empty(F, self.nodes)
+        self._stream()
+        self._check(self.lib.pm_assign_delta(self.h, _ptr(px), _ptr(py), px.numel(), _ptr(vals), F, _ptr(out)))
+        return out
+
+    def assign_flip(self, px, py, vals, out=None, node_volume=None, count_empty=False):
+        px, py, vals = self._f32(px), self._f32(py), self._f32(vals)
+        F = vals.numel() // max(1, px.numel())
+        out = out if out is not None else self._empty(F, self.nodes)
+        e = ctypes.c_longlong(0)
+        self._stream()
+        self._check(self.lib.pm_assign_flip(self.h, _ptr(px), _ptr(py), px.numel(), _ptr(vals), F, _ptr(out),
+                                            _ptr(node_volume), ctypes.byref(e) if count_empty else None))
+        return (out, e.value) if count_empty else out
+
+    def _opts(self, warm_start, rtol, max_iter, x0):
+        ws = {"delta": PM_WS_DELTA, "zero": PM_WS_ZERO, "user": PM_WS_USER}[warm_start]
+        return _Opts(ws, rtol, max_iter, x0.data_ptr() if x0 is not None else None)
+
+    def assign_mass(self, px, py, vals, out=None, warm_start="delta", rtol=1e-6, max_iter=200, x0=None,
+                    info=True):
+        px, py, vals, x0 = self._f32(px), self._f32(py), self._f32(vals), self._f32(x0)
+        F = vals.numel() // max(1, px.numel())
+        out = out if out is not None else self._empty(F, self.nodes)
+        o = self._opts(warm_start, rtol, max_iter, x0)
+        inf = (_Info * F)() if info else None
+        self._stream()
+        s = self.lib.pm_assign_mass(self.h, _ptr(px), _ptr(py), px.numel(), _ptr(vals), F, _ptr(out),
+                                    ctypes.byref(o), inf)
+        self._check(s)
+        if not info:
+            return out
+        return out, [SolveInfo(x.iters, x.init_rel_resid, x.rel_resid, x.sum_particles, x.sum_mesh, x.cons_err)
+                     for x in inf]
+
+    def mass_rhs(self, px, py, vals, out=None):
+        px, py, vals = self._f32(px), self._f32(py), self._f32(vals)
+        F = vals.numel() // max(1, px.numel())
+        out = out if out is not None else self._empty(F, self.nodes)
+        self._stream()
+        self._check(self.lib.pm_mass_rhs(self.h, _ptr(px), _ptr(py), px.numel(), _ptr(vals), F, _ptr(out)))
+        return out
+
+    def mass_apply(self, x, out=None):
+        x = self._f32(x)
+        F = x.numel() // self.nodes
+        out = out if out is not None else self._empty(F, self.nodes)
+        self._stream()
+        self._check(self.lib.pm_mass_apply(self.h, _ptr(x), F, _ptr(out)))
+        return out
+
+    def mass_solve(self, b, out=None, rtol=1e-6, max_iter=200, x0=None, info=True):
+        b, x0 = self._f32(b), self._f32(x0)
+        F = b.numel() // self.nodes
+        out = out if out is not None else self._empty(F, self.nodes)
+        o = self._opts("user" if x0 is not None else "zero", rtol, max_iter, x0)
+        inf = (_Info * F)() if info else None
+        self._stream()
+        self._check(self.lib.pm_mass_solve(self.h, _ptr(b), F, _ptr(out), ctypes.byref(o), inf))
+        if not info:
+            return out
+        return out, [SolveInfo(x.iters, x.init_rel_resid, x.rel_resid, x.sum_particles, x.sum_mesh, x.cons_err)
+                     for x in inf]
+
+    def particle_volumes(self, px, py=None, out=None):
+        px, py = self._f32(px), self._f32(py)
+        out = out if out is not None else self._empty(px.numel())
+        self._stream()
+        self._check(self.lib.pm_particle_volumes(self.h, _ptr(px), _ptr(py), px.numel(), _ptr(out)))
+        return out
+
+    def triangulate(self, px, py):
+        px, py = self._f32(px), self._f32(py)
+        cap = 2 * px.numel() + 64
+        tri = self.torch.empty((cap, 3), dtype=self.torch.int32, device=self.device)
+        off = self.torch.empty((cap, 4), dtype=self.torch.int32, device=self.device)
+        nt = ctypes.c_longlong(0)
+        self._stream()
+        self._check(self.lib.pm_triangulate(self.h, _ptr(px), _ptr(py), px.numel(), _ptr(tri), _ptr(off), cap,
+                                            ctypes.byref(nt)))
+        return tri[: nt.value], off[: nt.value]
+
+    def sort(self, px, py=None):
+        px, py = self._f32(px), self._f32(py)
+        perm = self.torch.empty(px.numel(), dtype=self.torch.int32, device=self.device)
+        cs = self.torch.empty(self.nodes + 1, dtype=self.torch.int32, device=self.device)
+        self._stream()
+        self._check(self.lib.pm_sort(self.h, _ptr(px), _ptr(py), px.numel(), _ptr(perm), _ptr(cs)))
+        return perm, cs

@@ -1,0 +1,341 @@
+// C ABI (include/pmt.h): context, workspace and the entry points. Each entry
+// validates its arguments on the host, then queues the kernels of its path on
+// the context's stream.
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "internal.cuh"
+
+struct pm_ctx {
+    Geo g;
+    Work w;
+    cudaStream_t st;
+    std::string err;
+    ll bytes;
+    int dev;
+};
+
+namespace {
+
+pm_status fail(pm_ctx *c, pm_status s, const char *msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+pm_status cuda_fail(pm_ctx *c, cudaError_t e, const char *where) {
+    if (c) c->err = std::string(where) + ": " + cudaGetErrorString(e);
+    return PM_ECUDA;
+}
+
+template <class T>
+bool alloc(pm_ctx *c, T **p, ll count) {
+    size_t b = sizeof(T) * (size_t)(count > 0 ? count : 1);
+    if (cudaMalloc((void **)p, b) != cudaSuccess) return false;
+    c->bytes += (ll)b;
+    return true;
+}
+
+pm_status map_status(pm_ctx *c, int s) {
+    if (s & (ST_NONFINITE | ST_DUP | ST_SPARSE | ST_DEGREE | ST_RANGE)) {
+        char buf[256];
+        snprintf(buf, sizeof buf, "degenerate input (device status 0x%x:%s%s%s%s%s)", s,
+                 s & ST_NONFINITE ? " non-finite value" : "", s & ST_DUP ? " coincident particles" : "",
+                 s & ST_SPARSE ? " triangulation not certified within the searched cells" : "",
+                 s & ST_DEGREE ? " Delaunay degree above capacity" : "", s & ST_RANGE ? " internal range" : "");
+        c->err = buf;
+        return PM_EDEGENERATE;
+    }
+    if (s & ST_TIMEOUT) return fail(c, PM_ETIMEOUT, "a device-side wait timed out");
+    if (s & ST_NOTCONV) return fail(c, PM_ENOTCONV, "mass solve did not reach the requested residual");
+    return PM_OK;
+}
+
+// Wait for the stream, fetch and clear the device status word.
+pm_status wait_status(pm_ctx *c) {
+    cudaError_t e = cudaMemcpyAsync(c->w.hstatus, c->w.status, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream");
+    int s = *c->w.hstatus;
+    if (s) cudaMemsetAsync(c->w.status, 0, sizeof(int), c->st);
+    return map_status(c, s);
+}
+
+pm_status check_launch(pm_ctx *c, const char *where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, where);
+    return PM_OK;
+}
+
+pm_status check_particles(pm_ctx *c, const float *px, const float *py, ll np, int F, const float *vals,
+                          ll min_np) {
+    if (!c) return PM_EINVAL;
+    if (np < min_np || np > c->w.np_max) return fail(c, PM_EINVAL, "particle count out of range");
+    if (np > 0 && (!px || (c->g.dim == 2 && !py))) return fail(c, PM_EINVAL, "null position array");
+    if (F < 0 || F > c->w.F_max) return fail(c, PM_EINVAL, "field count out of range");
+    if (F > 0 && np > 0 && !vals) return fail(c, PM_EINVAL, "null particle field array");
+    return PM_OK;
+}
+
+// Sort + particle functions: everything the assignments share.
+pm_status prepare(pm_ctx *c, const float *px, const float *py, ll np, const float *vals, int F, bool need_tri) {
+    launch_sort(c->g, c->w, px, py, np, vals, F, c->st);
+    if (need_tri) {
+        if (c->g.dim == 2)
+            launch_triangulate(c->g, c->w, np, c->st);
+        else
+            launch_volumes_1d(c->g, c->w, np, c->st);
+    }
+    return check_launch(c, "prepare");
+}
+
+}  // namespace
+
+extern "C" {
+
+pm_status pm_ctx_create(pm_ctx **out, int dim, int n, double L, long long max_particles, int max_fields,
+                        void *stream) {
+    if (!out) return PM_EINVAL;
+    *out = nullptr;
+    if ((dim != 1 && dim != 2) || n < 4 || !(L > 0.0) || max_particles < 0 || max_fields < 1 ||
+        max_fields > PM_MAXF)
+        return PM_EINVAL;
+    if (max_particles >= (1LL << 28)) return PM_EINVAL;
+    if (dim == 2 && (ll)n * n > (1LL << 30)) return PM_EINVAL;
+    pm_ctx *c = new pm_ctx();
+    c->bytes = 0;
+    c->st = (cudaStream_t)stream;
+    cudaGetDevice(&c->dev);
+    Geo &g = c->g;
+    g.dim = dim;
+    g.n = n;
+    g.L = L;
+    g.invL = (float)(1.0 / L);
+    g.h = (float)(L / n);
+    g.ncell = dim == 1 ? n : (ll)n * n;
+    Work &w = c->w;
+    memset(&w, 0, sizeof(w));
+    w.np_max = max_particles;
+    w.F_max = max_fields;
+    const ll np = max_particles, nc = g.ncell, F = max_fields;
+    w.nblk_psum = 256;
+    bool ok = alloc(c, &w.fx, np) && alloc(c, &w.key, np) && alloc(c, &w.slot, np) && alloc(c, &w.count, nc) &&
+              alloc(c, &w.cell_start, nc + 1) && alloc(c, &w.scan_tmp, nc / 4096 + 2) && alloc(c, &w.tmp, np) &&
+              alloc(c, &w.perm, np) && alloc(c, &w.pos, np) && alloc(c, &w.vals, np * F) &&
+              alloc(c, &w.maxabs, PM_MAXF) && alloc(c, &w.deg, np) && alloc(c, &w.vol, np) &&
+              alloc(c, &w.part, (dim == 2 ? 4 : 2) * (F + 1) * nc) && alloc(c, &w.bfix, F * nc) &&
+              alloc(c, &w.psum, 2 * PM_MAXF * (ll)w.nblk_psum) && alloc(c, &w.r, F * nc) &&
+              alloc(c, &w.p, F * nc) && alloc(c, &w.q, F * nc) && alloc(c, &w.b, F * nc) &&
+              alloc(c, &w.red, 6LL * PM_MAXF * 4096) && alloc(c, &w.scal, 16LL * PM_MAXF) &&
+              alloc(c, &w.bar, 2) && alloc(c, &w.status, 1) && alloc(c, &w.empty, 1) && alloc(c, &w.ntri, 1);
+    if (ok && dim == 2) ok = alloc(c, &w.nbr, (ll)PM_MAXDEG * np);
+    if (ok && cudaMallocHost((void **)&w.hstatus, sizeof(int)) != cudaSuccess) ok = false;
+    if (!ok) {
+        pm_ctx_destroy(c);
+        cudaGetLastError();
+        return PM_ENOMEM;
+    }
+    cudaMemset(w.status, 0, sizeof(int));
+    cudaMemset(w.scal, 0, sizeof(double) * 16 * PM_MAXF);
+    cudaMemset(w.deg, 0, (size_t)(np > 0 ? np : 1));
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        pm_ctx_destroy(c);
+        return PM_ECUDA;
+    }
+    *out = c;
+    return PM_OK;
+}
+
+void pm_ctx_destroy(pm_ctx *c) {
+    if (!c) return;
+    Work &w = c->w;
+    void *ptrs[] = {w.fx,  w.key, w.slot, w.count, w.cell_start, w.scan_tmp, w.tmp,  w.perm, w.pos,
+                    w.vals, w.maxabs, w.nbr, w.deg,  w.vol,  w.part,  w.bfix, w.psum, w.r,    w.p,
+                    w.q,   w.b,   w.red,  w.scal,  w.bar,  w.status, w.empty, w.ntri};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (w.hstatus) cudaFreeHost(w.hstatus);
+    delete c;
+}
+
+pm_status pm_ctx_set_stream(pm_ctx *c, void *stream) {
+    if (!c) return PM_EINVAL;
+    c->st = (cudaStream_t)stream;
+    return PM_OK;
+}
+
+pm_status pm_sync(pm_ctx *c) {
+    if (!c) return PM_EINVAL;
+    return wait_status(c);
+}
+
+const char *pm_last_error(const pm_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+long long pm_ctx_workspace_bytes(const pm_ctx *c) { return c ? c->bytes : 0; }
+
+pm_status pm_interpolate(pm_ctx *c, const float *mesh, int F, const float *px, const float *py, long long np,
+                         float *out) {
+    pm_status s = check_particles(c, px, py, np, 0, nullptr, 0);
+    if (s) return s;
+    if (F < 1 || F > c->w.F_max) return fail(c, PM_EINVAL, "field count out of range");
+    if (np > 0 && (!mesh || !out)) return fail(c, PM_EINVAL, "null mesh or output array");
+    launch_g2p(c->g, mesh, F, px, py, np, out, c->w.status, c->st);
+    return check_launch(c, "pm_interpolate");
+}
+
+pm_status pm_assign_delta(pm_ctx *c, const float *px, const float *py, long long np, const float *vals, int F,
+                          float *mesh_out) {
+    pm_status s = check_particles(c, px, py, np, F, vals, c && c->g.dim == 2 ? 3 : 2);
+    if (s) return s;
+    if (F < 1 || !mesh_out) return fail(c, PM_EINVAL, "null output or no field");
+    if ((s = prepare(c, px, py, np, vals, F, c->g.dim == 2))) return s;
+    launch_delta(c->g, c->w, np, F, mesh_out, c->st);
+    return check_launch(c, "pm_assign_delta");
+}
+
+pm_status pm_assign_flip(pm_ctx *c, const float *px, const float *py, long long np, const float *vals, int F,
+                         float *mesh_out, float *node_volume_out, long long *empty_nodes) {
+    pm_status s = check_particles(c, px, py, np, F, vals, c && c->g.dim == 2 ? 3 : 2);
+    if (s) return s;
+    if (F < 1 || !mesh_out) return fail(c, PM_EINVAL, "null output or no field");
+    if ((s = prepare(c, px, py, np, vals, F, true))) return s;
+    launch_flip(c->g, c->w, np, F, mesh_out, node_volume_out, c->st);
+    if ((s = check_launch(c, "pm_assign_flip"))) return s;
+    if (empty_nodes) {
+        int e = 0;
+        cudaMemcpyAsync(c->w.hstatus, c->w.empty, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+        cudaError_t ce = cudaStreamSynchronize(c->st);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "pm_assign_flip");
+        e = *c->w.hstatus;
+        *empty_nodes = e;
+        return wait_status(c);
+    }
+    return PM_OK;
+}
+
+static void default_opts(const pm_solve_opts *o, pm_solve_opts &d) {
+    d.warm_start = PM_WS_DELTA;
+    d.rtol = 1e-6;
+    d.max_iter = 200;
+    d.x0 = nullptr;
+    if (o) d = *o;
+    if (!(d.rtol > 0.0)) d.rtol = 1e-6;
+    if (d.max_iter <= 0) d.max_iter = 200;
+}
+
+static pm_status fill_info(pm_ctx *c, int F, pm_solve_info *info) {
+    pm_status s = wait_status(c);
+    double sc[16 * PM_MAXF];
+    cudaError_t e = cudaMemcpy(sc, c->w.scal, sizeof(double) * 16 * F, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "info");
+    for (int f = 0; f < F; ++f) {
+        const double *v = sc + 16 * f;
+        info[f].iters = (int)v[0];
+        info[f].init_rel_resid = v[1];
+        info[f].rel_resid = v[2];
+        info[f].sum_mesh = v[3];
+        info[f].sum_particles = v[4];
+        double den = v[5] > 0.0 ? v[5] : fabs(v[4]);
+        info[f].cons_err = den > 0.0 ? fabs(v[3] - v[4]) / den : fabs(v[3] - v[4]);
+    }
+    return s;
+}
+
+pm_status pm_assign_mass(pm_ctx *c, const float *px, const float *py, long long np, const float *vals, int F,
+                         float *mesh_out, const pm_solve_opts *opts, pm_solve_info *info) {
+    pm_status s = check_particles(c, px, py, np, F, vals, c && c->g.dim == 2 ? 3 : 2);
+    if (s) return s;
+    if (F < 1 || !mesh_out) return fail(c, PM_EINVAL, "null output or no field");
+    pm_solve_opts o;
+    default_opts(opts, o);
+    if (o.warm_start == PM_WS_USER && !o.x0) return fail(c, PM_EINVAL, "PM_WS_USER without x0");
+    if ((s = prepare(c, px, py, np, vals, F, true))) return s;
+    launch_psum(c->g, c->w, np, F, c->st);
+    launch_rhs(c->g, c->w, np, F, c->st);
+    bool start = true;
+    if (o.warm_start == PM_WS_DELTA)
+        launch_delta(c->g, c->w, np, F, mesh_out, c->st);
+    else if (o.warm_start == PM_WS_USER)
+        cudaMemcpyAsync(mesh_out, o.x0, sizeof(float) * F * c->g.ncell, cudaMemcpyDeviceToDevice, c->st);
+    else
+        start = false;
+    if ((s = check_launch(c, "pm_assign_mass"))) return s;
+    int e = launch_cg(c->g, c->w, F, nullptr, true, mesh_out, start, o.rtol, o.max_iter, c->st);
+    if (e) return cuda_fail(c, (cudaError_t)e, "pm_assign_mass solve launch");
+    if (info) return fill_info(c, F, info);
+    return PM_OK;
+}
+
+pm_status pm_mass_rhs(pm_ctx *c, const float *px, const float *py, long long np, const float *vals, int F,
+                      float *b_out) {
+    pm_status s = check_particles(c, px, py, np, F, vals, c && c->g.dim == 2 ? 3 : 2);
+    if (s) return s;
+    if (F < 1 || !b_out) return fail(c, PM_EINVAL, "null output or no field");
+    if ((s = prepare(c, px, py, np, vals, F, true))) return s;
+    launch_rhs(c->g, c->w, np, F, c->st);
+    launch_rhs_to_float(c->g, c->w, F, b_out, c->st);
+    return check_launch(c, "pm_mass_rhs");
+}
+
+pm_status pm_mass_apply(pm_ctx *c, const float *x, int F, float *y) {
+    if (!c) return PM_EINVAL;
+    if (F < 1 || F > c->w.F_max || !x || !y) return fail(c, PM_EINVAL, "bad mass_apply arguments");
+    launch_mass_apply(c->g, x, F, y, c->st);
+    return check_launch(c, "pm_mass_apply");
+}
+
+pm_status pm_mass_solve(pm_ctx *c, const float *b, int F, float *x, const pm_solve_opts *opts,
+                        pm_solve_info *info) {
+    if (!c) return PM_EINVAL;
+    if (F < 1 || F > c->w.F_max || !b || !x) return fail(c, PM_EINVAL, "bad mass_solve arguments");
+    pm_solve_opts o;
+    default_opts(opts, o);
+    bool start = false;
+    if (o.warm_start == PM_WS_USER) {
+        if (!o.x0) return fail(c, PM_EINVAL, "PM_WS_USER without x0");
+        if (o.x0 != x) cudaMemcpyAsync(x, o.x0, sizeof(float) * F * c->g.ncell, cudaMemcpyDeviceToDevice, c->st);
+        start = true;
+    }
+    int e = launch_cg(c->g, c->w, F, b, false, x, start, o.rtol, o.max_iter, c->st);
+    if (e) return cuda_fail(c, (cudaError_t)e, "pm_mass_solve launch");
+    if (info) return fill_info(c, F, info);
+    return PM_OK;
+}
+
+pm_status pm_particle_volumes(pm_ctx *c, const float *px, const float *py, long long np, float *v_out) {
+    pm_status s = check_particles(c, px, py, np, 0, nullptr, c && c->g.dim == 2 ? 3 : 2);
+    if (s) return s;
+    if (!v_out) return fail(c, PM_EINVAL, "null output");
+    if ((s = prepare(c, px, py, np, nullptr, 0, true))) return s;
+    launch_scatter_sorted(np, c->w.perm, c->w.vol, v_out, c->st);
+    return check_launch(c, "pm_particle_volumes");
+}
+
+pm_status pm_triangulate(pm_ctx *c, const float *px, const float *py, long long np, int *tri_out, int *off_out,
+                         long long max_tri, long long *ntri) {
+    pm_status s = check_particles(c, px, py, np, 0, nullptr, 3);
+    if (s) return s;
+    if (c->g.dim != 2) return fail(c, PM_EINVAL, "pm_triangulate needs dim == 2");
+    if (!tri_out || !off_out || !ntri || max_tri < 0) return fail(c, PM_EINVAL, "bad output arguments");
+    if ((s = prepare(c, px, py, np, nullptr, 0, true))) return s;
+    launch_export_tris(c->g, c->w, np, tri_out, off_out, max_tri, c->st);
+    if ((s = check_launch(c, "pm_triangulate"))) return s;
+    ll cnt = 0;
+    cudaMemcpyAsync(&cnt, c->w.ntri, sizeof(ll), cudaMemcpyDeviceToHost, c->st);
+    s = wait_status(c);
+    *ntri = cnt;
+    if (!s && cnt > max_tri) return fail(c, PM_EINVAL, "max_tri too small");
+    return s;
+}
+
+pm_status pm_sort(pm_ctx *c, const float *px, const float *py, long long np, int *perm_out, int *cell_start_out) {
+    pm_status s = check_particles(c, px, py, np, 0, nullptr, 0);
+    if (s) return s;
+    if (!perm_out || !cell_start_out) return fail(c, PM_EINVAL, "null output");
+    if ((s = prepare(c, px, py, np, nullptr, 0, false))) return s;
+    if (np > 0) cudaMemcpyAsync(perm_out, c->w.perm, sizeof(int) * np, cudaMemcpyDeviceToDevice, c->st);
+    cudaMemcpyAsync(cell_start_out, c->w.cell_start, sizeof(int) * (c->g.ncell + 1), cudaMemcpyDeviceToDevice, c->st);
+    return check_launch(c, "pm_sort");
+}
+
+}  // extern "C"

@@ -1,0 +1,146 @@
+// Internal declarations shared by the CUDA translation units of libpmt.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pmt.h"
+
+#define PM_MAXDEG 24   // Delaunay degree stored per particle
+#define PM_MAXW 32     // capacity of the working Voronoi polygon
+#define PM_MAXF 8      // fields per call
+#define PM_RCAP 12     // rings of cells searched by the triangulation
+
+typedef long long ll;
+typedef unsigned long long ull;
+typedef __int128 i128;
+
+// Device status bits (OR-ed into one word, mapped to pm_status on the host).
+enum {
+    ST_NONFINITE = 1,
+    ST_DUP = 2,
+    ST_SPARSE = 4,
+    ST_DEGREE = 8,
+    ST_NOTCONV = 16,
+    ST_TIMEOUT = 32,
+    ST_RANGE = 64,
+};
+
+// One periodic mesh.
+struct Geo {
+    int dim;       // 1 or 2
+    int n;         // nodes (= cells) per side
+    double L;      // box length
+    float invL;    // fl32(1/L), defines the torus coordinate
+    float h;       // fl32(L/n)
+    ll ncell;      // n^dim
+};
+
+// Device workspace of a context (all sized at creation).
+struct Work {
+    ll np_max;
+    int F_max;
+    // sort
+    uint2 *fx;          // torus coordinates, caller order
+    int *key, *slot;    // cell and arrival slot, caller order
+    int *count;         // [ncell] particles per cell
+    int *cell_start;    // [ncell + 1]
+    int *scan_tmp;      // block sums of the scan
+    int *tmp;           // caller indices placed by cell, before canonical order
+    int *perm;          // sorted slot -> caller index
+    uint2 *pos;         // torus coordinates, sorted
+    float *vals;        // [F][np] particle fields, sorted
+    unsigned *maxabs;   // [F] max |A| bit patterns
+    // particle functions
+    int *nbr;           // [PM_MAXDEG][np] Delaunay neighbours (sorted index | image code << 28)
+    unsigned char *deg; // [np]
+    float *vol;         // [np] v_mu, sorted order
+    // scatter / rhs
+    float *part;        // [4 (F+1)][ncell] per-cell corner partials (FLIP)
+    ll *bfix;           // [F][ncell] fixed-point right-hand side
+    double *psum;       // [2 F][nblk] per-block particle sums (sum v A, sum v |A|)
+    int nblk_psum;
+    // solver
+    float *r, *p, *q, *b;  // [F][ncell]
+    double *red;           // reduction partials [slots][grid]
+    double *scal;          // solver scalars per field
+    unsigned *bar;         // grid barrier words (2)
+    int *status;           // device status word
+    int *hstatus;          // pinned host mirror
+    int *empty;            // empty-node counter
+    ll *ntri;              // triangle counter
+};
+
+// ---------------------------------------------------------------------------
+// Torus coordinate: X = floor(frac(fl32(x * fl32(1/L))) 2^32).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t torus_coord(float x, float invL) {
+    float t = __fmul_rn(x, invL);
+    float f = __fsub_rn(t, floorf(t));
+    if (!(f < 1.0f)) f = 0.0f;
+    return (uint32_t)__fmul_rn(f, 4294967296.0f);
+}
+__device__ __forceinline__ int cell_of(uint32_t X, int n) { return (int)(((ull)X * (ull)n) >> 32); }
+__device__ __forceinline__ uint32_t cell_frac(uint32_t X, int n) { return (uint32_t)((ull)X * (ull)n); }
+__device__ __forceinline__ float frac_f(uint32_t X, int n) { return (float)cell_frac(X, n) * 2.3283064365386963e-10f; }
+__device__ __forceinline__ int wrapi(int i, int n) { int r = i % n; return r < 0 ? r + n : r; }
+
+// Compensated (Kahan-Babuska/Neumaier) accumulator in FP32.
+struct KSum {
+    float s, c;
+    __device__ __forceinline__ KSum() : s(0.f), c(0.f) {}
+    __device__ __forceinline__ void add(float x) {
+        float t = s + x;
+        c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+        s = t;
+    }
+    __device__ __forceinline__ float get() const { return s + c; }
+};
+
+// Error-free product and sum (for compensated dot products).
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = __fmul_rn(a, b);
+    e = fmaf(a, b, -p);
+}
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+// Dot2-style accumulator: sum of products carried as (hi, lo).
+struct Dot2 {
+    float hi, lo;
+    __device__ __forceinline__ Dot2() : hi(0.f), lo(0.f) {}
+    __device__ __forceinline__ void fma_acc(float a, float b) {
+        float p, e, s, e2;
+        two_prod(a, b, p, e);
+        two_sum(hi, p, s, e2);
+        hi = s;
+        lo += e + e2;
+    }
+    __device__ __forceinline__ void add(float a) {
+        float s, e;
+        two_sum(hi, a, s, e);
+        hi = s;
+        lo += e;
+    }
+};
+
+static inline int div_up(ll a, int b) { return (int)((a + b - 1) / b); }
+
+// Launchers (one per translation unit, all asynchronous on `st`).
+void launch_sort(const Geo &g, Work &w, const float *px, const float *py, ll np, const float *vals, int F,
+                 cudaStream_t st);
+void launch_g2p(const Geo &g, const float *mesh, int F, const float *px, const float *py, ll np, float *out,
+                int *status, cudaStream_t st);
+void launch_triangulate(const Geo &g, Work &w, ll np, cudaStream_t st);
+void launch_volumes_1d(const Geo &g, Work &w, ll np, cudaStream_t st);
+void launch_delta(const Geo &g, Work &w, ll np, int F, float *mesh_out, cudaStream_t st);
+void launch_flip(const Geo &g, Work &w, ll np, int F, float *mesh_out, float *node_vol, cudaStream_t st);
+void launch_rhs(const Geo &g, Work &w, ll np, int F, cudaStream_t st);
+void launch_rhs_to_float(const Geo &g, Work &w, int F, float *b_out, cudaStream_t st);
+void launch_mass_apply(const Geo &g, const float *x, int F, float *y, cudaStream_t st);
+int launch_cg(const Geo &g, Work &w, int F, const float *b_float, bool b_from_fix, float *x, bool x_has_start,
+              double rtol, int max_iter, cudaStream_t st);
+void launch_scatter_sorted(ll np, const int *perm, const float *src, float *dst, cudaStream_t st);
+void launch_export_tris(const Geo &g, Work &w, ll np, int *tri, int *off, ll max_tri, cudaStream_t st);
+void launch_psum(const Geo &g, Work &w, ll np, int F, cudaStream_t st);

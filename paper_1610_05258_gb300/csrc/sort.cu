@@ -1,0 +1,173 @@
+// Counting sort of particles by mesh cell.
+//
+// The particles of one cell end up contiguous ("particles around node",
+// Sec. 2.3), which every scatter and the triangulation rely on. Order inside a
+// cell is canonical: by caller index in 2D, by (torus coordinate, caller
+// index) in 1D, so that the sorted array is the periodic particle order that
+// defines the 1D hat functions (Sec. 3.1). Arrival slots are taken with
+// integer atomics (order-free), then every cell segment is put in canonical
+// order, so the result is deterministic.
+#include "internal.cuh"
+
+namespace {
+
+__global__ void k_key(Geo g, const float *__restrict__ px, const float *__restrict__ py, ll np,
+                      uint2 *__restrict__ fx, int *__restrict__ key, int *__restrict__ slot, int *__restrict__ count,
+                      int *__restrict__ status) {
+    ll k = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= np) return;
+    float x = px[k];
+    float y = g.dim == 2 ? py[k] : 0.0f;
+    if (!isfinite(x) || !isfinite(y)) {
+        atomicOr(status, ST_NONFINITE);
+        x = 0.0f;
+        y = 0.0f;
+    }
+    uint32_t X = torus_coord(x, g.invL);
+    uint32_t Y = g.dim == 2 ? torus_coord(y, g.invL) : 0u;
+    int c = cell_of(X, g.n);
+    if (g.dim == 2) c += cell_of(Y, g.n) * g.n;
+    fx[k] = make_uint2(X, Y);
+    key[k] = c;
+    slot[k] = atomicAdd(&count[c], 1);
+}
+
+// Block-wide exclusive scan of 4 values per thread (1024 threads).
+__device__ int block_scan4(int v[4], int *sh) {
+    int t = v[0] + v[1] + v[2] + v[3];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int inc = t;
+    for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    if (lane == 31) sh[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int w = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+        int wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += u;
+        }
+        sh[lane] = wi - w;       // exclusive warp offsets
+        if (lane == 31) sh[32] = wi;  // block total
+    }
+    __syncthreads();
+    int base = sh[wid] + inc - t;
+    int run = base;
+    for (int i = 0; i < 4; ++i) {
+        int x = v[i];
+        v[i] = run;
+        run += x;
+    }
+    int total = sh[32];
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_local(const int *__restrict__ in, ll m, int *__restrict__ out,
+                                                     int *__restrict__ bsum) {
+    __shared__ int sh[33];
+    ll base = (ll)blockIdx.x * 4096 + threadIdx.x * 4;
+    int v[4];
+    for (int i = 0; i < 4; ++i) v[i] = base + i < m ? in[base + i] : 0;
+    int tot = block_scan4(v, sh);
+    for (int i = 0; i < 4; ++i)
+        if (base + i < m) out[base + i] = v[i];
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(int *__restrict__ bsum, int nb, int *__restrict__ total_out) {
+    __shared__ int sh[33];
+    int carry = 0;
+    for (int c0 = 0; c0 < nb; c0 += 4096) {
+        int v[4];
+        int base = c0 + threadIdx.x * 4;
+        for (int i = 0; i < 4; ++i) v[i] = base + i < nb ? bsum[base + i] : 0;
+        int tot = block_scan4(v, sh);
+        for (int i = 0; i < 4; ++i)
+            if (base + i < nb) bsum[base + i] = v[i] + carry;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void k_scan_add(int *__restrict__ out, ll m, const int *__restrict__ bsum) {
+    ll i = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) out[i] += bsum[i / 4096];
+}
+
+__global__ void k_place(ll np, const int *__restrict__ key, const int *__restrict__ slot,
+                        const int *__restrict__ cell_start, int *__restrict__ tmp) {
+    ll k = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= np) return;
+    tmp[cell_start[key[k]] + slot[k]] = (int)k;
+}
+
+// One thread per cell: canonical order inside the cell, then gather the
+// particle records into sorted order and track max |A| per field.
+__global__ void k_canon(Geo g, ll np, const int *__restrict__ cell_start, int *__restrict__ tmp,
+                        const uint2 *__restrict__ fx, const float *__restrict__ vals, int F, int *__restrict__ perm,
+                        uint2 *__restrict__ pos, float *__restrict__ vals_s, unsigned *__restrict__ maxabs,
+                        int *__restrict__ status) {
+    ll c = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    float mx[PM_MAXF];
+    for (int f = 0; f < PM_MAXF; ++f) mx[f] = 0.0f;
+    bool bad = false;
+    if (c < g.ncell) {
+        int s0 = cell_start[c], s1 = cell_start[c + 1];
+        for (int i = s0 + 1; i < s1; ++i) {
+            int v = tmp[i];
+            uint32_t xv = g.dim == 1 ? fx[v].x : 0u;
+            int j = i - 1;
+            while (j >= s0) {
+                int u = tmp[j];
+                bool greater;
+                if (g.dim == 1) {
+                    uint32_t xu = fx[u].x;
+                    greater = xu > xv || (xu == xv && u > v);
+                } else {
+                    greater = u > v;
+                }
+                if (!greater) break;
+                tmp[j + 1] = u;
+                --j;
+            }
+            tmp[j + 1] = v;
+        }
+        for (int s = s0; s < s1; ++s) {
+            int idx = tmp[s];
+            perm[s] = idx;
+            pos[s] = fx[idx];
+            for (int f = 0; f < F; ++f) {
+                float a = vals[(ll)f * np + idx];
+                if (!isfinite(a)) bad = true;
+                vals_s[(ll)f * np + s] = a;
+                mx[f] = fmaxf(mx[f], fabsf(a));
+            }
+        }
+    }
+    if (bad) atomicOr(status, ST_NONFINITE);
+    for (int f = 0; f < F; ++f) {
+        float m = mx[f];
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(&maxabs[f], __float_as_uint(m));
+    }
+}
+
+}  // namespace
+
+void launch_sort(const Geo &g, Work &w, const float *px, const float *py, ll np, const float *vals, int F,
+                 cudaStream_t st) {
+    cudaMemsetAsync(w.count, 0, sizeof(int) * g.ncell, st);
+    cudaMemsetAsync(w.maxabs, 0, sizeof(unsigned) * PM_MAXF, st);
+    if (np > 0) k_key<<<div_up(np, 256), 256, 0, st>>>(g, px, py, np, w.fx, w.key, w.slot, w.count, w.status);
+    int nb = div_up(g.ncell, 4096);
+    k_scan_local<<<nb, 1024, 0, st>>>(w.count, g.ncell, w.cell_start, w.scan_tmp);
+    k_scan_top<<<1, 1024, 0, st>>>(w.scan_tmp, nb, w.cell_start + g.ncell);
+    k_scan_add<<<div_up(g.ncell, 256), 256, 0, st>>>(w.cell_start, g.ncell, w.scan_tmp);
+    if (np > 0) k_place<<<div_up(np, 256), 256, 0, st>>>(np, w.key, w.slot, w.cell_start, w.tmp);
+    k_canon<<<div_up(g.ncell, 128), 128, 0, st>>>(g, np, w.cell_start, w.tmp, w.fx, vals, vals ? F : 0, w.perm,
+                                                   w.pos, w.vals, w.maxabs, w.status);
+}

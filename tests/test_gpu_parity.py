@@ -1,0 +1,238 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element,
+on the same seeded inputs. Tolerance: relative L2 <= 1e-5 for floating point
+results; bit-exact for the sort, the cell table and the triangulation."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1610_05258_gb300 import workloads as W
+from gpu_util import canon_tris, rel_l2, to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def ctx_for(inst, F=None, extra=0):
+    from paper_1610_05258_gb300 import Context
+    return Context(inst.dim, inst.n, inst.L, inst.np + extra, F or inst.F)
+
+
+def dev(inst):
+    px, py, vals = to_dev(torch, inst.px, inst.py, inst.vals)
+    return px, py, vals
+
+
+CASES_2D = [
+    ("uniform_n40_ppc4", lambda: W.uniform_instance(40, 4, F=2, seed=101)),
+    ("uniform_n37_ppc1", lambda: W.uniform_instance(37, 1, F=1, seed=102)),
+    ("uniform_n64_ppc7", lambda: W.uniform_instance(64, 7, F=3, seed=103)),
+    ("zalesak_n48", lambda: W.zalesak(48, seed=104)),
+    ("taylor_green_n33", lambda: W.taylor_green(33, 4, seed=105)),
+]
+CASES_1D = [
+    ("tophat_128", lambda: W.tophat_1d(128, 128, seed=16101)),
+    ("tophat_ragged", lambda: W.tophat_1d(203, 517, seed=7)),
+    ("tophat_sparse", lambda: W.tophat_1d(300, 40, seed=8)),
+]
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_1610_05258_gb300 import build
+    build.build()
+    return True
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name,mk", CASES_2D + CASES_1D)
+def test_sort_exact(built, name, mk):
+    inst = mk()
+    c = ctx_for(inst)
+    px, py, _ = dev(inst)
+    perm, cs = c.sort(px, py)
+    perm, cs = perm.cpu().numpy(), cs.cpu().numpy()
+    if inst.dim == 2:
+        want_perm, want_cs = oracle.sort_by_cell(2, inst.n, inst.L, inst.px, inst.py)
+    else:
+        X = oracle.fixed_coords(inst.px, inst.L).astype(np.int64)
+        cell = (X * inst.n) >> 32
+        want_perm = np.lexsort((np.arange(inst.np), X, cell))
+        want_cs = np.concatenate([[0], np.cumsum(np.bincount(cell, minlength=inst.n))])
+    np.testing.assert_array_equal(perm, want_perm)
+    np.testing.assert_array_equal(cs, want_cs)
+
+
+@pytest.mark.parametrize("dim,n,npart,F", [(2, 50, 20011, 3), (2, 7, 333, 1), (1, 129, 5003, 2), (2, 256, 70000, 2)])
+def test_interpolate(built, dim, n, npart, F):
+    from paper_1610_05258_gb300 import Context
+    g = np.random.default_rng(dim * 1000 + n)
+    L = 2.0 * math.pi
+    px = g.uniform(-L, 2 * L, npart).astype(np.float32)
+    py = g.uniform(-L, 2 * L, npart).astype(np.float32)
+    mesh = g.standard_normal((F, n ** dim))
+    c = Context(dim, n, L, npart, F)
+    dpx, dpy, dmesh = to_dev(torch, px, py if dim == 2 else None, mesh)
+    got = c.interpolate(dmesh, dpx, dpy).cpu().numpy()
+    want = oracle.interpolate(dim, n, L, mesh, px, py)
+    assert rel_l2(got, want) <= TOL
+    assert np.abs(got - want).max() <= 1e-5 * np.abs(mesh).max()
+
+
+def test_interpolate_empty(built):
+    from paper_1610_05258_gb300 import Context
+    c = Context(2, 16, 1.0, 10, 1)
+    z = torch.zeros(0, dtype=torch.float32, device="cuda")
+    out = c.interpolate(torch.ones(256, device="cuda"), z, z)
+    assert out.shape == (1, 0)
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name,mk", CASES_2D)
+def test_triangulation_exact(built, name, mk):
+    inst = mk()
+    c = ctx_for(inst)
+    px, py, _ = dev(inst)
+    tri, off = c.triangulate(px, py)
+    got = canon_tris(tri.cpu().numpy(), off.cpu().numpy())
+    t, o, _ = oracle.triangulate(inst.L, inst.px, inst.py)
+    assert len(got) == 2 * inst.np
+    assert got == canon_tris(t, o)
+
+
+def test_triangulation_degenerate_lattice(built):
+    """Perfect lattice (every cell's corners cocircular): the symbolic
+    perturbation must pick the same diagonals as the oracle."""
+    from paper_1610_05258_gb300 import Context
+    m = 64
+    i = (np.arange(m) + 0.5) / m
+    xx, yy = np.meshgrid(i, i, indexing="xy")
+    px, py = xx.ravel().astype(np.float32), yy.ravel().astype(np.float32)
+    c = Context(2, 32, 1.0, px.size, 1)
+    dpx, dpy = to_dev(torch, px, py)
+    tri, off = c.triangulate(dpx, dpy)
+    t, o, _ = oracle.triangulate(1.0, px, py)
+    assert canon_tris(tri.cpu().numpy(), off.cpu().numpy()) == canon_tris(t, o)
+
+
+@pytest.mark.parametrize("name,mk", CASES_2D[:3] + CASES_1D)
+def test_particle_volumes(built, name, mk):
+    inst = mk()
+    c = ctx_for(inst)
+    px, py, _ = dev(inst)
+    got = c.particle_volumes(px, py).cpu().numpy()
+    want = oracle.particle_volumes(inst.dim, inst.L, inst.px, inst.py)
+    assert rel_l2(got, want) <= TOL
+    assert got.astype(np.float64).sum() == pytest.approx(inst.L ** inst.dim, rel=1e-5)
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name,mk", CASES_2D + CASES_1D)
+def test_delta(built, name, mk):
+    inst = mk()
+    c = ctx_for(inst)
+    px, py, vals = dev(inst)
+    got = c.assign_delta(px, py, vals).cpu().numpy()
+    want = oracle.delta(inst.dim, inst.n, inst.L, inst.px, inst.py, inst.vals)
+    assert rel_l2(got, want) <= TOL
+
+
+@pytest.mark.parametrize("name,mk", CASES_2D + CASES_1D)
+def test_flip(built, name, mk):
+    inst = mk()
+    c = ctx_for(inst)
+    px, py, vals = dev(inst)
+    vol = torch.empty(inst.n ** inst.dim, device="cuda")
+    got, empty = c.assign_flip(px, py, vals, node_volume=vol, count_empty=True)
+    want, wvol, wempty = oracle.flip(inst.dim, inst.n, inst.L, inst.px, inst.py, inst.vals)
+    assert rel_l2(got.cpu().numpy(), want) <= TOL
+    assert rel_l2(vol.cpu().numpy(), wvol) <= TOL
+    assert empty == wempty
+
+
+@pytest.mark.parametrize("name,mk", CASES_2D + CASES_1D)
+def test_mass_rhs(built, name, mk):
+    inst = mk()
+    c = ctx_for(inst)
+    px, py, vals = dev(inst)
+    got = c.mass_rhs(px, py, vals).cpu().numpy()
+    want = oracle.rhs(inst.dim, inst.n, inst.L, inst.px, inst.py, inst.vals)
+    for f in range(inst.F):
+        assert rel_l2(got[f], want[f]) <= TOL
+
+
+@pytest.mark.parametrize("dim,n,F", [(1, 64, 2), (1, 1001, 1), (2, 48, 3), (2, 301, 1)])
+def test_mass_apply_and_solve(built, dim, n, F):
+    from paper_1610_05258_gb300 import Context
+    L = 1.3
+    b = W.mesh_field(dim, n, L, F=F, seed=n, kind="noise")
+    c = Context(dim, n, L, 16, F)
+    (db,) = to_dev(torch, b)
+    y = c.mass_apply(db).cpu().numpy()
+    assert rel_l2(y, oracle.mass_apply(dim, n, L, b)) <= 1e-6
+    x, info = c.mass_solve(db, rtol=1e-6)
+    want = oracle.mass_solve(dim, n, L, b)
+    for f in range(F):
+        assert rel_l2(x.cpu().numpy()[f], want[f]) <= TOL
+        assert info[f].rel_resid <= 1e-6
+        kappa = 3.0 if dim == 1 else 9.0
+        rate = (math.sqrt(kappa) - 1) / (math.sqrt(kappa) + 1)
+        assert info[f].iters <= math.ceil(math.log(2 * math.sqrt(kappa) / 1e-6) / math.log(1 / rate)) + 3
+
+
+@pytest.mark.parametrize("name,mk", CASES_2D + CASES_1D)
+@pytest.mark.parametrize("warm", ["delta", "zero"])
+def test_assign_mass(built, name, mk, warm):
+    inst = mk()
+    c = ctx_for(inst)
+    px, py, vals = dev(inst)
+    got, info = c.assign_mass(px, py, vals, warm_start=warm, rtol=1e-6)
+    want = oracle.assign_mass(inst.dim, inst.n, inst.L, inst.px, inst.py, inst.vals)
+    got = got.cpu().numpy()
+    for f in range(inst.F):
+        assert rel_l2(got[f], want[f]) <= TOL, (f, rel_l2(got[f], want[f]))
+        assert info[f].rel_resid <= 1e-6
+        assert info[f].cons_err <= 1e-6
+    v = oracle.particle_volumes(inst.dim, inst.L, inst.px, inst.py)
+    for f in range(inst.F):
+        assert info[f].sum_particles == pytest.approx(float((v * inst.vals[f]).sum()), rel=1e-5, abs=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# errors are reported, never faults
+# ---------------------------------------------------------------------------
+def test_invalid_arguments(built):
+    from paper_1610_05258_gb300 import Context, PMError
+    with pytest.raises(PMError):
+        Context(3, 16, 1.0, 10, 1)
+    c = Context(2, 16, 1.0, 100, 1)
+    px, py, vals = to_dev(torch, np.zeros(200), np.zeros(200), np.zeros(200))
+    with pytest.raises(PMError) as e:
+        c.assign_delta(px, py, vals)
+    assert e.value.status == 1
+
+
+def test_nonfinite_and_coincident_positions(built):
+    from paper_1610_05258_gb300 import Context, PMError
+    inst = W.uniform_instance(16, 4, F=1, seed=3)
+    c = ctx_for(inst)
+    x = inst.px.copy()
+    x[5] = np.nan
+    px, py, vals = to_dev(torch, x, inst.py, inst.vals)
+    with pytest.raises(PMError) as e:
+        c.assign_mass(px, py, vals)
+    assert e.value.status == 5
+    x = inst.px.copy()
+    y = inst.py.copy()
+    x[7], y[7] = x[3], y[3]
+    px, py, vals = to_dev(torch, x, y, inst.vals)
+    with pytest.raises(PMError) as e:
+        c.assign_mass(px, py, vals)
+    assert e.value.status == 5
+    # the context stays usable afterwards
+    px, py, vals = dev(inst)
+    out, info = c.assign_mass(px, py, vals)
+    assert info[0].rel_resid <= 1e-6

@@ -21,17 +21,25 @@ TWO32 = 2 ** 32
 # fixed-point positions
 # --------------------------------------------------------------------------
 def test_fixed_coords_definition():
-    """X = floor(frac(x/L) 2^32), checked with exact rationals."""
+    """X = floor(frac(fl32(x fl32(1/L))) 2^32): bit-exact against numpy's IEEE
+    single-precision arithmetic, and within a few float ulps of the exact
+    rational frac(x/L) 2^32."""
     g = np.random.default_rng(1)
     L = 2 * math.pi
-    x = np.concatenate([g.uniform(-20, 20, 500), [0.0, -0.0, L, -L, 1e-30, -1e-30, 3 * L]]).astype(np.float32)
+    x = np.concatenate([g.uniform(-20, 20, 500), [0.0, -0.0, L, -L, 1e-30, -1e-30, 3 * L, 1e-7, -1e-7]]).astype(np.float32)
     X = oracle.fixed_coords(x, L)
+    invL = np.float32(1.0 / L)
+    t = (x * invL).astype(np.float32)
+    f = (t - np.floor(t)).astype(np.float32)
+    f = np.where(f >= np.float32(1.0), np.float32(0.0), f)
+    want = (f.astype(np.float64) * TWO32).astype(np.uint64).astype(np.uint32)
+    np.testing.assert_array_equal(X, want)
     for xi, Xi in zip(x.astype(np.float64), X):
-        t = Fraction(float(xi)) / Fraction(L)
-        fr = t - math.floor(t)
-        want = math.floor(fr * TWO32) % TWO32
-        # the oracle rounds x/L once in double; allow that single rounding
-        assert abs(int(Xi) - want) <= 2 or abs(abs(int(Xi) - want) - TWO32) <= 2
+        exact = Fraction(float(xi)) / Fraction(L)
+        ex = (exact - math.floor(exact)) * TWO32
+        d = abs(float(ex) - int(Xi))
+        d = min(d, TWO32 - d)
+        assert d <= 2 ** 9 * (1 + abs(float(xi)) / L) + 1  # a few ulps of t
 
 
 # --------------------------------------------------------------------------
