@@ -1,0 +1,343 @@
+"""Benchmark of the particle <-> mesh transfer hot path on GB300.
+
+One step = one time step of the Taylor-Green experiment (Sec. 3.3) on a
+1024^2 periodic bilinear mesh with 4 uniform random particles per cell
+(4,194,304 particles) and F = 2 fields (u, v):
+    G2P   Abb = sum_i Ab_i psi_i(r)           (pm_interpolate, Eq. delta2)
+    move  midpoint rule with the mesh velocity, viscous decay of the values
+          (pm_advect_rk2)
+    P2G   mass assignment to 1e-6 relative residual (pm_assign_mass: cell sort,
+          periodic Delaunay stars, exact right-hand side, delta warm start,
+          CG on the mass matrix, Eqs. proj and phi_def)
+Metric: particles * fields / s of the whole step. Device-resident inputs;
+the L2 cache (129 MB) is flushed by writing a 512 MB buffer before every timed
+step, and each step is timed with CUDA events on the launching stream.
+
+--impl reference times the FP64 CPU oracle (single thread) on a bounded
+sample of the same workload (a 32^2 Taylor-Green box, 4 particles per cell).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "mass-assignment particles*fields/s at 1e-6 residual (plain CG, delta warm start); % HBM peak"
+UNIT = "particle-fields/s"
+NU = 0.01
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+
+def workload(args):
+    from paper_1610_05258_gb300 import workloads as W
+    if args.workload == "taylor_green":
+        inst = W.taylor_green(args.n, 4, seed=16103 + args.rank)
+    elif args.workload == "mixture":
+        inst = W.mixture(args.n, 4, F=4, seed=16105 + args.rank)
+    else:
+        raise SystemExit(f"unknown workload {args.workload}")
+    return inst
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.p = None
+        self.path = os.path.join("/tmp", f"pm_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(seconds_hint=10.0):
+    """The FP64 oracle as it stands (single-threaded C) on a bounded sample:
+    Taylor-Green 32^2 box, 4 particles per cell, F = 2: G2P + mass assignment."""
+    import numpy as np
+
+    import oracle
+    from paper_1610_05258_gb300 import workloads as W
+
+    inst = W.taylor_green(32, 4, seed=16103)
+    mesh = oracle.assign_mass(2, inst.n, inst.L, inst.px, inst.py, inst.vals)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        vel = oracle.interpolate(2, inst.n, inst.L, mesh, inst.px, inst.py)
+        mesh = oracle.assign_mass(2, inst.n, inst.L, inst.px, inst.py, vel * math.exp(-2 * NU * 1e-3))
+        reps += 1
+        if time.perf_counter() - t0 > seconds_hint:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": inst.np * inst.F / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"taylor_green 32^2, {inst.np} particles, F=2, {reps} steps of G2P + mass assignment "
+                      f"(FP64, single thread), {dt * 1e3:.1f} ms/step"}
+
+
+def run_reference(args):
+    import numpy as np
+
+    import oracle
+    from paper_1610_05258_gb300 import workloads as W
+
+    if args.world > 1 and args.rank != 0:
+        return
+    inst = W.taylor_green(32, 4, seed=16103)
+    mesh = oracle.assign_mass(2, inst.n, inst.L, inst.px, inst.py, inst.vals)
+    px, py = inst.px.copy(), inst.py.copy()
+    dt = 0.5 * (inst.L / inst.n)
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        vel = oracle.interpolate(2, inst.n, inst.L, mesh, px, py)
+        # midpoint rule with the oracle's G2P
+        xm = np.mod(px + 0.5 * dt * vel[0], inst.L).astype(np.float32)
+        ym = np.mod(py + 0.5 * dt * vel[1], inst.L).astype(np.float32)
+        vm = oracle.interpolate(2, inst.n, inst.L, mesh, xm, ym)
+        px = np.mod(px + dt * vm[0], inst.L).astype(np.float32)
+        py = np.mod(py + dt * vm[1], inst.L).astype(np.float32)
+        mesh = oracle.assign_mass(2, inst.n, inst.L, px, py, vel * math.exp(-2 * NU * dt))
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    v = inst.np * inst.F / t
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "taylor_green_32x32_ppc4_F2 (bounded CPU sample of taylor_green_1024x1024_ppc4_F2)",
+                   "particles": inst.np, "fields": inst.F, "mesh": f"{inst.n}x{inst.n}"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"taylor_green 32^2, {inst.np} particles, F=2, G2P + midpoint move + mass "
+                                   f"assignment per step, FP64 single thread"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="taylor_green", choices=["taylor_green", "mixture"])
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.rank = int(os.environ.get("RANK", "0"))
+    args.world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_1610_05258_gb300 as pm
+    from paper_1610_05258_gb300 import build
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if args.world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    pm.load_library()
+
+    inst = workload(args)
+    n, L, F, N = inst.n, inst.L, inst.F, inst.np
+    h = L / n
+    dt = 0.5 * h / 1.0  # Courant number 0.5 for u0 = 1 (Sec. 3.3)
+    decay = math.exp(-2.0 * NU * dt)
+    dev = torch.device("cuda", local)
+    ctx = pm.Context(2, n, L, N, F, device=dev)
+    px0 = torch.from_numpy(inst.px).to(dev)
+    py0 = torch.from_numpy(inst.py).to(dev)
+    vals0 = torch.from_numpy(inst.vals).to(dev)
+    px, py = px0.clone(), py0.clone()
+    vel = torch.empty(F, N, device=dev)
+    mesh, _ = ctx.assign_mass(px, py, vals0)
+    mesh2 = torch.empty_like(mesh)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(m_in, m_out):
+        ctx.interpolate(m_in, px, py, out=vel)
+        ctx.advect_rk2(m_in, vel, px, py, dt, vals=vel, factor=decay)
+        ctx.assign_mass(px, py, vel, out=m_out, info=False)
+
+    for _ in range(args.warmup):
+        step(mesh, mesh2)
+        mesh, mesh2 = mesh2, mesh
+    torch.cuda.synchronize()
+    ctx.sync()
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = pm.kernel_launches()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        step(mesh, mesh2)
+        ev[k][1].record(stream)
+        mesh, mesh2 = mesh2, mesh
+    torch.cuda.synchronize()
+    launches = pm.kernel_launches() - launches0
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    t_step = sum(ms) / len(ms)
+    prof = ctx.profile_read(reset=True)
+    ctx.profile(False)
+    # accuracy of the last step: solve report
+    _, info = ctx.assign_mass(px, py, vel, out=mesh2)
+    if dist:
+        t = torch.tensor([t_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+
+    # ---- end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hpx = px0.cpu().pin_memory()
+        hpy = py0.cpu().pin_memory()
+        hmesh = mesh.cpu().pin_memory()
+        hout = torch.empty_like(hmesh).pin_memory()
+        dpx, dpy, dmesh = torch.empty_like(px), torch.empty_like(py), torch.empty_like(mesh)
+        bi = hpx.numel() * 4 + hpy.numel() * 4 + hmesh.numel() * 4
+        bo = hout.numel() * 4
+        e2e_ms = []
+        for k in range(args.warmup + args.steps):
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dpx.copy_(hpx, non_blocking=True)
+            dpy.copy_(hpy, non_blocking=True)
+            dmesh.copy_(hmesh, non_blocking=True)
+            ctx.interpolate(dmesh, dpx, dpy, out=vel)
+            ctx.advect_rk2(dmesh, vel, dpx, dpy, dt, vals=vel, factor=decay)
+            ctx.assign_mass(dpx, dpy, vel, out=mesh2, info=False)
+            hout.copy_(mesh2, non_blocking=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                e2e_ms.append(a.elapsed_time(b))
+        te = sum(e2e_ms) / len(e2e_ms)
+        e2e = {"value": args.world * N * F / (te * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi,
+               "d2h_bytes_per_step": bo, "ms_per_step": te}
+
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    # dominant phase and its roofline (algorithmic bytes per launch: see the design doc)
+    phase_ms = {k: v[0] / max(1, args.steps) for k, v in prof.items()}
+    dom = max(phase_ms, key=phase_ms.get)
+    nn = n * n
+    alg = {
+        # minimal traffic of each phase per launch (bytes)
+        "sort": N * (8 + 4 + 4 + 4 + 4 + 4 + 8 + 4 * F + 4 * F + 4) + nn * 4 * 3,
+        "triangulate": N * (8 + 4 + 4 * 6 + 1 + 4),
+        "rhs": N * (8 + 4 * F + 4 * 6 + 1 + 4) + nn * 8 * F,
+        "delta": N * (8 + 4 * F + 4 * 6 + 1) + nn * 4 * F,
+        "solve": nn * 4 * F * 3,
+        "g2p": N * (8 + 4 * F) + nn * 4 * F,
+        "advect": N * (16 + 8 * F) + nn * 4 * F,
+    }
+    dom_bytes = alg.get(dom, 0)
+    achieved = dom_bytes / (phase_ms[dom] * 1e-3) / 1e9 if phase_ms[dom] > 0 else 0.0
+    roof = {"kernel_phase": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "peak_source": "measured" if "fallback" not in peaks else "fallback"}
+
+    cpu = None
+    if args.rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(10.0)
+
+    value = args.world * N * F / (t_step * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{inst.name}: {N} particles (4 per cell, uniform random), F={F} (u, v), "
+                               f"mesh {n}x{n} periodic bilinear, L=2pi, step = G2P + midpoint move + mass "
+                               f"assignment (rtol 1e-6, delta warm start)",
+                   "l2": "flushed before every timed step (512 MB write)", "parallelism": f"replicas x{args.world}"},
+        "phase_ms_per_step": {k: round(v, 4) for k, v in phase_ms.items() if v > 0},
+        "solve": {"iters": [i.iters for i in info], "rel_resid": [i.rel_resid for i in info],
+                  "cons_err": [i.cons_err for i in info], "init_rel_resid": [i.init_rel_resid for i in info]},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": ck,
+    }
+    if args.rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -164,6 +164,48 @@ pm_status pm_triangulate(pm_ctx *ctx, const float *px, const float *py, long lon
  * Asynchronous. */
 pm_status pm_sort(pm_ctx *ctx, const float *px, const float *py, long long np, int *perm_out, int *cell_start_out);
 
+/* ---------------------------------------------------------------------------
+ * Particle advection: the driver step between mesh->particle and
+ * particle->mesh in the paper's experiments (Sec. 3.1 dx/dt = u, Sec. 3.2
+ * rigid rotation, Sec. 3.3 motion with the interpolated velocity). Positions
+ * are updated in place and wrapped into [0, L). Asynchronous.
+ * ------------------------------------------------------------------------- */
+/* x += dx (and y += dy in 2D). */
+pm_status pm_advect_shift(pm_ctx *ctx, float *px, float *py, long long np, double dx, double dy);
+/* Rotate every particle about (cx, cy) by `angle` radians (2D only). */
+pm_status pm_advect_rotate(pm_ctx *ctx, float *px, float *py, long long np, double cx, double cy, double angle);
+/* Explicit midpoint step  r += dt u(r + dt/2 vel)  with u interpolated from
+ * the mesh velocity mesh_vel [dim][n^dim] (Eq. delta2) and vel [dim][np] the
+ * particle velocity at the current position; vals [F][np] (may be NULL) are
+ * multiplied by `factor` in the same pass. */
+pm_status pm_advect_rk2(pm_ctx *ctx, const float *mesh_vel, const float *vel, float *px, float *py, long long np,
+                        double dt, float *vals, int F, double factor);
+
+/* ---------------------------------------------------------------------------
+ * Instrumentation (no counterpart in the paper).
+ * ------------------------------------------------------------------------- */
+enum {
+    PM_PH_SORT = 0,
+    PM_PH_TRIANGULATE = 1, /* particle functions: Delaunay stars (2D) or 1D order, volumes */
+    PM_PH_DELTA = 2,
+    PM_PH_FLIP = 3,
+    PM_PH_RHS = 4,
+    PM_PH_SOLVE = 5,
+    PM_PH_G2P = 6,
+    PM_PH_ADVECT = 7,
+    PM_PH_OTHER = 8,
+    PM_NPHASE = 9
+};
+/* When enabled, every phase's kernels are bracketed by CUDA events recorded
+ * on the context's stream; pm_profile_read() waits for the stream and returns
+ * the accumulated milliseconds and call counts per phase (arrays of
+ * PM_NPHASE, either may be NULL), resetting them if `reset`. */
+pm_status pm_profile(pm_ctx *ctx, int enable);
+pm_status pm_profile_read(pm_ctx *ctx, double *ms, long long *calls, int reset);
+const char *pm_phase_name(int phase);
+/* Number of kernels this library has launched in the process so far. */
+long long pm_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

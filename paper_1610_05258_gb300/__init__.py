@@ -12,7 +12,7 @@ import ctypes
 import os
 from dataclasses import dataclass
 
-__all__ = ["Context", "PMError", "SolveInfo", "load_library", "library_path"]
+__all__ = ["Context", "PMError", "SolveInfo", "load_library", "library_path", "kernel_launches"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBPATH = os.path.join(_HERE, "_build", "libpmt.so")
@@ -25,8 +25,10 @@ _STATUS = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ENOTCONV", 4: "PM_
 EXPORTS = [
     "pm_ctx_create", "pm_ctx_destroy", "pm_ctx_set_stream", "pm_sync", "pm_last_error", "pm_ctx_workspace_bytes",
     "pm_interpolate", "pm_assign_delta", "pm_assign_flip", "pm_assign_mass", "pm_mass_rhs", "pm_mass_apply",
-    "pm_mass_solve", "pm_particle_volumes", "pm_triangulate", "pm_sort",
+    "pm_mass_solve", "pm_particle_volumes", "pm_triangulate", "pm_sort", "pm_advect_shift", "pm_advect_rotate",
+    "pm_advect_rk2", "pm_profile", "pm_profile_read", "pm_phase_name", "pm_kernel_launches",
 ]
+PHASES = ["sort", "triangulate", "delta", "flip", "rhs", "solve", "g2p", "advect", "other"]
 
 
 class PMError(RuntimeError):
@@ -86,16 +88,30 @@ def load_library(path: str | None = None):
         "pm_particle_volumes": [vp, vp, vp, ll, vp],
         "pm_triangulate": [vp, vp, vp, ll, vp, vp, ll, ctypes.POINTER(ll)],
         "pm_sort": [vp, vp, vp, ll, vp, vp],
+        "pm_advect_shift": [vp, vp, vp, ll, d, d],
+        "pm_advect_rotate": [vp, vp, vp, ll, d, d, d],
+        "pm_advect_rk2": [vp, vp, vp, vp, vp, ll, d, vp, i, d],
+        "pm_profile": [vp, i],
+        "pm_profile_read": [vp, vp, vp, i],
+        "pm_phase_name": [i],
+        "pm_kernel_launches": [],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = ctypes.c_int
     lib.pm_last_error.restype = ctypes.c_char_p
+    lib.pm_phase_name.restype = ctypes.c_char_p
+    lib.pm_kernel_launches.restype = ctypes.c_longlong
     lib.pm_ctx_workspace_bytes.restype = ctypes.c_longlong
     lib.pm_ctx_destroy.restype = None
     _lib = lib
     return lib
+
+
+def kernel_launches() -> int:
+    """Kernels this library has launched in the process so far."""
+    return load_library().pm_kernel_launches()
 
 
 def _ptr(t):
@@ -260,3 +276,32 @@ class Context:
         self._stream()
         self._check(self.lib.pm_sort(self.h, _ptr(px), _ptr(py), px.numel(), _ptr(perm), _ptr(cs)))
         return perm, cs
+
+    # ---------------------------------------------------------------- advection
+    def advect_shift(self, px, py, dx, dy=0.0):
+        px, py = self._f32(px), self._f32(py)
+        self._stream()
+        self._check(self.lib.pm_advect_shift(self.h, _ptr(px), _ptr(py), px.numel(), float(dx), float(dy)))
+
+    def advect_rotate(self, px, py, cx, cy, angle):
+        px, py = self._f32(px), self._f32(py)
+        self._stream()
+        self._check(self.lib.pm_advect_rotate(self.h, _ptr(px), _ptr(py), px.numel(), float(cx), float(cy),
+                                              float(angle)))
+
+    def advect_rk2(self, mesh_vel, vel, px, py, dt, vals=None, factor=1.0):
+        mesh_vel, vel, px, py, vals = (self._f32(t) for t in (mesh_vel, vel, px, py, vals))
+        F = vals.numel() // max(1, px.numel()) if vals is not None else 0
+        self._stream()
+        self._check(self.lib.pm_advect_rk2(self.h, _ptr(mesh_vel), _ptr(vel), _ptr(px), _ptr(py), px.numel(),
+                                           float(dt), _ptr(vals), F, float(factor)))
+
+    # ---------------------------------------------------------- instrumentation
+    def profile(self, enable=True):
+        self._check(self.lib.pm_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self, reset=True):
+        ms = (ctypes.c_double * len(PHASES))()
+        calls = (ctypes.c_longlong * len(PHASES))()
+        self._check(self.lib.pm_profile_read(self.h, ms, calls, 1 if reset else 0))
+        return {PHASES[k]: (ms[k], calls[k]) for k in range(len(PHASES))}

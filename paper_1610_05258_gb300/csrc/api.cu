@@ -1,11 +1,22 @@
 // C ABI (include/pmt.h): context, workspace and the entry points. Each entry
 // validates its arguments on the host, then queues the kernels of its path on
 // the context's stream.
+#include <atomic>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "internal.cuh"
+
+static std::atomic<long long> g_launch_total{0};
+void count_launches(int k) { g_launch_total += k; }
+
+struct PendingEvent {
+    cudaEvent_t a, b;
+    int ph;
+};
 
 struct pm_ctx {
     Geo g;
@@ -14,6 +25,12 @@ struct pm_ctx {
     std::string err;
     ll bytes;
     int dev;
+    // profiling: CUDA events around every phase, on the context's stream
+    bool prof = false;
+    std::vector<PendingEvent> ev;
+    size_t nev = 0;
+    double acc_ms[PM_NPHASE] = {0};
+    ll acc_calls[PM_NPHASE] = {0};
 };
 
 namespace {
@@ -61,6 +78,41 @@ pm_status wait_status(pm_ctx *c) {
     return map_status(c, s);
 }
 
+void resolve_events(pm_ctx *c) {
+    if (!c->nev) return;
+    cudaStreamSynchronize(c->st);
+    for (size_t k = 0; k < c->nev; ++k) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, c->ev[k].a, c->ev[k].b) == cudaSuccess) {
+            c->acc_ms[c->ev[k].ph] += ms;
+            c->acc_calls[c->ev[k].ph] += 1;
+        }
+    }
+    c->nev = 0;
+}
+
+// RAII phase marker: records a CUDA event pair around the phase's kernels.
+struct Phase {
+    pm_ctx *c;
+    size_t k;
+    Phase(pm_ctx *c_, int ph) : c(c_), k((size_t)-1) {
+        if (!c->prof) return;
+        if (c->nev == 256) resolve_events(c);
+        if (c->nev == c->ev.size()) {
+            PendingEvent e;
+            cudaEventCreate(&e.a);
+            cudaEventCreate(&e.b);
+            c->ev.push_back(e);
+        }
+        k = c->nev++;
+        c->ev[k].ph = ph;
+        cudaEventRecord(c->ev[k].a, c->st);
+    }
+    ~Phase() {
+        if (k != (size_t)-1) cudaEventRecord(c->ev[k].b, c->st);
+    }
+};
+
 pm_status check_launch(pm_ctx *c, const char *where) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, where);
@@ -79,8 +131,12 @@ pm_status check_particles(pm_ctx *c, const float *px, const float *py, ll np, in
 
 // Sort + particle functions: everything the assignments share.
 pm_status prepare(pm_ctx *c, const float *px, const float *py, ll np, const float *vals, int F, bool need_tri) {
-    launch_sort(c->g, c->w, px, py, np, vals, F, c->st);
+    {
+        Phase ph(c, PM_PH_SORT);
+        launch_sort(c->g, c->w, px, py, np, vals, F, c->st);
+    }
     if (need_tri) {
+        Phase ph(c, PM_PH_TRIANGULATE);
         if (c->g.dim == 2)
             launch_triangulate(c->g, c->w, np, c->st);
         else
@@ -155,6 +211,10 @@ void pm_ctx_destroy(pm_ctx *c) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (w.hstatus) cudaFreeHost(w.hstatus);
+    for (auto &e : c->ev) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
     delete c;
 }
 
@@ -179,7 +239,10 @@ pm_status pm_interpolate(pm_ctx *c, const float *mesh, int F, const float *px, c
     if (s) return s;
     if (F < 1 || F > c->w.F_max) return fail(c, PM_EINVAL, "field count out of range");
     if (np > 0 && (!mesh || !out)) return fail(c, PM_EINVAL, "null mesh or output array");
-    launch_g2p(c->g, mesh, F, px, py, np, out, c->w.status, c->st);
+    {
+        Phase ph(c, PM_PH_G2P);
+        launch_g2p(c->g, mesh, F, px, py, np, out, c->w.status, c->st);
+    }
     return check_launch(c, "pm_interpolate");
 }
 
@@ -189,7 +252,10 @@ pm_status pm_assign_delta(pm_ctx *c, const float *px, const float *py, long long
     if (s) return s;
     if (F < 1 || !mesh_out) return fail(c, PM_EINVAL, "null output or no field");
     if ((s = prepare(c, px, py, np, vals, F, c->g.dim == 2))) return s;
-    launch_delta(c->g, c->w, np, F, mesh_out, c->st);
+    {
+        Phase ph(c, PM_PH_DELTA);
+        launch_delta(c->g, c->w, np, F, mesh_out, c->st);
+    }
     return check_launch(c, "pm_assign_delta");
 }
 
@@ -199,7 +265,10 @@ pm_status pm_assign_flip(pm_ctx *c, const float *px, const float *py, long long 
     if (s) return s;
     if (F < 1 || !mesh_out) return fail(c, PM_EINVAL, "null output or no field");
     if ((s = prepare(c, px, py, np, vals, F, true))) return s;
-    launch_flip(c->g, c->w, np, F, mesh_out, node_volume_out, c->st);
+    {
+        Phase ph(c, PM_PH_FLIP);
+        launch_flip(c->g, c->w, np, F, mesh_out, node_volume_out, c->st);
+    }
     if ((s = check_launch(c, "pm_assign_flip"))) return s;
     if (empty_nodes) {
         int e = 0;
@@ -250,17 +319,25 @@ pm_status pm_assign_mass(pm_ctx *c, const float *px, const float *py, long long 
     default_opts(opts, o);
     if (o.warm_start == PM_WS_USER && !o.x0) return fail(c, PM_EINVAL, "PM_WS_USER without x0");
     if ((s = prepare(c, px, py, np, vals, F, true))) return s;
-    launch_psum(c->g, c->w, np, F, c->st);
-    launch_rhs(c->g, c->w, np, F, c->st);
+    {
+        Phase ph(c, PM_PH_RHS);
+        launch_psum(c->g, c->w, np, F, c->st);
+        launch_rhs(c->g, c->w, np, F, c->st);
+    }
     bool start = true;
-    if (o.warm_start == PM_WS_DELTA)
+    if (o.warm_start == PM_WS_DELTA) {
+        Phase ph(c, PM_PH_DELTA);
         launch_delta(c->g, c->w, np, F, mesh_out, c->st);
-    else if (o.warm_start == PM_WS_USER)
+    } else if (o.warm_start == PM_WS_USER)
         cudaMemcpyAsync(mesh_out, o.x0, sizeof(float) * F * c->g.ncell, cudaMemcpyDeviceToDevice, c->st);
     else
         start = false;
     if ((s = check_launch(c, "pm_assign_mass"))) return s;
-    int e = launch_cg(c->g, c->w, F, nullptr, true, mesh_out, start, o.rtol, o.max_iter, c->st);
+    int e;
+    {
+        Phase ph(c, PM_PH_SOLVE);
+        e = launch_cg(c->g, c->w, F, nullptr, true, mesh_out, start, o.rtol, o.max_iter, c->st);
+    }
     if (e) return cuda_fail(c, (cudaError_t)e, "pm_assign_mass solve launch");
     if (info) return fill_info(c, F, info);
     return PM_OK;
@@ -272,8 +349,11 @@ pm_status pm_mass_rhs(pm_ctx *c, const float *px, const float *py, long long np,
     if (s) return s;
     if (F < 1 || !b_out) return fail(c, PM_EINVAL, "null output or no field");
     if ((s = prepare(c, px, py, np, vals, F, true))) return s;
-    launch_rhs(c->g, c->w, np, F, c->st);
-    launch_rhs_to_float(c->g, c->w, F, b_out, c->st);
+    {
+        Phase ph(c, PM_PH_RHS);
+        launch_rhs(c->g, c->w, np, F, c->st);
+        launch_rhs_to_float(c->g, c->w, F, b_out, c->st);
+    }
     return check_launch(c, "pm_mass_rhs");
 }
 
@@ -296,7 +376,11 @@ pm_status pm_mass_solve(pm_ctx *c, const float *b, int F, float *x, const pm_sol
         if (o.x0 != x) cudaMemcpyAsync(x, o.x0, sizeof(float) * F * c->g.ncell, cudaMemcpyDeviceToDevice, c->st);
         start = true;
     }
-    int e = launch_cg(c->g, c->w, F, b, false, x, start, o.rtol, o.max_iter, c->st);
+    int e;
+    {
+        Phase ph(c, PM_PH_SOLVE);
+        e = launch_cg(c->g, c->w, F, b, false, x, start, o.rtol, o.max_iter, c->st);
+    }
     if (e) return cuda_fail(c, (cudaError_t)e, "pm_mass_solve launch");
     if (info) return fill_info(c, F, info);
     return PM_OK;
@@ -327,6 +411,69 @@ pm_status pm_triangulate(pm_ctx *c, const float *px, const float *py, long long 
     if (!s && cnt > max_tri) return fail(c, PM_EINVAL, "max_tri too small");
     return s;
 }
+
+pm_status pm_advect_shift(pm_ctx *c, float *px, float *py, long long np, double dx, double dy) {
+    pm_status s = check_particles(c, px, py, np, 0, nullptr, 0);
+    if (s) return s;
+    {
+        Phase ph(c, PM_PH_ADVECT);
+        launch_advect_shift(c->g, px, py, np, (float)dx, (float)dy, c->st);
+    }
+    return check_launch(c, "pm_advect_shift");
+}
+
+pm_status pm_advect_rotate(pm_ctx *c, float *px, float *py, long long np, double cx, double cy, double angle) {
+    pm_status s = check_particles(c, px, py, np, 0, nullptr, 0);
+    if (s) return s;
+    if (c->g.dim != 2) return fail(c, PM_EINVAL, "pm_advect_rotate needs dim == 2");
+    {
+        Phase ph(c, PM_PH_ADVECT);
+        launch_advect_rotate(c->g, px, py, np, (float)cx, (float)cy, (float)cos(angle), (float)sin(angle), c->st);
+    }
+    return check_launch(c, "pm_advect_rotate");
+}
+
+pm_status pm_advect_rk2(pm_ctx *c, const float *mesh_vel, const float *vel, float *px, float *py, long long np,
+                        double dt, float *vals, int F, double factor) {
+    pm_status s = check_particles(c, px, py, np, F, vals, 0);
+    if (s) return s;
+    if (np > 0 && (!mesh_vel || !vel)) return fail(c, PM_EINVAL, "null velocity array");
+    {
+        Phase ph(c, PM_PH_ADVECT);
+        launch_advect_rk2(c->g, mesh_vel, vel, px, py, np, (float)dt, vals, vals ? F : 0, (float)factor,
+                          c->w.status, c->st);
+    }
+    return check_launch(c, "pm_advect_rk2");
+}
+
+pm_status pm_profile(pm_ctx *c, int enable) {
+    if (!c) return PM_EINVAL;
+    if (!enable) resolve_events(c);
+    c->prof = enable != 0;
+    return PM_OK;
+}
+
+pm_status pm_profile_read(pm_ctx *c, double *ms, long long *calls, int reset) {
+    if (!c) return PM_EINVAL;
+    resolve_events(c);
+    for (int k = 0; k < PM_NPHASE; ++k) {
+        if (ms) ms[k] = c->acc_ms[k];
+        if (calls) calls[k] = c->acc_calls[k];
+        if (reset) {
+            c->acc_ms[k] = 0.0;
+            c->acc_calls[k] = 0;
+        }
+    }
+    return PM_OK;
+}
+
+const char *pm_phase_name(int ph) {
+    static const char *names[PM_NPHASE] = {"sort", "triangulate", "delta", "flip", "rhs",
+                                           "solve", "g2p", "advect", "other"};
+    return ph >= 0 && ph < PM_NPHASE ? names[ph] : "?";
+}
+
+long long pm_kernel_launches(void) { return g_launch_total.load(); }
 
 pm_status pm_sort(pm_ctx *c, const float *px, const float *py, long long np, int *perm_out, int *cell_start_out) {
     pm_status s = check_particles(c, px, py, np, 0, nullptr, 0);

@@ -261,15 +261,20 @@ void launch_triangulate(const Geo &g, Work &w, ll np, cudaStream_t st) {
     float scale = (float)(u * u / 6.0);
     k_delaunay<<<div_up(np, 128), 128, 0, st>>>(g, np, w.pos, w.cell_start, w.perm, w.nbr, w.deg, w.vol, scale,
                                                  w.status);
+    count_launches(1);
 }
 
 void launch_volumes_1d(const Geo &g, Work &w, ll np, cudaStream_t st) {
     if (np <= 0) return;
     float scale = (float)(0.5 * g.L / 4294967296.0);
     k_vol1d<<<div_up(np, 256), 256, 0, st>>>(np, w.pos, w.vol, scale);
+    count_launches(1);
 }
 
 void launch_export_tris(const Geo &g, Work &w, ll np, int *tri, int *off, ll max_tri, cudaStream_t st) {
     cudaMemsetAsync(w.ntri, 0, sizeof(ll), st);
-    if (np > 0) k_export<<<div_up(np, 256), 256, 0, st>>>(np, w.pos, w.nbr, w.deg, w.perm, tri, off, max_tri, w.ntri);
+    if (np > 0) {
+        k_export<<<div_up(np, 256), 256, 0, st>>>(np, w.pos, w.nbr, w.deg, w.perm, tri, off, max_tri, w.ntri);
+        count_launches(1);
+    }
 }

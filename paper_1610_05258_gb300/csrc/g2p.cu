@@ -65,8 +65,12 @@ void launch_g2p(const Geo &g, const float *mesh, int F, const float *px, const f
         k_g2p<1><<<div_up(np, 256), 256, 0, st>>>(g, mesh, F, px, py, np, out, status);
     else
         k_g2p<2><<<div_up(np, 256), 256, 0, st>>>(g, mesh, F, px, py, np, out, status);
+    count_launches(1);
 }
 
 void launch_scatter_sorted(ll np, const int *perm, const float *src, float *dst, cudaStream_t st) {
-    if (np > 0) k_unsort<<<div_up(np, 256), 256, 0, st>>>(np, perm, src, dst);
+    if (np > 0) {
+        k_unsort<<<div_up(np, 256), 256, 0, st>>>(np, perm, src, dst);
+        count_launches(1);
+    }
 }

@@ -127,6 +127,10 @@ struct Dot2 {
 
 static inline int div_up(ll a, int b) { return (int)((a + b - 1) / b); }
 
+// Process-wide count of kernel launches issued by the library (each launcher
+// adds the number of kernels it queued).
+void count_launches(int k);
+
 // Launchers (one per translation unit, all asynchronous on `st`).
 void launch_sort(const Geo &g, Work &w, const float *px, const float *py, ll np, const float *vals, int F,
                  cudaStream_t st);
@@ -144,3 +148,8 @@ int launch_cg(const Geo &g, Work &w, int F, const float *b_float, bool b_from_fi
 void launch_scatter_sorted(ll np, const int *perm, const float *src, float *dst, cudaStream_t st);
 void launch_export_tris(const Geo &g, Work &w, ll np, int *tri, int *off, ll max_tri, cudaStream_t st);
 void launch_psum(const Geo &g, Work &w, ll np, int F, cudaStream_t st);
+void launch_advect_shift(const Geo &g, float *px, float *py, ll np, float dx, float dy, cudaStream_t st);
+void launch_advect_rotate(const Geo &g, float *px, float *py, ll np, float cx, float cy, float c, float s,
+                          cudaStream_t st);
+void launch_advect_rk2(const Geo &g, const float *mesh_vel, const float *vel, float *px, float *py, ll np, float dt,
+                       float *vals, int F, float factor, int *status, cudaStream_t st);

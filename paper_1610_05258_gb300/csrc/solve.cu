@@ -379,6 +379,7 @@ void launch_mass_apply(const Geo &g, const float *x, int F, float *y, cudaStream
         k_mass_apply<1><<<div_up(g.ncell, 256), 256, 0, st>>>(g, x, F, y);
     else
         k_mass_apply<2><<<div_up(g.ncell, 256), 256, 0, st>>>(g, x, F, y);
+    count_launches(1);
 }
 
 // Returns 0 or a CUDA error code.
@@ -421,5 +422,6 @@ int launch_cg(const Geo &g, Work &w, int F, const float *b_float, bool b_from_fi
     cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st);
     void *args[] = {&a};
     cudaError_t e = cudaLaunchCooperativeKernel((void *)kern, dim3(grid), dim3(256), args, 0, st);
+    count_launches(1);
     return (int)e;
 }

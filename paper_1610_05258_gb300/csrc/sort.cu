@@ -170,4 +170,5 @@ void launch_sort(const Geo &g, Work &w, const float *px, const float *py, ll np,
     if (np > 0) k_place<<<div_up(np, 256), 256, 0, st>>>(np, w.key, w.slot, w.cell_start, w.tmp);
     k_canon<<<div_up(g.ncell, 128), 128, 0, st>>>(g, np, w.cell_start, w.tmp, w.fx, vals, vals ? F : 0, w.perm,
                                                    w.pos, w.vals, w.maxabs, w.status);
+    count_launches(np > 0 ? 6 : 4);
 }

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(128) k_delta2d(Geo g, ll np, const uint2 *__re
             const float D = fax * fby - fay * fbx;
             for (ll j = j0; j <= j1; ++j)
                 for (ll i = i0; i <= i1; ++i) {
-                    const ll qx = (i << 32) - Xn, qy = (j << 32) - Yn;
+                    const ll qx = i * 4294967296LL - Xn, qy = j * 4294967296LL - Yn;
                     if (orient_pert(Ax, Ay, Bx, By, qx, qy) < 0) continue;
                     if (orient_pert(Bx, By, 0, 0, qx, qy) < 0) continue;
                     if (orient_pert(0, 0, Ax, Ay, qx, qy) < 0) continue;
@@ -420,6 +420,7 @@ void launch_delta(const Geo &g, Work &w, ll np, int F, float *mesh_out, cudaStre
         k_delta2d<<<div_up(np, 128), 128, 0, st>>>(g, np, w.pos, w.nbr, w.deg, w.vals, F, mesh_out);
     else
         k_delta1d<<<div_up(g.n, 128), 128, 0, st>>>(g, np, w.pos, w.cell_start, w.vals, F, mesh_out);
+    count_launches(1);
 }
 
 void launch_flip(const Geo &g, Work &w, ll np, int F, float *mesh_out, float *node_vol, cudaStream_t st) {
@@ -431,6 +432,7 @@ void launch_flip(const Geo &g, Work &w, ll np, int F, float *mesh_out, float *no
         k_flip_cells<1><<<div_up(g.ncell, 128), 128, 0, st>>>(g, np, w.cell_start, w.pos, w.vals, w.vol, F, w.part);
         k_flip_nodes<1><<<div_up(g.ncell, 256), 256, 0, st>>>(g, F, w.part, mesh_out, node_vol, w.empty);
     }
+    count_launches(2);
 }
 
 void launch_rhs(const Geo &g, Work &w, ll np, int F, cudaStream_t st) {
@@ -440,13 +442,16 @@ void launch_rhs(const Geo &g, Work &w, ll np, int F, cudaStream_t st) {
         k_rhs2d<<<div_up(np, 128), 128, 0, st>>>(g, np, w.pos, w.nbr, w.deg, w.vals, F, w.maxabs, w.bfix);
     else
         k_rhs1d<<<div_up(np, 128), 128, 0, st>>>(g, np, w.pos, w.vals, F, w.maxabs, w.bfix);
+    count_launches(1);
 }
 
 void launch_rhs_to_float(const Geo &g, Work &w, int F, float *b_out, cudaStream_t st) {
     k_fix_to_float<<<div_up(g.ncell * F, 256), 256, 0, st>>>(g, F, w.bfix, w.maxabs, b_out);
+    count_launches(1);
 }
 
 void launch_psum(const Geo &g, Work &w, ll np, int F, cudaStream_t st) {
     (void)g;
     k_psum<<<w.nblk_psum, 256, 0, st>>>(np, w.vals, w.vol, F, w.psum, w.nblk_psum);
+    count_launches(1);
 }
