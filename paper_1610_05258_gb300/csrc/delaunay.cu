@@ -8,10 +8,12 @@
 // the cell-sorted array. The cell is a cyclic list of neighbours q_k; its
 // vertex k is the circumcentre of (p, q_k, q_k+1). A candidate s removes
 // vertex k iff s lies strictly inside the circle through (p, q_k, q_k+1):
-// the in-circle predicate, evaluated exactly on the 32-bit torus
-// coordinates (float filter, 128-bit integer fallback), with exact ties
-// broken by symbolic perturbation of the lifted coordinate |r|^2 + eps^rank,
-// rank = caller index. After ring r the cell is final once every vertex v
+// the in-circle predicate, equivalently 2 c_k . s > |s|^2 for the
+// circumcentre c_k. It is decided in float from c_k and a rigorous bound on
+// its error, and exactly on the 32-bit torus coordinates (128-bit integers)
+// when the float value falls inside the error margin; exact ties are broken
+// by symbolic perturbation of the lifted coordinate |r|^2 + eps^rank, rank =
+// caller index. After ring r the cell is final once every vertex v
 // satisfies 2|v| < (distance from p to the unscanned cells). The neighbour
 // cycle is p's Delaunay star. Because every decision is exact and the
 // perturbation is a property of the point set, the stars of all particles
@@ -54,63 +56,181 @@ __device__ __noinline__ bool incircle_exact(int ax, int ay, int bx, int by, int 
     return false;
 }
 
-// Float filter of the same predicate: +1 inside, -1 outside, 0 undecided.
-// |error| of the float evaluation is far below 1e-5 of the permanent.
-__device__ __forceinline__ int incircle_filter(float ax, float ay, float bx, float by, float sx, float sy) {
-    float al = ax * ax + ay * ay, bl = bx * bx + by * by, sl = sx * sx + sy * sy;
-    float t1 = by * sl - sy * bl, t2 = bx * sl - sx * bl, t3 = bx * sy - by * sx;
-    float det = ax * t1 - ay * t2 + al * t3;
-    float pm = fabsf(ax) * (fabsf(by) * sl + fabsf(sy) * bl) + fabsf(ay) * (fabsf(bx) * sl + fabsf(sx) * bl) +
-               al * (fabsf(bx * sy) + fabsf(by * sx));
-    float eb = 1e-5f * pm;
-    if (det < -eb) return 1;
-    if (det > eb) return -1;
-    return 0;
-}
-
-// Upper bound of |circumcentre(0, a, b)|^2 (infinite when ill-conditioned).
-__device__ __forceinline__ float circ_bound2(float ax, float ay, float bx, float by) {
-    float al = ax * ax + ay * ay, bl = bx * bx + by * by;
-    float D = 2.0f * (ax * by - ay * bx);
-    float eD = 2e-5f * (fabsf(ax * by) + fabsf(ay * bx));
-    float Nx = by * al - ay * bl, Ny = ax * bl - bx * al;
-    float eNx = 1e-5f * (fabsf(by * al) + fabsf(ay * bl));
-    float eNy = 1e-5f * (fabsf(ax * bl) + fabsf(bx * al));
-    float den = fabsf(D) - eD;
-    if (!(den > 0.0f)) return INFINITY;
-    float cx = (fabsf(Nx) + eNx) / den, cy = (fabsf(Ny) + eNy) / den;
-    return cx * cx + cy * cy;
-}
-
 __device__ __forceinline__ int prio(int enc, const int *__restrict__ perm) {
     return enc >= 0 ? perm[enc & 0x0fffffff] : 0x7fffffff + enc;  // virtual points rank last
 }
 
-struct Poly {
-    int x[2][PM_MAXW], y[2][PM_MAXW], e[2][PM_MAXW];
-    float c[2][PM_MAXW];
+#define DBLK 64  // threads per block of the triangulation kernel
+#define DMAXW 24 // working polygon capacity (>= PM_MAXDEG)
+
+// Float circumcentre c of (0, a, b) and a bound e on the error of each of its
+// components (infinite when the triangle is too flat to bound). Inputs are
+// exact integers below 2^30 in magnitude; every rounding, including the
+// conversion of the inputs to float, is covered by the 8u factors.
+__device__ __forceinline__ void circumcentre(float ax, float ay, float bx, float by, float &cx, float &cy, float &e) {
+    const float u8 = 4.8e-7f;  // 8 units of roundoff
+    float al = ax * ax + ay * ay, bl = bx * bx + by * by;
+    float D = 2.0f * (ax * by - ay * bx);
+    float eD = 2.0f * u8 * (fabsf(ax * by) + fabsf(ay * bx));
+    float Nx = by * al - ay * bl, Ny = ax * bl - bx * al;
+    float eN = u8 * fmaxf(fabsf(by * al) + fabsf(ay * bl), fabsf(ax * bl) + fabsf(bx * al));
+    float den = fabsf(D) - eD;
+    const float iD = __frcp_rn(D);
+    cx = Nx * iD;
+    cy = Ny * iD;
+    if (!(den > 0.0f)) {
+        e = INFINITY;
+        return;
+    }
+    float cm = fmaxf(fabsf(cx), fabsf(cy));
+    // per-component bound (the reciprocal and product roundings are inside
+    // the u8 term), doubled to cover the vector norm (sqrt 2) with slack
+    e = 2.0f * ((eN + cm * eD) * __frcp_ru(den) + u8 * cm);
+    if (!(e < INFINITY) || !(cm < INFINITY)) e = INFINITY;
+}
+
+// Polygon state of one thread: neighbour entry k = (x, y, code, bits of w_k)
+// with w_k = e_k + 8u |c_k| (so that the float test  2 c_k . s > |s|^2  is
+// certain outside the margin  w_k |s| + 4u |s|^2), and vertex k, the
+// circumcentre c_k of (p, q_k, q_k+1).
+struct PolyS {
+    int4 (*q)[DBLK];
+    float2 (*v)[DBLK];
+    int t;
 };
 
-__global__ void __launch_bounds__(128) k_delaunay(Geo g, ll np, const uint2 *__restrict__ pos,
-                                                  const int *__restrict__ cell_start, const int *__restrict__ perm,
-                                                  int *__restrict__ nbr, unsigned char *__restrict__ deg,
-                                                  float *__restrict__ vol, float vol_scale, int *__restrict__ status) {
-    ll pl = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void set_vertex(PolyS P, int k, float ax, float ay, float bx, float by) {
+    float cx, cy, e;
+    circumcentre(ax, ay, bx, by, cx, cy, e);
+    P.v[k][P.t] = make_float2(cx, cy);
+    float w = e + 4.8e-7f * fmaxf(fabsf(cx), fabsf(cy)) * 1.5f;
+    P.q[k][P.t].w = __float_as_int(w < INFINITY ? w : INFINITY);
+}
+
+// Upper bound of the largest (|c_k| + w_k)^2, without square roots:
+// (|c| + w)^2 <= |c|^2 + 2 sqrt2 max(|cx|,|cy|) w + w^2 (infinite if any
+// vertex is unbounded).
+__device__ __forceinline__ float max_radius2(PolyS P, int m) {
+    float R2 = 0.0f;
+    for (int k = 0; k < m; ++k) {
+        const float2 c = P.v[k][P.t];
+        const float w = __int_as_float(P.q[k][P.t].w);
+        const float rr = (c.x * c.x + c.y * c.y) * 1.000001f + 2.8285f * fmaxf(fabsf(c.x), fabsf(c.y)) * w + w * w;
+        if (!(rr < INFINITY)) return INFINITY;
+        R2 = fmaxf(R2, rr);
+    }
+    return R2;
+}
+
+// Clip the cell of p by the bisector of candidate s (relative position
+// (sx, sy), sorted index sidx, image code). Returns an error bit or 0.
+__device__ __forceinline__ int clip_by(PolyS P, int &m, float &R2, int sx, int sy, int sidx, int code, int p,
+                                       int &pp, const int *__restrict__ perm) {
+    const float fsx = (float)sx, fsy = (float)sy;
+    const float d2 = fsx * fsx + fsy * fsy;
+    if (d2 > 4.0001f * R2) return 0;  // |s| > 2 max|c|: no vertex can be cut
+    // |s| <= sqrt2 max(|sx|, |sy|) stands in for the norm in the margin
+    const float hs = 0.5f * d2, ns = 1.41422f * fmaxf(fabsf(fsx), fabsf(fsy)), mr = 2.4e-7f * d2;
+    unsigned mask = 0;
+    int ps = -2;
+    const int t = P.t;
+    for (int k = 0; k < m; ++k) {
+        const float2 c = P.v[k][t];
+        const float hk = c.x * fsx + c.y * fsy - hs;
+        const float mg = __int_as_float(P.q[k][t].w) * ns + mr;
+        int v;
+        if (hk > mg) v = 1;
+        else if (hk < -mg) v = -1;
+        else {
+            const int4 A = P.q[k][t], Bq = P.q[k + 1 == m ? 0 : k + 1][t];
+            if (pp == -2) pp = perm[p];
+            if (ps == -2) ps = perm[sidx];
+            v = incircle_exact(A.x, A.y, Bq.x, Bq.y, sx, sy, pp, prio(A.z, perm), prio(Bq.z, perm), ps) ? 1 : -1;
+        }
+        if (v > 0) mask |= 1u << k;
+    }
+    if (mask == 0) return 0;
+    const unsigned full = (1u << m) - 1u;
+    const int cnt = __popc(mask);
+    const unsigned prevm = ((mask << 1) | (mask >> (m - 1))) & full;
+    const unsigned starts = mask & ~prevm;
+    if (cnt >= m || __popc(starts) != 1) return ST_RANGE;
+    const int i0 = __ffs(starts) - 1;  // first removed vertex; q_i0 is kept
+    const int nd = cnt - 1;            // neighbours q_{i0+1..i0+nd} are removed
+    if (m - nd + 1 > DMAXW) return ST_DEGREE;
+    const int4 S = make_int4(sx, sy, sidx | (code << 28), 0);
+    int ipos;
+    if (i0 + nd < m) {
+        if (nd == 0) {
+            for (int k = m; k > i0 + 1; --k) {
+                P.q[k][t] = P.q[k - 1][t];
+                P.v[k][t] = P.v[k - 1][t];
+            }
+            m += 1;
+        } else if (nd > 1) {
+            for (int k = i0 + 2; k + nd - 1 < m; ++k) {
+                P.q[k][t] = P.q[k + nd - 1][t];
+                P.v[k][t] = P.v[k + nd - 1][t];
+            }
+            m -= nd - 1;
+        }
+        P.q[i0 + 1][t] = S;
+        ipos = i0 + 1;
+    } else {
+        const int dbeg = nd - (m - 1 - i0);
+        for (int k = 0; k <= i0 - dbeg; ++k) {
+            P.q[k][t] = P.q[k + dbeg][t];
+            P.v[k][t] = P.v[k + dbeg][t];
+        }
+        m = i0 - dbeg + 1;
+        P.q[m][t] = S;
+        ipos = m;
+        m += 1;
+    }
+    const int iprev = ipos == 0 ? m - 1 : ipos - 1, inext = ipos + 1 == m ? 0 : ipos + 1;
+    const int4 Q = P.q[iprev][t], Nq = P.q[inext][t];
+    set_vertex(P, iprev, (float)Q.x, (float)Q.y, fsx, fsy);
+    set_vertex(P, ipos, fsx, fsy, (float)Nq.x, (float)Nq.y);
+    R2 = max_radius2(P, m);
+    return 0;
+}
+
+// Cell (dx, dy) of the neighbourhood of cell (cx, cy): wrapped index, image offsets.
+__device__ __forceinline__ int nb_cell(int cx, int cy, int dx, int dy, int n, int &ox, int &oy) {
+    int ux = cx + dx, uy = cy + dy;
+    ox = ux < 0 ? -1 : (ux >= n ? 1 : 0);
+    oy = uy < 0 ? -1 : (uy >= n ? 1 : 0);
+    return (uy - oy * n) * n + (ux - ox * n);
+}
+
+// The working polygon of every thread lives in shared memory, one column per
+// thread. Candidates are taken ring by ring of cells around p until the cell
+// is certified.
+__global__ void __launch_bounds__(DBLK) k_delaunay(Geo g, ll np, const uint2 *__restrict__ pos,
+                                                   const int *__restrict__ cell_start, const int *__restrict__ perm,
+                                                   int *__restrict__ nbr, unsigned char *__restrict__ deg,
+                                                   float *__restrict__ vol, float vol_scale, int *__restrict__ status) {
+    __shared__ int4 sq[DMAXW][DBLK];
+    __shared__ float2 sv[DMAXW][DBLK];
+    const int t = threadIdx.x;
+    ll pl = (ll)blockIdx.x * blockDim.x + t;
     if (pl >= np) return;
     const int p = (int)pl;
     const int n = g.n;
-    Poly P;
-    int cur = 0, m = 4;
+    PolyS P{sq, sv, t};
+    int m = 4;
     const int B = 1 << 29;
+    const float hb = 0.5f * (float)B;
     // initial cell: the square cut out by four virtual points at distance B
-    const int ix[4] = {B, 0, -B, 0}, iy[4] = {0, B, 0, -B};
-    for (int k = 0; k < 4; ++k) {
-        P.x[0][k] = ix[k];
-        P.y[0][k] = iy[k];
-        P.e[0][k] = -1 - k;
-        P.c[0][k] = 0.5f * (float)B * (float)B;
-    }
-    float maxc2 = 0.5f * (float)B * (float)B;
+    sq[0][t] = make_int4(B, 0, -1, 0);
+    sq[1][t] = make_int4(0, B, -2, 0);
+    sq[2][t] = make_int4(-B, 0, -3, 0);
+    sq[3][t] = make_int4(0, -B, -4, 0);
+    sv[0][t] = make_float2(hb, hb);
+    sv[1][t] = make_float2(-hb, hb);
+    sv[2][t] = make_float2(-hb, -hb);
+    sv[3][t] = make_float2(hb, -hb);
+    float R2 = 2.0f * hb * hb;
     const uint2 Xp = pos[p];
     const int cx = cell_of(Xp.x, n), cy = cell_of(Xp.y, n);
     const float cw = 4294967296.0f / (float)n;
@@ -119,10 +239,12 @@ __global__ void __launch_bounds__(128) k_delaunay(Geo g, ll np, const uint2 *__r
     int pp = -2;  // priority of p, loaded on first exact test
     int rmax = min(PM_RCAP, n / 4 - 1);
     if (rmax < 0) rmax = 0;
-    bool done = false;
     int err = 0;
+    bool done = false;
+    // --- rings 0, 1, 2, ... until certified. Differences of torus coordinates
+    // in 32-bit arithmetic are the minimal-image offsets (all |.| < 2^31).
     for (int r = 0; r <= rmax && !done && !err; ++r) {
-        int ncells = r == 0 ? 1 : 8 * r;
+        const int ncells = r == 0 ? 1 : 8 * r;
         for (int ci = 0; ci < ncells && !err; ++ci) {
             int dx, dy;
             if (r == 0) { dx = 0; dy = 0; }
@@ -130,77 +252,21 @@ __global__ void __launch_bounds__(128) k_delaunay(Geo g, ll np, const uint2 *__r
             else if (ci < 4 * r + 2) { dx = ci - (3 * r + 1); dy = r; }
             else if (ci < 6 * r + 1) { dx = -r; dy = ci - (5 * r + 1); }
             else { dx = r; dy = ci - (7 * r); }
-            int ux = cx + dx, uy = cy + dy;
-            int ox = ux < 0 ? -1 : (ux >= n ? 1 : 0), oy = uy < 0 ? -1 : (uy >= n ? 1 : 0);
-            int c = (uy - oy * n) * n + (ux - ox * n);
-            int s0 = cell_start[c], s1 = cell_start[c + 1];
+            int ox, oy, c = nb_cell(cx, cy, dx, dy, n, ox, oy);
+            const int code = (ox + 1) * 3 + (oy + 1);
+            const int s0 = __ldg(cell_start + c), s1 = __ldg(cell_start + c + 1);
             for (int s = s0; s < s1; ++s) {
                 if (s == p) continue;
-                uint2 Xs = pos[s];
-                ll rx = (ll)Xs.x + (ll)ox * 4294967296LL - (ll)Xp.x;
-                ll ry = (ll)Xs.y + (ll)oy * 4294967296LL - (ll)Xp.y;
-                if (rx == 0 && ry == 0) { err |= ST_DUP; break; }
-                if (rx > (1LL << 30) || rx < -(1LL << 30) || ry > (1LL << 30) || ry < -(1LL << 30)) continue;
-                const int sx = (int)rx, sy = (int)ry;
-                const float fsx = (float)sx, fsy = (float)sy;
-                const float d2 = fsx * fsx + fsy * fsy;
-                if (d2 > 4.0001f * maxc2) continue;
-                // which vertices does s cut away?
-                unsigned mask = 0;
-                int ps = -2;
-                for (int k = 0; k < m; ++k) {
-                    if (d2 > 4.0001f * P.c[cur][k]) continue;
-                    int k1 = k + 1 == m ? 0 : k + 1;
-                    int ax = P.x[cur][k], ay = P.y[cur][k], bx = P.x[cur][k1], by = P.y[cur][k1];
-                    int v = incircle_filter((float)ax, (float)ay, (float)bx, (float)by, fsx, fsy);
-                    if (v == 0) {
-                        if (pp == -2) pp = perm[p];
-                        if (ps == -2) ps = perm[s];
-                        v = incircle_exact(ax, ay, bx, by, sx, sy, pp, prio(P.e[cur][k], perm),
-                                           prio(P.e[cur][k1], perm), ps)
-                                ? 1
-                                : -1;
-                    }
-                    if (v > 0) mask |= 1u << k;
-                }
-                if (mask == 0) continue;
-                int cnt = __popc(mask);
-                if (cnt >= m) { err |= ST_RANGE; break; }
-                // first vertex of the (cyclic) run of removed vertices
-                int i0 = 0;
-                for (int k = 0; k < m; ++k) {
-                    int km = k == 0 ? m - 1 : k - 1;
-                    if ((mask >> k & 1u) && !(mask >> km & 1u)) { i0 = k; break; }
-                }
-                int j1 = i0 + cnt;  // index (mod m) of the first kept neighbour after the run
-                int mm = m - cnt + 2;
-                if (mm > PM_MAXW) { err |= ST_DEGREE; break; }
-                const int nx = cur ^ 1;
-                int t = 0;
-                for (; t <= m - cnt; ++t) {
-                    int k = (j1 + t) % m;
-                    P.x[nx][t] = P.x[cur][k];
-                    P.y[nx][t] = P.y[cur][k];
-                    P.e[nx][t] = P.e[cur][k];
-                    P.c[nx][t] = P.c[cur][k];
-                }
-                // kept q_i (last copied) now meets s, and s meets the first kept
-                int qi = m - cnt;
-                P.c[nx][qi] = circ_bound2((float)P.x[nx][qi], (float)P.y[nx][qi], fsx, fsy);
-                P.x[nx][t] = sx;
-                P.y[nx][t] = sy;
-                P.e[nx][t] = s | (((ox + 1) * 3 + (oy + 1)) << 28);
-                P.c[nx][t] = circ_bound2(fsx, fsy, (float)P.x[nx][0], (float)P.y[nx][0]);
-                cur = nx;
-                m = mm;
-                maxc2 = 0.0f;
-                for (int k = 0; k < m; ++k) maxc2 = fmaxf(maxc2, P.c[cur][k]);
+                const uint2 Xs = __ldg(pos + s);
+                const int rx = (int)(Xs.x - Xp.x), ry = (int)(Xs.y - Xp.y);
+                if ((rx | ry) == 0) { err |= ST_DUP; break; }
+                if (rx > (1 << 30) || rx < -(1 << 30) || ry > (1 << 30) || ry < -(1 << 30)) continue;
+                err |= clip_by(P, m, R2, rx, ry, s, code, p, pp, perm);
+                if (err) break;
             }
         }
-        // certified when every vertex is closer than half the distance to
-        // anything not yet scanned
-        float dmin = edge + (float)r * cw;
-        if (4.0001f * maxc2 < dmin * dmin) done = true;
+        const float dmin = edge + (float)r * cw;
+        if (4.0001f * R2 < dmin * dmin) done = true;
     }
     if (!done && !err) err |= ST_SPARSE;
     if (m > PM_MAXDEG) err |= ST_DEGREE;
@@ -211,10 +277,12 @@ __global__ void __launch_bounds__(128) k_delaunay(Geo g, ll np, const uint2 *__r
         return;
     }
     ll area2 = 0;
+    int4 A = sq[0][t];
     for (int k = 0; k < m; ++k) {
-        int k1 = k + 1 == m ? 0 : k + 1;
-        area2 += (ll)P.x[cur][k] * P.y[cur][k1] - (ll)P.y[cur][k] * P.x[cur][k1];
-        nbr[(ll)k * np + p] = P.e[cur][k];
+        int4 Bq = sq[k + 1 == m ? 0 : k + 1][t];
+        area2 += (ll)A.x * Bq.y - (ll)A.y * Bq.x;
+        nbr[(ll)k * np + p] = A.z;
+        A = Bq;
     }
     deg[p] = (unsigned char)m;
     vol[p] = (float)area2 * vol_scale;
@@ -259,8 +327,8 @@ void launch_triangulate(const Geo &g, Work &w, ll np, cudaStream_t st) {
     if (np <= 0) return;
     double u = g.L / 4294967296.0;
     float scale = (float)(u * u / 6.0);
-    k_delaunay<<<div_up(np, 128), 128, 0, st>>>(g, np, w.pos, w.cell_start, w.perm, w.nbr, w.deg, w.vol, scale,
-                                                 w.status);
+    k_delaunay<<<div_up(np, DBLK), DBLK, 0, st>>>(g, np, w.pos, w.cell_start, w.perm, w.nbr, w.deg, w.vol, scale,
+                                                   w.status);
     count_launches(1);
 }
 

@@ -208,35 +208,12 @@ __global__ void k_flip_nodes(Geo g, int F, const float *__restrict__ part, float
 // mass right-hand side, exact
 // ---------------------------------------------------------------------------
 
-// Sutherland-Hodgman clip of a convex polygon (in place into out) against
-// the half plane  sgn * (coord) <= lim  (coord = x if ax == 0 else y).
-__device__ __forceinline__ int clip_poly(const float *xi, const float *yi, int m, int axis, float sgn, float lim,
-                                         float *xo, float *yo) {
-    int k = 0;
-    for (int a = 0; a < m; ++a) {
-        int b = a + 1 == m ? 0 : a + 1;
-        float da = sgn * (axis == 0 ? xi[a] : yi[a]) - lim;
-        float db = sgn * (axis == 0 ? xi[b] : yi[b]) - lim;
-        if (da <= 0.0f) { xo[k] = xi[a]; yo[k] = yi[a]; ++k; }
-        if ((da < 0.0f && db > 0.0f) || (da > 0.0f && db < 0.0f)) {
-            float t = da / (da - db);
-            xo[k] = fmaf(t, xi[b] - xi[a], xi[a]);
-            yo[k] = fmaf(t, yi[b] - yi[a], yi[a]);
-            ++k;
-        }
-    }
-    return k;
-}
-
-// Moments int s^a t^b over a counter-clockwise polygon by Green's theorem
-// (edge sums of the cross term c_k times binomial vertex polynomials).
-// M = {M00, M10, M01, M20, M11, M02, M21, M12}
-__device__ __forceinline__ void poly_moments(const float *x, const float *y, int m, float M[8]) {
+// Green's-theorem edge sums of the directed segment (x0,y0) -> (x1,y1) for the
+// moments  int s^a t^b  (a + b <= 3, without s^3 and t^3); scaled at the end.
+struct Mom {
     float a0 = 0, a10 = 0, a01 = 0, a20 = 0, a11 = 0, a02 = 0, a21 = 0, a12 = 0;
-    for (int k = 0; k < m; ++k) {
-        int l = k + 1 == m ? 0 : k + 1;
-        float x0 = x[k], y0 = y[k], x1 = x[l], y1 = y[l];
-        float c = x0 * y1 - x1 * y0;
+    __device__ __forceinline__ void seg(float x0, float y0, float x1, float y1) {
+        const float c = x0 * y1 - x1 * y0;
         a0 += c;
         a10 += c * (x0 + x1);
         a01 += c * (y0 + y1);
@@ -248,95 +225,243 @@ __device__ __forceinline__ void poly_moments(const float *x, const float *y, int
         a12 += c * (3.0f * y1 * y1 * x1 + 2.0f * y0 * y1 * x1 + y0 * y0 * x1 + y1 * y1 * x0 + 2.0f * y0 * y1 * x0 +
                     3.0f * y0 * y0 * x0);
     }
-    M[0] = a0 * 0.5f;
-    M[1] = a10 * (1.0f / 6.0f);
-    M[2] = a01 * (1.0f / 6.0f);
-    M[3] = a20 * (1.0f / 12.0f);
-    M[4] = a11 * (1.0f / 24.0f);
-    M[5] = a02 * (1.0f / 12.0f);
-    M[6] = a21 * (1.0f / 60.0f);
-    M[7] = a12 * (1.0f / 60.0f);
+};
+
+// Liang-Barsky step for the constraint p t <= q on t in [t0, t1].
+__device__ __forceinline__ bool lb(float p, float q, float &t0, float &t1) {
+    if (p == 0.0f) return q >= 0.0f;
+    float r = q / p;
+    if (p < 0.0f) t0 = fmaxf(t0, r);
+    else t1 = fminf(t1, r);
+    return true;
 }
 
-__global__ void __launch_bounds__(128) k_rhs2d(Geo g, ll np, const uint2 *__restrict__ pos,
-                                               const int *__restrict__ nbr, const unsigned char *__restrict__ deg,
-                                               const float *__restrict__ vals, int F,
-                                               const unsigned *__restrict__ maxabs, ll *__restrict__ bfix) {
-    ll pl = (ll)blockIdx.x * blockDim.x + threadIdx.x;
-    if (pl >= np) return;
-    const int p = (int)pl, n = g.n, m = deg[p];
-    if (m < 3) return;
-    const float hd = g.h * g.h;
-    int E[PM_MAXF];
-    for (int f = 0; f < F; ++f) E[f] = fix_exp(maxabs, f, hd);
-    const uint2 Xp = pos[p];
-    const int cxp = cell_of(Xp.x, n), cyp = cell_of(Xp.y, n);
-    const float up = frac_f(Xp.x, n), wp = frac_f(Xp.y, n);
-    const float sc = (float)n * 2.3283064365386963e-10f;
-    float Ap[PM_MAXF];
-    for (int f = 0; f < F; ++f) Ap[f] = vals[(ll)f * np + p];
-    int ida;
-    ll ax, ay;
-    rel_of(nbr[(ll)(m - 1) * np + p], Xp, pos, ida, ax, ay);
-    for (int k = 0; k < m; ++k) {
-        int idb;
-        ll bx, by;
-        rel_of(nbr[(ll)k * np + p], Xp, pos, idb, bx, by);
-        if (ida > p && idb > p) {
-            // triangle in cell units relative to p's cell corner
-            float tx[3] = {up, up + (float)ax * sc, up + (float)bx * sc};
-            float ty[3] = {wp, wp + (float)ay * sc, wp + (float)by * sc};
-            float e1x = tx[1] - tx[0], e1y = ty[1] - ty[0], e2x = tx[2] - tx[0], e2y = ty[2] - ty[0];
-            float det = e1x * e2y - e1y * e2x;
-            float ga[PM_MAXF][2];
-            for (int f = 0; f < F; ++f) {
-                float da = vals[(ll)f * np + ida] - Ap[f], db = vals[(ll)f * np + idb] - Ap[f];
-                ga[f][0] = (da * e2y - db * e1y) / det;
-                ga[f][1] = (db * e1x - da * e2x) / det;
-            }
-            int i0 = (int)floorf(fminf(tx[0], fminf(tx[1], tx[2]))), i1 = (int)floorf(fmaxf(tx[0], fmaxf(tx[1], tx[2])));
-            int j0 = (int)floorf(fminf(ty[0], fminf(ty[1], ty[2]))), j1 = (int)floorf(fmaxf(ty[0], fmaxf(ty[1], ty[2])));
-            for (int cj = j0; cj <= j1; ++cj)
-                for (int ci = i0; ci <= i1; ++ci) {
-                    float xa[8], ya[8], xb[8], yb[8];
-                    for (int v = 0; v < 3; ++v) { xa[v] = tx[v] - (float)ci; ya[v] = ty[v] - (float)cj; }
-                    int mm = clip_poly(xa, ya, 3, 0, -1.0f, 0.0f, xb, yb);
-                    mm = clip_poly(xb, yb, mm, 0, 1.0f, 1.0f, xa, ya);
-                    mm = clip_poly(xa, ya, mm, 1, -1.0f, 0.0f, xb, yb);
-                    mm = clip_poly(xb, yb, mm, 1, 1.0f, 1.0f, xa, ya);
-                    if (mm < 3) continue;
-                    const float s0 = xa[0], t0 = ya[0];
-                    for (int v = 0; v < mm; ++v) { xb[v] = xa[v] - s0; yb[v] = ya[v] - t0; }
-                    float M[8];
-                    poly_moments(xb, yb, mm, M);
-                    if (!(M[0] > 0.0f)) continue;
-                    // corners (bx, by): psi = phi_bx(s) phi_by(t), phi_0 = 1 - s, phi_1 = s
-                    float K[4][3];
-                    for (int c = 0; c < 4; ++c) {
-                        float A1 = (c & 1) ? s0 : 1.0f - s0, B1 = (c & 1) ? 1.0f : -1.0f;
-                        float A2 = (c & 2) ? t0 : 1.0f - t0, B2 = (c & 2) ? 1.0f : -1.0f;
-                        float aa = A1 * A2, ab = A1 * B2, ba = B1 * A2, bb = B1 * B2;
-                        K[c][0] = aa * M[0] + ab * M[2] + ba * M[1] + bb * M[4];
-                        K[c][1] = aa * M[1] + ab * M[4] + ba * M[3] + bb * M[6];
-                        K[c][2] = aa * M[2] + ab * M[5] + ba * M[4] + bb * M[7];
-                    }
-                    const int gx0 = wrapi(cxp + ci, n), gy0 = wrapi(cyp + cj, n);
-                    const int gx1 = gx0 + 1 == n ? 0 : gx0 + 1, gy1 = gy0 + 1 == n ? 0 : gy0 + 1;
-                    const ll nodes[4] = {(ll)gy0 * n + gx0, (ll)gy0 * n + gx1, (ll)gy1 * n + gx0, (ll)gy1 * n + gx1};
-                    const float dsx = s0 + (float)ci - up, dty = t0 + (float)cj - wp;
-                    for (int f = 0; f < F; ++f) {
-                        float al = Ap[f] + ga[f][0] * dsx + ga[f][1] * dty;  // A at the polygon's first vertex
-                        for (int c = 0; c < 4; ++c) {
-                            float val = (al * K[c][0] + ga[f][0] * K[c][1] + ga[f][1] * K[c][2]) * hd;
-                            ll iv = __float2ll_rn(ldexpf(val, E[f]));
-                            if (iv) atomicAdd((ull *)&bfix[(ll)f * g.ncell + nodes[c]], (ull)iv);
-                        }
-                    }
-                }
+// Moments of (triangle T) intersected with the unit cell [0,1]^2, in
+// coordinates relative to the origin (ox, oy). T counter-clockwise, given in
+// cell coordinates. The boundary of the intersection is the part of T's
+// edges inside the cell plus the part of the cell's edges inside T.
+__device__ __forceinline__ Mom tri_cell_moments(const float tx[3], const float ty[3], float ox, float oy) {
+    Mom M;
+    for (int k = 0; k < 3; ++k) {
+        const int k1 = k == 2 ? 0 : k + 1;
+        const float px = tx[k], py = ty[k], dx = tx[k1] - px, dy = ty[k1] - py;
+        // an edge lying exactly on a cell line is accounted for by the cell edge
+        if ((dx == 0.0f && (px == 0.0f || px == 1.0f)) || (dy == 0.0f && (py == 0.0f || py == 1.0f))) continue;
+        float t0 = 0.0f, t1 = 1.0f;
+        if (!lb(-dx, px, t0, t1) || !lb(dx, 1.0f - px, t0, t1) || !lb(-dy, py, t0, t1) || !lb(dy, 1.0f - py, t0, t1))
+            continue;
+        if (!(t0 < t1)) continue;
+        M.seg(px + t0 * dx - ox, py + t0 * dy - oy, px + t1 * dx - ox, py + t1 * dy - oy);
+    }
+    const float cxs[5] = {0.0f, 1.0f, 1.0f, 0.0f, 0.0f}, cys[5] = {0.0f, 0.0f, 1.0f, 1.0f, 0.0f};
+    for (int e = 0; e < 4; ++e) {
+        const float ux = cxs[e], uy = cys[e], vx = cxs[e + 1], vy = cys[e + 1];
+        float t0 = 0.0f, t1 = 1.0f;
+        bool ok = true;
+        for (int k = 0; k < 3 && ok; ++k) {
+            const int k1 = k == 2 ? 0 : k + 1;
+            const float ex = tx[k1] - tx[k], ey = ty[k1] - ty[k];
+            const float q0 = ex * (uy - ty[k]) - ey * (ux - tx[k]);
+            const float dq = ex * (vy - uy) - ey * (vx - ux);
+            ok = lb(-dq, q0, t0, t1);
         }
-        ida = idb;
-        ax = bx;
-        ay = by;
+        if (!ok || !(t0 < t1)) continue;
+        M.seg(ux + t0 * (vx - ux) - ox, uy + t0 * (vy - uy) - oy, ux + t1 * (vx - ux) - ox, uy + t1 * (vy - uy) - oy);
+    }
+    return M;
+}
+
+#define RTS 16                      // cells per tile side
+#define RHALO 2                     // window halo in cells
+#define RWIN (RTS + 2 * RHALO + 1)  // window side in nodes
+
+// Triangle k of particle p's star, (p, q_{k-1}, q_k), in cell units relative
+// to p's cell corner, and its cell bounding box. Returns false when p does not
+// own it (ownership: lowest sorted index).
+struct Tri {
+    float vx[3], vy[3];
+    int a, b, i0, i1, j0, j1;
+};
+__device__ __forceinline__ bool owned_tri(int p, int m, int k, uint2 Xp, float up, float wp, float sc,
+                                          const uint2 *__restrict__ pos, const int *__restrict__ nbr, ll np, Tri &T) {
+    ll ax, ay, bx, by;
+    rel_of(nbr[(ll)(k == 0 ? m - 1 : k - 1) * np + p], Xp, pos, T.a, ax, ay);
+    rel_of(nbr[(ll)k * np + p], Xp, pos, T.b, bx, by);
+    if (T.a <= p || T.b <= p) return false;
+    T.vx[0] = up; T.vx[1] = up + (float)ax * sc; T.vx[2] = up + (float)bx * sc;
+    T.vy[0] = wp; T.vy[1] = wp + (float)ay * sc; T.vy[2] = wp + (float)by * sc;
+    T.i0 = (int)floorf(fminf(T.vx[0], fminf(T.vx[1], T.vx[2])));
+    T.i1 = (int)floorf(fmaxf(T.vx[0], fmaxf(T.vx[1], T.vx[2])));
+    T.j0 = (int)floorf(fminf(T.vy[0], fminf(T.vy[1], T.vy[2])));
+    T.j1 = (int)floorf(fmaxf(T.vy[0], fmaxf(T.vy[1], T.vy[2])));
+    return true;
+}
+
+// One block per tile of RTS x RTS cells. The (triangle, cell) pieces of the
+// triangles owned by the tile's particles are spread evenly over the lanes of
+// each warp (prefix sum of per-particle piece counts, then every lane takes
+// one piece per round), integrated exactly, and their four corner integrals
+// go to a shared window of nodes (64-bit fixed point, order-free integer
+// sums) or, outside the window, straight to global memory.
+template <int FF>
+__global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__restrict__ pos,
+                                               const int *__restrict__ cell_start, const int *__restrict__ nbr,
+                                               const unsigned char *__restrict__ deg, const float *__restrict__ vals,
+                                               int F, const unsigned *__restrict__ maxabs, ll *__restrict__ bfix,
+                                               int tiles_x) {
+    __shared__ ull acc[FF][RWIN * RWIN];
+    __shared__ int rowpre[RTS + 1];
+    __shared__ int rowbeg[RTS];
+    const int n = g.n;
+    const int tx0 = (blockIdx.x % tiles_x) * RTS, ty0 = (blockIdx.x / tiles_x) * RTS;
+    const int wx0 = tx0 - RHALO, wy0 = ty0 - RHALO;
+    for (int i = threadIdx.x; i < FF * RWIN * RWIN; i += blockDim.x) (&acc[0][0])[i] = 0ull;
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        const int xe = min(tx0 + RTS, n);
+        for (int r = 0; r < RTS; ++r) {
+            rowpre[r] = tot;
+            int y = ty0 + r;
+            if (y < n) {
+                rowbeg[r] = cell_start[(ll)y * n + tx0];
+                tot += cell_start[(ll)y * n + xe] - rowbeg[r];
+            } else {
+                rowbeg[r] = 0;
+            }
+        }
+        rowpre[RTS] = tot;
+    }
+    __syncthreads();
+    const float hd = g.h * g.h;
+    const float sc = (float)n * 2.3283064365386963e-10f;
+    int E[FF];
+    for (int f = 0; f < FF; ++f) E[f] = f < F ? fix_exp(maxabs, f, hd) : 0;
+    const int total = rowpre[RTS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int base = wid * 32; base < total; base += nw * 32) {
+        // this lane's particle and its number of pieces
+        const int k = base + lane;
+        int p = -1, cnt = 0;
+        if (k < total) {
+            int r = 0;
+            while (rowpre[r + 1] <= k) ++r;
+            p = rowbeg[r] + (k - rowpre[r]);
+            const int m = deg[p];
+            if (m >= 3) {
+                const uint2 Xp = pos[p];
+                const float up = frac_f(Xp.x, n), wp = frac_f(Xp.y, n);
+                for (int kk = 0; kk < m; ++kk) {
+                    Tri T;
+                    if (owned_tri(p, m, kk, Xp, up, wp, sc, pos, nbr, np, T))
+                        cnt += (T.i1 - T.i0 + 1) * (T.j1 - T.j0 + 1);
+                }
+            }
+        }
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int excl = incl - cnt;
+        const int T_all = __shfl_sync(0xffffffffu, incl, 31);
+        for (int j0 = 0; j0 < T_all; j0 += 32) {
+            const int j = j0 + lane;
+            // owner lane of piece j: the first lane whose inclusive count exceeds j
+            int lo = 0;
+            for (int step = 16; step > 0; step >>= 1) {
+                int v = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+                if (v <= j) lo += step;
+            }
+            const int src = lo;
+            const int ps = __shfl_sync(0xffffffffu, p, src);
+            const int jj = j - __shfl_sync(0xffffffffu, excl, src);
+            if (j >= T_all) continue;
+            // locate the piece inside particle ps
+            const int m = deg[ps];
+            const uint2 Xp = pos[ps];
+            const int cxp = cell_of(Xp.x, n), cyp = cell_of(Xp.y, n);
+            const float up = frac_f(Xp.x, n), wp = frac_f(Xp.y, n);
+            Tri T;
+            int rem = jj, ci = 0, cj = 0;
+            bool found = false;
+            for (int kk = 0; kk < m && !found; ++kk) {
+                if (!owned_tri(ps, m, kk, Xp, up, wp, sc, pos, nbr, np, T)) continue;
+                const int w = T.i1 - T.i0 + 1, c = w * (T.j1 - T.j0 + 1);
+                if (rem < c) {
+                    ci = T.i0 + rem % w;
+                    cj = T.j0 + rem / w;
+                    found = true;
+                } else {
+                    rem -= c;
+                }
+            }
+            if (!found) continue;
+            const float fci = (float)ci, fcj = (float)cj;
+            const float xmin = fminf(T.vx[0], fminf(T.vx[1], T.vx[2])), xmax = fmaxf(T.vx[0], fmaxf(T.vx[1], T.vx[2]));
+            const float ymin = fminf(T.vy[0], fminf(T.vy[1], T.vy[2])), ymax = fmaxf(T.vy[0], fmaxf(T.vy[1], T.vy[2]));
+            const float tx[3] = {T.vx[0] - fci, T.vx[1] - fci, T.vx[2] - fci};
+            const float ty[3] = {T.vy[0] - fcj, T.vy[1] - fcj, T.vy[2] - fcj};
+            const float ox = 0.5f * (fmaxf(0.0f, xmin - fci) + fminf(1.0f, xmax - fci));
+            const float oy = 0.5f * (fmaxf(0.0f, ymin - fcj) + fminf(1.0f, ymax - fcj));
+            Mom Mm = tri_cell_moments(tx, ty, ox, oy);
+            if (!(Mm.a0 > 0.0f)) continue;
+            const float M00 = Mm.a0 * 0.5f, M10 = Mm.a10 * (1.0f / 6.0f), M01 = Mm.a01 * (1.0f / 6.0f);
+            const float M20 = Mm.a20 * (1.0f / 12.0f), M11 = Mm.a11 * (1.0f / 24.0f);
+            const float M02 = Mm.a02 * (1.0f / 12.0f), M21 = Mm.a21 * (1.0f / 60.0f);
+            const float M12 = Mm.a12 * (1.0f / 60.0f);
+            // A on the triangle: value at p plus gradient (cell units)
+            const float e1x = T.vx[1] - T.vx[0], e1y = T.vy[1] - T.vy[0];
+            const float e2x = T.vx[2] - T.vx[0], e2y = T.vy[2] - T.vy[0];
+            const float idet = 1.0f / (e1x * e2y - e1y * e2x);
+            const float dsx = ox + fci - up, dty = oy + fcj - wp;
+            const int gcx = cxp + ci, gcy = cyp + cj;  // unwrapped cell
+            float al[FF], gx[FF], gy[FF];
+#pragma unroll
+            for (int f = 0; f < FF; ++f) {
+                if (f < F) {
+                    const float A0 = vals[(ll)f * np + ps];
+                    const float da = vals[(ll)f * np + T.a] - A0, db = vals[(ll)f * np + T.b] - A0;
+                    gx[f] = (da * e2y - db * e1y) * idet;
+                    gy[f] = (db * e1x - da * e2x) * idet;
+                    al[f] = A0 + gx[f] * dsx + gy[f] * dty;  // A at the local origin
+                } else {
+                    gx[f] = gy[f] = al[f] = 0.0f;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float A1 = (c & 1) ? ox : 1.0f - ox, B1 = (c & 1) ? 1.0f : -1.0f;
+                const float A2 = (c & 2) ? oy : 1.0f - oy, B2 = (c & 2) ? 1.0f : -1.0f;
+                const float aa = A1 * A2, ab = A1 * B2, ba = B1 * A2, bb = B1 * B2;
+                const float K0 = aa * M00 + ab * M01 + ba * M10 + bb * M11;
+                const float K1 = aa * M10 + ab * M11 + ba * M20 + bb * M21;
+                const float K2 = aa * M01 + ab * M02 + ba * M11 + bb * M12;
+                const int nx = gcx + (c & 1), ny = gcy + ((c >> 1) & 1);
+                const int lx = nx - wx0, ly = ny - wy0;
+                const bool inwin = lx >= 0 && lx < RWIN && ly >= 0 && ly < RWIN;
+                const ll node = (ll)wrapi(ny, n) * n + wrapi(nx, n);
+#pragma unroll
+                for (int f = 0; f < FF; ++f) {
+                    if (f >= F) break;
+                    const float val = (al[f] * K0 + gx[f] * K1 + gy[f] * K2) * hd;
+                    const ll iv = __float2ll_rn(ldexpf(val, E[f]));
+                    if (!iv) continue;
+                    if (inwin)
+                        atomicAdd(&acc[f][ly * RWIN + lx], (ull)iv);
+                    else
+                        atomicAdd((ull *)&bfix[(ll)f * g.ncell + node], (ull)iv);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < RWIN * RWIN; i += blockDim.x) {
+        const int lx = i % RWIN, ly = i / RWIN;
+        const ll node = (ll)wrapi(wy0 + ly, n) * n + wrapi(wx0 + lx, n);
+        for (int f = 0; f < F && f < FF; ++f) {
+            ull v = acc[f][i];
+            if (v) atomicAdd((ull *)&bfix[(ll)f * g.ncell + node], v);
+        }
     }
 }
 
@@ -438,9 +563,16 @@ void launch_flip(const Geo &g, Work &w, ll np, int F, float *mesh_out, float *no
 void launch_rhs(const Geo &g, Work &w, ll np, int F, cudaStream_t st) {
     cudaMemsetAsync(w.bfix, 0, sizeof(ll) * g.ncell * F, st);
     if (np <= 0) return;
-    if (g.dim == 2)
-        k_rhs2d<<<div_up(np, 128), 128, 0, st>>>(g, np, w.pos, w.nbr, w.deg, w.vals, F, w.maxabs, w.bfix);
-    else
+    if (g.dim == 2) {
+        const int tx = div_up(g.n, RTS), nt = tx * tx;
+        if (F <= 2)
+            k_rhs2d<2><<<nt, 256, 0, st>>>(g, np, w.pos, w.cell_start, w.nbr, w.deg, w.vals, F, w.maxabs, w.bfix, tx);
+        else if (F <= 4)
+            k_rhs2d<4><<<nt, 256, 0, st>>>(g, np, w.pos, w.cell_start, w.nbr, w.deg, w.vals, F, w.maxabs, w.bfix, tx);
+        else
+            k_rhs2d<PM_MAXF><<<nt, 256, 0, st>>>(g, np, w.pos, w.cell_start, w.nbr, w.deg, w.vals, F, w.maxabs, w.bfix,
+                                                 tx);
+    } else
         k_rhs1d<<<div_up(np, 128), 128, 0, st>>>(g, np, w.pos, w.vals, F, w.maxabs, w.bfix);
     count_launches(1);
 }
