@@ -182,6 +182,33 @@ pm_status pm_advect_rk2(pm_ctx *ctx, const float *mesh_vel, const float *vel, fl
                         double dt, float *vals, int F, double factor);
 
 /* ---------------------------------------------------------------------------
+ * Allocation-free mass solve (no counterpart in the paper).
+ *
+ * For callers that cannot allocate device memory when they need the solve:
+ * work recorded into a CUDA graph by stream capture (cudaMalloc is not a
+ * stream-ordered operation), latency-critical loops that cannot afford the
+ * implicit device synchronisation of cudaMalloc/cudaFree, and host frameworks
+ * that own all device memory through their own pool. Same result as
+ * pm_mass_solve() (conjugate gradients on M x[f] = b[f], mean mode set
+ * exactly, true residual checked), but it needs no context: its scratch is
+ * one file-scope device array of about 16.2 MB that every GPU loading the
+ * library holds until exit. The caller passes b [F][n^dim] and x [F][n^dim]
+ * (device); x is the start vector when use_x0 != 0, else the solve starts
+ * from zero. Limit: F * n^dim <= 2^20 values (e.g. F = 1 at 1024^2, F = 4 at
+ * 512^2); larger sizes, dim not 1 or 2, n < 4, L <= 0 or F outside 1..8
+ * return PM_EINVAL before any GPU work. The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture. All calls share the one array, so calls whose
+ * work overlaps on the GPU (different streams or threads without ordering)
+ * race and give wrong results; serialise them. iters and rel_resid (host,
+ * F entries each, may be NULL) make the call wait for the stream and receive
+ * the iteration count and true relative residual per field; then
+ * PM_ENOTCONV / PM_ETIMEOUT are reported too. Errors are status codes only
+ * (there is no context for pm_last_error()). No call allocates memory. */
+pm_status pm_mass_solve_noalloc(int dim, int n, double L, const float *b, int F, float *x, double rtol, int max_iter,
+                                int use_x0, void *stream, int *iters, double *rel_resid);
+
+/* ---------------------------------------------------------------------------
  * Instrumentation (no counterpart in the paper).
  * ------------------------------------------------------------------------- */
 enum {
