@@ -182,6 +182,34 @@ pm_status pm_advect_rk2(pm_ctx *ctx, const float *mesh_vel, const float *vel, fl
                         double dt, float *vals, int F, double factor);
 
 /* ---------------------------------------------------------------------------
+ * Batches of independent instances (no counterpart in the paper: many
+ * periodic problems of uneven mesh and particle sizes advanced together).
+ * ------------------------------------------------------------------------- */
+typedef struct pm_batch pm_batch;
+/* ninst 2D instances; instance k has an n[k] x n[k] mesh of box length L[k]
+ * and up to max_np[k] particles (all host arrays). Creates one context per
+ * instance (all workspace allocated now) and the batch's own streams; stream
+ * is the caller's stream the batch synchronises with. streams = number of
+ * concurrent streams for the particle phases, 0 = choose by timing on the
+ * first call (1, 2, 4, 8 or 16). */
+pm_status pm_batch_create(pm_batch **out, int ninst, const int *n, const double *L, const long long *max_np,
+                          int max_fields, int streams, void *stream);
+void pm_batch_destroy(pm_batch *b);
+const char *pm_batch_last_error(const pm_batch *b);
+/* The chosen stream count and the step time measured when choosing it. */
+pm_status pm_batch_tuning(const pm_batch *b, int *streams, double *step_ms);
+/* Mass assignment (as pm_assign_mass, delta warm start) of every instance.
+ * px, py, vals, mesh_out are HOST arrays of ninst DEVICE pointers (instance
+ * k: px[k][np[k]], vals[k] [F][np[k]], mesh_out[k] [F][n[k]^2]); np is a host
+ * array. One step is captured into a CUDA graph (particle phases of all
+ * instances spread over the streams, then the solves in order) and replayed
+ * while the pointers, counts and options stay the same. info (host,
+ * ninst*F entries, instance-major, may be NULL) makes the call wait. */
+pm_status pm_batch_assign_mass(pm_batch *b, const float *const *px, const float *const *py, const long long *np,
+                               const float *const *vals, int F, float *const *mesh_out, double rtol, int max_iter,
+                               pm_solve_info *info);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free mass solve (no counterpart in the paper).
  *
  * For callers that cannot allocate device memory when they need the solve:

@@ -12,10 +12,11 @@ import ctypes
 import os
 from dataclasses import dataclass
 
-__all__ = ["Context", "PMError", "SolveInfo", "load_library", "library_path", "kernel_launches"]
+__all__ = ["Context", "Batch", "PMError", "SolveInfo", "load_library", "library_path", "kernel_launches"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIBPATH = os.path.join(_HERE, "_build", "libpmt.so")
+_LIBPATH = os.environ.get("PM_LIBRARY") or os.path.join(
+    _HERE, "_build_checked" if os.environ.get("PM_CHECKED") == "1" else "_build", "libpmt.so")
 _lib = None
 
 PM_WS_DELTA, PM_WS_ZERO, PM_WS_USER = 0, 1, 2
@@ -27,6 +28,7 @@ EXPORTS = [
     "pm_interpolate", "pm_assign_delta", "pm_assign_flip", "pm_assign_mass", "pm_mass_rhs", "pm_mass_apply",
     "pm_mass_solve", "pm_particle_volumes", "pm_triangulate", "pm_sort", "pm_advect_shift", "pm_advect_rotate",
     "pm_advect_rk2", "pm_profile", "pm_profile_read", "pm_phase_name", "pm_kernel_launches",
+    "pm_batch_create", "pm_batch_destroy", "pm_batch_last_error", "pm_batch_tuning", "pm_batch_assign_mass",
 ]
 PHASES = ["sort", "triangulate", "delta", "flip", "rhs", "solve", "g2p", "advect", "other"]
 
@@ -95,6 +97,11 @@ def load_library(path: str | None = None):
         "pm_profile_read": [vp, vp, vp, i],
         "pm_phase_name": [i],
         "pm_kernel_launches": [],
+        "pm_batch_create": [ctypes.POINTER(vp), i, vp, vp, vp, i, i, vp],
+        "pm_batch_destroy": [vp],
+        "pm_batch_last_error": [vp],
+        "pm_batch_tuning": [vp, ctypes.POINTER(i), ctypes.POINTER(d)],
+        "pm_batch_assign_mass": [vp, vp, vp, vp, vp, i, vp, d, i, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -102,6 +109,8 @@ def load_library(path: str | None = None):
         fn.restype = ctypes.c_int
     lib.pm_last_error.restype = ctypes.c_char_p
     lib.pm_phase_name.restype = ctypes.c_char_p
+    lib.pm_batch_last_error.restype = ctypes.c_char_p
+    lib.pm_batch_destroy.restype = None
     lib.pm_kernel_launches.restype = ctypes.c_longlong
     lib.pm_ctx_workspace_bytes.restype = ctypes.c_longlong
     lib.pm_ctx_destroy.restype = None
@@ -305,3 +314,53 @@ class Context:
         calls = (ctypes.c_longlong * len(PHASES))()
         self._check(self.lib.pm_profile_read(self.h, ms, calls, 1 if reset else 0))
         return {PHASES[k]: (ms[k], calls[k]) for k in range(len(PHASES))}
+
+
+class Batch:
+    """Many independent 2D instances advanced together (pm_batch_*)."""
+
+    def __init__(self, sizes, Ls, max_particles, max_fields=1, streams=0, device=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_1610_05258_gb300 needs a CUDA device (no CPU fallback)")
+        self.torch = torch
+        self.lib = load_library()
+        self.device = torch.device(device if device is not None else "cuda")
+        self.k = len(sizes)
+        self.sizes = list(sizes)
+        n = (ctypes.c_int * self.k)(*sizes)
+        L = (ctypes.c_double * self.k)(*Ls)
+        mp = (ctypes.c_longlong * self.k)(*max_particles)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = torch.cuda.current_stream().cuda_stream
+            s = self.lib.pm_batch_create(ctypes.byref(h), self.k, n, L, mp, max_fields, streams, ctypes.c_void_p(st))
+        if s != 0:
+            raise PMError(s, "pm_batch_create failed")
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.lib is not None:
+            self.lib.pm_batch_destroy(self.h)
+            self.h = None
+
+    def tuning(self):
+        s, ms = ctypes.c_int(0), ctypes.c_double(0.0)
+        self.lib.pm_batch_tuning(self.h, ctypes.byref(s), ctypes.byref(ms))
+        return s.value, ms.value
+
+    def assign_mass(self, pxs, pys, vals, outs, rtol=1e-6, max_iter=200, info=True):
+        K = self.k
+        arr = lambda ts: (ctypes.c_void_p * K)(*[t.data_ptr() for t in ts])
+        np_ = (ctypes.c_longlong * K)(*[t.numel() for t in pxs])
+        F = vals[0].numel() // max(1, pxs[0].numel())
+        inf = (_Info * (K * F))() if info else None
+        s = self.lib.pm_batch_assign_mass(self.h, arr(pxs), arr(pys), np_, arr(vals), F, arr(outs), rtol, max_iter,
+                                          inf)
+        if s != 0:
+            raise PMError(s, self.lib.pm_batch_last_error(self.h).decode())
+        if not info:
+            return None
+        return [[SolveInfo(x.iters, x.init_rel_resid, x.rel_resid, x.sum_particles, x.sum_mesh, x.cons_err)
+                 for x in inf[k * F:(k + 1) * F]] for k in range(K)]

@@ -11,10 +11,13 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-OUT = os.path.join(HERE, "_build")
+CHECKED = os.environ.get("PM_CHECKED") == "1"  # debugging build with index checks
+OUT = os.path.join(HERE, "_build_checked" if CHECKED else "_build")
 LIB = os.path.join(OUT, "libpmt.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", CSRC]
+if CHECKED:
+    FLAGS.append("-DPM_CHECKED")
 
 
 def _nvcc():

@@ -113,8 +113,24 @@ struct Phase {
     }
 };
 
+// PM_DEBUG_SYNC=1 in the environment: wait for the stream after every phase
+// so that an execution error is reported with the phase that caused it.
+bool debug_sync() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("PM_DEBUG_SYNC");
+        v = e && e[0] == '1';
+    }
+    return v == 1;
+}
+
 pm_status check_launch(pm_ctx *c, const char *where) {
     cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && debug_sync()) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(c->st, &cs);
+        if (cs == cudaStreamCaptureStatusNone) e = cudaStreamSynchronize(c->st);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, where);
     return PM_OK;
 }
@@ -135,6 +151,7 @@ pm_status prepare(pm_ctx *c, const float *px, const float *py, ll np, const floa
         Phase ph(c, PM_PH_SORT);
         launch_sort(c->g, c->w, px, py, np, vals, F, c->st);
     }
+    if (pm_status s = check_launch(c, "sort")) return s;
     if (need_tri) {
         Phase ph(c, PM_PH_TRIANGULATE);
         if (c->g.dim == 2)
@@ -142,7 +159,7 @@ pm_status prepare(pm_ctx *c, const float *px, const float *py, ll np, const floa
         else
             launch_volumes_1d(c->g, c->w, np, c->st);
     }
-    return check_launch(c, "prepare");
+    return check_launch(c, "particle functions");
 }
 
 }  // namespace
@@ -156,7 +173,7 @@ pm_status pm_ctx_create(pm_ctx **out, int dim, int n, double L, long long max_pa
     if ((dim != 1 && dim != 2) || n < 4 || !(L > 0.0) || max_particles < 0 || max_fields < 1 ||
         max_fields > PM_MAXF)
         return PM_EINVAL;
-    if (max_particles >= (1LL << 28)) return PM_EINVAL;
+    if (max_particles >= (1LL << 28) - 16) return PM_EINVAL;  // star entries: 28-bit index, top 16 reserved
     if (dim == 2 && (ll)n * n > (1LL << 30)) return PM_EINVAL;
     pm_ctx *c = new pm_ctx();
     c->bytes = 0;
@@ -310,6 +327,41 @@ static pm_status fill_info(pm_ctx *c, int F, pm_solve_info *info) {
     return s;
 }
 
+// Everything of a mass assignment before the solve: sort, particle
+// functions, particle sums, right-hand side and the warm start.
+static pm_status mass_front(pm_ctx *c, const float *px, const float *py, ll np, const float *vals, int F,
+                            float *mesh_out, const pm_solve_opts &o, bool &start) {
+    pm_status s;
+    if ((s = prepare(c, px, py, np, vals, F, true))) return s;
+    {
+        Phase ph(c, PM_PH_RHS);
+        launch_psum(c->g, c->w, np, F, c->st);
+        if ((s = check_launch(c, "particle sums"))) return s;
+        launch_rhs(c->g, c->w, np, F, c->st);
+        if ((s = check_launch(c, "right-hand side"))) return s;
+    }
+    start = true;
+    if (o.warm_start == PM_WS_DELTA) {
+        Phase ph(c, PM_PH_DELTA);
+        launch_delta(c->g, c->w, np, F, mesh_out, c->st);
+    } else if (o.warm_start == PM_WS_USER) {
+        cudaMemcpyAsync(mesh_out, o.x0, sizeof(float) * F * c->g.ncell, cudaMemcpyDeviceToDevice, c->st);
+    } else {
+        start = false;
+    }
+    return check_launch(c, "warm start");
+}
+
+static pm_status mass_solve_launch(pm_ctx *c, int F, float *mesh_out, bool start, const pm_solve_opts &o) {
+    int e;
+    {
+        Phase ph(c, PM_PH_SOLVE);
+        e = launch_cg(c->g, c->w, F, nullptr, true, mesh_out, start, o.rtol, o.max_iter, c->st);
+    }
+    if (e) return cuda_fail(c, (cudaError_t)e, "pm_assign_mass solve launch");
+    return check_launch(c, "solve");
+}
+
 pm_status pm_assign_mass(pm_ctx *c, const float *px, const float *py, long long np, const float *vals, int F,
                          float *mesh_out, const pm_solve_opts *opts, pm_solve_info *info) {
     pm_status s = check_particles(c, px, py, np, F, vals, c && c->g.dim == 2 ? 3 : 2);
@@ -318,27 +370,9 @@ pm_status pm_assign_mass(pm_ctx *c, const float *px, const float *py, long long 
     pm_solve_opts o;
     default_opts(opts, o);
     if (o.warm_start == PM_WS_USER && !o.x0) return fail(c, PM_EINVAL, "PM_WS_USER without x0");
-    if ((s = prepare(c, px, py, np, vals, F, true))) return s;
-    {
-        Phase ph(c, PM_PH_RHS);
-        launch_psum(c->g, c->w, np, F, c->st);
-        launch_rhs(c->g, c->w, np, F, c->st);
-    }
     bool start = true;
-    if (o.warm_start == PM_WS_DELTA) {
-        Phase ph(c, PM_PH_DELTA);
-        launch_delta(c->g, c->w, np, F, mesh_out, c->st);
-    } else if (o.warm_start == PM_WS_USER)
-        cudaMemcpyAsync(mesh_out, o.x0, sizeof(float) * F * c->g.ncell, cudaMemcpyDeviceToDevice, c->st);
-    else
-        start = false;
-    if ((s = check_launch(c, "pm_assign_mass"))) return s;
-    int e;
-    {
-        Phase ph(c, PM_PH_SOLVE);
-        e = launch_cg(c->g, c->w, F, nullptr, true, mesh_out, start, o.rtol, o.max_iter, c->st);
-    }
-    if (e) return cuda_fail(c, (cudaError_t)e, "pm_assign_mass solve launch");
+    if ((s = mass_front(c, px, py, np, vals, F, mesh_out, o, start))) return s;
+    if ((s = mass_solve_launch(c, F, mesh_out, start, o))) return s;
     if (info) return fill_info(c, F, info);
     return PM_OK;
 }
@@ -474,6 +508,238 @@ const char *pm_phase_name(int ph) {
 }
 
 long long pm_kernel_launches(void) { return g_launch_total.load(); }
+
+#ifdef PM_CHECKED
+}  // extern "C"
+void pm_dbg_fetch_sort(int *);
+void pm_dbg_fetch_delaunay(int *);
+void pm_dbg_fetch_transfer(int *);
+void pm_dbg_fetch_solve(int *);
+extern "C" {
+// Checked build only: first violated site code and violation count of each
+// file (sort, delaunay, transfer, solve), then reset.
+int pm_debug_read(int *out) {
+    pm_dbg_fetch_sort(out);
+    pm_dbg_fetch_delaunay(out + 2);
+    pm_dbg_fetch_transfer(out + 4);
+    pm_dbg_fetch_solve(out + 6);
+    return 0;
+}
+#endif
+
+// ---------------------------------------------------------------------------
+// Batches of independent instances
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct pm_batch {
+    int ninst = 0, F_max = 0, S = 0;
+    std::vector<pm_ctx *> ctx;
+    std::vector<cudaStream_t> streams;
+    cudaStream_t main = nullptr, user = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr, done = nullptr, t0 = nullptr, t1 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const void *> key;
+    double tuned_ms = 0.0;
+    long long graph_kernels = 0;  // kernels recorded in the captured step
+    std::string err;
+};
+
+namespace {
+
+pm_status bfail(pm_batch *b, pm_status s, const std::string &m) {
+    b->err = m;
+    return s;
+}
+
+// Queue one step for every instance: particle phases spread over S streams,
+// then every solve in order on the main stream (two persistent cooperative
+// grids never run at the same time).
+pm_status batch_enqueue(pm_batch *b, int S, const float *const *px, const float *const *py, const ll *np,
+                        const float *const *vals, int F, float *const *mesh, const pm_solve_opts &o,
+                        std::vector<char> &start) {
+    cudaEventRecord(b->fork, b->main);
+    for (int j = 0; j < S; ++j) cudaStreamWaitEvent(b->streams[j], b->fork, 0);
+    for (int k = 0; k < b->ninst; ++k) {
+        pm_ctx *c = b->ctx[k];
+        c->st = b->streams[k % S];
+        bool st = true;
+        pm_status s = mass_front(c, px[k], py[k], np[k], vals[k], F, mesh[k], o, st);
+        if (s) return bfail(b, s, c->err);
+        start[k] = st;
+    }
+    for (int j = 0; j < S; ++j) {
+        cudaEventRecord(b->join[j], b->streams[j]);
+        cudaStreamWaitEvent(b->main, b->join[j], 0);
+    }
+    for (int k = 0; k < b->ninst; ++k) {
+        pm_ctx *c = b->ctx[k];
+        c->st = b->main;
+        pm_status s = mass_solve_launch(c, F, mesh[k], start[k] != 0, o);
+        if (s) return bfail(b, s, c->err);
+    }
+    return PM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pm_status pm_batch_create(pm_batch **out, int ninst, const int *n, const double *L, const long long *max_np,
+                          int max_fields, int streams, void *stream) {
+    if (!out || ninst < 1 || !n || !L || !max_np || streams < 0 || streams > 32) return PM_EINVAL;
+    *out = nullptr;
+    pm_batch *b = new pm_batch();
+    b->ninst = ninst;
+    b->F_max = max_fields;
+    b->S = streams;
+    b->user = (cudaStream_t)stream;
+    const int smax = 32;
+    bool ok = cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) == cudaSuccess;
+    for (int j = 0; ok && j < smax; ++j) {
+        cudaStream_t s;
+        cudaEvent_t e;
+        ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+        if (ok) {
+            b->streams.push_back(s);
+            b->join.push_back(e);
+        }
+    }
+    ok = ok && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreate(&b->t0) == cudaSuccess && cudaEventCreate(&b->t1) == cudaSuccess;
+    for (int k = 0; ok && k < ninst; ++k) {
+        pm_ctx *c = nullptr;
+        pm_status s = pm_ctx_create(&c, 2, n[k], L[k], max_np[k], max_fields, b->main);
+        if (s) {
+            pm_batch_destroy(b);
+            return s;
+        }
+        b->ctx.push_back(c);
+    }
+    if (!ok) {
+        pm_batch_destroy(b);
+        return PM_ECUDA;
+    }
+    *out = b;
+    return PM_OK;
+}
+
+void pm_batch_destroy(pm_batch *b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (pm_ctx *c : b->ctx) pm_ctx_destroy(c);
+    for (auto s : b->streams) cudaStreamDestroy(s);
+    for (auto e : b->join) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->t0) cudaEventDestroy(b->t0);
+    if (b->t1) cudaEventDestroy(b->t1);
+    if (b->main) cudaStreamDestroy(b->main);
+    delete b;
+}
+
+const char *pm_batch_last_error(const pm_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+pm_status pm_batch_tuning(const pm_batch *b, int *streams, double *step_ms) {
+    if (!b) return PM_EINVAL;
+    if (streams) *streams = b->S;
+    if (step_ms) *step_ms = b->tuned_ms;
+    return PM_OK;
+}
+
+pm_status pm_batch_assign_mass(pm_batch *b, const float *const *px, const float *const *py, const long long *np,
+                               const float *const *vals, int F, float *const *mesh_out, double rtol, int max_iter,
+                               pm_solve_info *info) {
+    if (!b || !px || !py || !np || !vals || !mesh_out || F < 1 || F > b->F_max) return PM_EINVAL;
+    for (int k = 0; k < b->ninst; ++k) {
+        pm_status s = check_particles(b->ctx[k], px[k], py[k], np[k], F, vals[k], 3);
+        if (s) return bfail(b, s, "instance " + std::to_string(k) + ": " + b->ctx[k]->err);
+        if (!mesh_out[k]) return bfail(b, PM_EINVAL, "null output");
+    }
+    pm_solve_opts o;
+    o.warm_start = PM_WS_DELTA;
+    o.rtol = rtol > 0.0 ? rtol : 1e-6;
+    o.max_iter = max_iter > 0 ? max_iter : 200;
+    o.x0 = nullptr;
+    std::vector<char> start(b->ninst, 1);
+    // the main stream follows the caller's stream
+    cudaEventRecord(b->fork, b->user);
+    cudaStreamWaitEvent(b->main, b->fork, 0);
+    // autotune the number of concurrent streams once (timed, not captured)
+    if (b->S == 0) {
+        double best = 1e30;
+        int bestS = 1;
+        for (int S : {1, 2, 4, 8, 16}) {
+            for (int rep = 0; rep < 2; ++rep) {
+                cudaEventRecord(b->t0, b->main);
+                pm_status s = batch_enqueue(b, S, px, py, np, vals, F, mesh_out, o, start);
+                if (s) return s;
+                cudaEventRecord(b->t1, b->main);
+            }
+            if (cudaEventSynchronize(b->t1) != cudaSuccess) return bfail(b, PM_ECUDA, "autotune");
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, b->t0, b->t1);
+            if (ms < best) {
+                best = ms;
+                bestS = S;
+            }
+        }
+        b->S = bestS;
+        b->tuned_ms = best;
+    }
+    // capture one step into a CUDA graph, replay it while the arguments match
+    std::vector<const void *> key;
+    key.push_back((const void *)(ll)F);
+    for (int k = 0; k < b->ninst; ++k) {
+        key.push_back(px[k]);
+        key.push_back(py[k]);
+        key.push_back(vals[k]);
+        key.push_back(mesh_out[k]);
+        key.push_back((const void *)np[k]);
+    }
+    key.push_back((const void *)(ll)(o.max_iter));
+    key.push_back((const void *)(ll)(o.rtol * 1e12));
+    if (!b->exec || key != b->key) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+        cudaError_t ce = cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal);
+        if (ce != cudaSuccess) return bfail(b, PM_ECUDA, std::string("capture: ") + cudaGetErrorString(ce));
+        const long long l0 = g_launch_total.load();
+        pm_status s = batch_enqueue(b, b->S, px, py, np, vals, F, mesh_out, o, start);
+        b->graph_kernels = g_launch_total.load() - l0;
+        g_launch_total -= b->graph_kernels;  // counted when the graph runs
+        ce = cudaStreamEndCapture(b->main, &b->graph);
+        if (s) return s;
+        if (ce != cudaSuccess) return bfail(b, PM_ECUDA, std::string("end capture: ") + cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&b->exec, b->graph, 0);
+        if (ce != cudaSuccess) return bfail(b, PM_ECUDA, std::string("instantiate: ") + cudaGetErrorString(ce));
+        b->key = key;
+    }
+    cudaError_t ce = cudaGraphLaunch(b->exec, b->main);
+    if (ce != cudaSuccess) return bfail(b, PM_ECUDA, std::string("graph launch: ") + cudaGetErrorString(ce));
+    count_launches((int)b->graph_kernels);
+    cudaEventRecord(b->done, b->main);
+    cudaStreamWaitEvent(b->user, b->done, 0);
+    if (!info) return PM_OK;
+    pm_status worst = PM_OK;
+    for (int k = 0; k < b->ninst; ++k) {
+        pm_ctx *c = b->ctx[k];
+        c->st = b->main;
+        pm_status s = fill_info(c, F, info + (ll)k * F);
+        if (s && !worst) {
+            worst = s;
+            b->err = "instance " + std::to_string(k) + ": " + c->err;
+        }
+    }
+    return worst;
+}
 
 pm_status pm_sort(pm_ctx *c, const float *px, const float *py, long long np, int *perm_out, int *cell_start_out) {
     pm_status s = check_particles(c, px, py, np, 0, nullptr, 0);

@@ -20,6 +20,8 @@
 // agree: every triangle (p, a, b) appears in the stars of p, a and b.
 #include "internal.cuh"
 
+PM_DEBUG_DECL(delaunay)
+
 namespace {
 
 __device__ __forceinline__ int sgn_ll(ll v) { return (v > 0) - (v < 0); }
@@ -56,8 +58,13 @@ __device__ __noinline__ bool incircle_exact(int ax, int ay, int bx, int by, int 
     return false;
 }
 
+// Star entries carry the sorted index in the low 28 bits and the image code
+// in the high 4 (so real entries may be negative as ints); the four virtual
+// points of the initial cell use the indices PM_VIRT..PM_VIRT+3 and rank last.
+#define PM_VIRT 0x0ffffff0
 __device__ __forceinline__ int prio(int enc, const int *__restrict__ perm) {
-    return enc >= 0 ? perm[enc & 0x0fffffff] : 0x7fffffff + enc;  // virtual points rank last
+    const int id = enc & 0x0fffffff;
+    return id >= PM_VIRT ? 0x7ffffff0 + (id - PM_VIRT) : __ldg(perm + id);
 }
 
 #define DBLK 64  // threads per block of the triangulation kernel
@@ -158,6 +165,7 @@ __device__ __forceinline__ int clip_by(PolyS P, int &m, float &R2, int sx, int s
     const int i0 = __ffs(starts) - 1;  // first removed vertex; q_i0 is kept
     const int nd = cnt - 1;            // neighbours q_{i0+1..i0+nd} are removed
     if (m - nd + 1 > DMAXW) return ST_DEGREE;
+    PM_CHK(m + 1 <= DMAXW, 204, return ST_DEGREE)
     const int4 S = make_int4(sx, sy, sidx | (code << 28), 0);
     int ipos;
     if (i0 + nd < m) {
@@ -219,13 +227,18 @@ __global__ void __launch_bounds__(DBLK) k_delaunay(Geo g, ll np, const uint2 *__
     const int n = g.n;
     PolyS P{sq, sv, t};
     int m = 4;
-    const int B = 1 << 29;
+    // Initial cell: the square cut out by four virtual points at distance
+    // B = 2^30, the largest coordinate the exact predicates take. A vertex
+    // involving a virtual point is at least 2^29 from p, which the scan
+    // (< 2^30) can never certify, so a certified cell is bounded by real
+    // particles only; a cell still touching a virtual point after the last
+    // ring is reported as ST_SPARSE.
+    const int B = 1 << 30;
     const float hb = 0.5f * (float)B;
-    // initial cell: the square cut out by four virtual points at distance B
-    sq[0][t] = make_int4(B, 0, -1, 0);
-    sq[1][t] = make_int4(0, B, -2, 0);
-    sq[2][t] = make_int4(-B, 0, -3, 0);
-    sq[3][t] = make_int4(0, -B, -4, 0);
+    sq[0][t] = make_int4(B, 0, PM_VIRT + 0, 0);
+    sq[1][t] = make_int4(0, B, PM_VIRT + 1, 0);
+    sq[2][t] = make_int4(-B, 0, PM_VIRT + 2, 0);
+    sq[3][t] = make_int4(0, -B, PM_VIRT + 3, 0);
     sv[0][t] = make_float2(hb, hb);
     sv[1][t] = make_float2(-hb, hb);
     sv[2][t] = make_float2(-hb, -hb);
@@ -254,7 +267,9 @@ __global__ void __launch_bounds__(DBLK) k_delaunay(Geo g, ll np, const uint2 *__
             else { dx = r; dy = ci - (7 * r); }
             int ox, oy, c = nb_cell(cx, cy, dx, dy, n, ox, oy);
             const int code = (ox + 1) * 3 + (oy + 1);
+            PM_CHK(c >= 0 && c < g.ncell, 201, continue)
             const int s0 = __ldg(cell_start + c), s1 = __ldg(cell_start + c + 1);
+            PM_CHK(s0 >= 0 && s1 <= np && s0 <= s1, 202, continue)
             for (int s = s0; s < s1; ++s) {
                 if (s == p) continue;
                 const uint2 Xs = __ldg(pos + s);
@@ -269,6 +284,8 @@ __global__ void __launch_bounds__(DBLK) k_delaunay(Geo g, ll np, const uint2 *__
         if (4.0001f * R2 < dmin * dmin) done = true;
     }
     if (!done && !err) err |= ST_SPARSE;
+    for (int k = 0; k < m && !err; ++k)
+        if ((sq[k][t].z & 0x0fffffff) >= PM_VIRT) err |= ST_SPARSE;
     if (m > PM_MAXDEG) err |= ST_DEGREE;
     if (err) {
         atomicOr(status, err);
@@ -277,6 +294,7 @@ __global__ void __launch_bounds__(DBLK) k_delaunay(Geo g, ll np, const uint2 *__
         return;
     }
     ll area2 = 0;
+    PM_CHK(m >= 3 && m <= PM_MAXDEG, 203, return)
     int4 A = sq[0][t];
     for (int k = 0; k < m; ++k) {
         int4 Bq = sq[k + 1 == m ? 0 : k + 1][t];

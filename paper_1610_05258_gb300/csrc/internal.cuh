@@ -127,6 +127,28 @@ struct Dot2 {
 
 static inline int div_up(ll a, int b) { return (int)((a + b - 1) / b); }
 
+// Checked build (-DPM_CHECKED, a debugging aid): every data-derived index is
+// validated; the first violation's site code is recorded in a per-file
+// device word and the access is skipped (`action` is return/continue/break).
+#ifdef PM_CHECKED
+#define PM_DEBUG_DECL(tu)                                                        \
+    static __device__ int pm_dbg_word[2];                                       \
+    void pm_dbg_fetch_##tu(int *o) {                                            \
+        cudaMemcpyFromSymbol(o, pm_dbg_word, 2 * sizeof(int));                  \
+        int z[2] = {0, 0};                                                      \
+        cudaMemcpyToSymbol(pm_dbg_word, z, 2 * sizeof(int));                    \
+    }
+#define PM_CHK(cond, code, action)                   \
+    if (!(cond)) {                                   \
+        atomicCAS(&pm_dbg_word[0], 0, (code));       \
+        atomicAdd(&pm_dbg_word[1], 1);               \
+        action;                                      \
+    }
+#else
+#define PM_DEBUG_DECL(tu)
+#define PM_CHK(cond, code, action)
+#endif
+
 // Process-wide count of kernel launches issued by the library (each launcher
 // adds the number of kernels it queued).
 void count_launches(int k);

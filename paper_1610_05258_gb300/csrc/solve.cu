@@ -20,6 +20,8 @@
 
 #include "internal.cuh"
 
+PM_DEBUG_DECL(solve)
+
 namespace {
 
 struct CG {
@@ -86,6 +88,7 @@ __device__ void block_partial(double v[PM_MAXF], int F, double *red, int slot) {
     if (threadIdx.x < F) {
         double s = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[threadIdx.x][w];
+        PM_CHK((ll)(slot * F + threadIdx.x + 1) * gridDim.x <= 6LL * PM_MAXF * 1024, 401, s = 0)
         red[(ll)(slot * F + threadIdx.x) * gridDim.x + blockIdx.x] = s;
     }
     __syncthreads();

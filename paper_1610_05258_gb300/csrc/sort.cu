@@ -9,6 +9,8 @@
 // order, so the result is deterministic.
 #include "internal.cuh"
 
+PM_DEBUG_DECL(sort)
+
 namespace {
 
 __global__ void k_key(Geo g, const float *__restrict__ px, const float *__restrict__ py, ll np,
@@ -27,6 +29,7 @@ __global__ void k_key(Geo g, const float *__restrict__ px, const float *__restri
     uint32_t Y = g.dim == 2 ? torus_coord(y, g.invL) : 0u;
     int c = cell_of(X, g.n);
     if (g.dim == 2) c += cell_of(Y, g.n) * g.n;
+    PM_CHK(c >= 0 && c < g.ncell, 101, return)
     fx[k] = make_uint2(X, Y);
     key[k] = c;
     slot[k] = atomicAdd(&count[c], 1);
@@ -102,6 +105,8 @@ __global__ void k_place(ll np, const int *__restrict__ key, const int *__restric
                         const int *__restrict__ cell_start, int *__restrict__ tmp) {
     ll k = (ll)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= np) return;
+    PM_CHK(key[k] >= 0, 102, return)
+    PM_CHK((ll)cell_start[key[k]] + slot[k] < np, 103, return)
     tmp[cell_start[key[k]] + slot[k]] = (int)k;
 }
 
@@ -117,6 +122,7 @@ __global__ void k_canon(Geo g, ll np, const int *__restrict__ cell_start, int *_
     bool bad = false;
     if (c < g.ncell) {
         int s0 = cell_start[c], s1 = cell_start[c + 1];
+        PM_CHK(s0 >= 0 && s0 <= s1 && s1 <= np, 104, s1 = s0)
         for (int i = s0 + 1; i < s1; ++i) {
             int v = tmp[i];
             uint32_t xv = g.dim == 1 ? fx[v].x : 0u;
@@ -138,6 +144,7 @@ __global__ void k_canon(Geo g, ll np, const int *__restrict__ cell_start, int *_
         }
         for (int s = s0; s < s1; ++s) {
             int idx = tmp[s];
+            PM_CHK(idx >= 0 && idx < np, 105, continue)
             perm[s] = idx;
             pos[s] = fx[idx];
             for (int f = 0; f < F; ++f) {

@@ -11,6 +11,10 @@
 // sum does not depend on the order of the atomic additions.
 #include "internal.cuh"
 
+#define PM_VIRT_LIMIT 0x0ffffff0
+
+PM_DEBUG_DECL(transfer)
+
 namespace {
 
 __device__ __forceinline__ void decode(int e, int &id, int &ox, int &oy) {
@@ -24,6 +28,7 @@ __device__ __forceinline__ void decode(int e, int &id, int &ox, int &oy) {
 __device__ __forceinline__ void rel_of(int e, uint2 Xp, const uint2 *__restrict__ pos, int &id, ll &rx, ll &ry) {
     int ox, oy;
     decode(e, id, ox, oy);
+    PM_CHK(id >= 0 && id < PM_VIRT_LIMIT, 301, id = 0)
     uint2 Xq = pos[id];
     rx = (ll)Xq.x + (ll)ox * 4294967296LL - (ll)Xp.x;
     ry = (ll)Xq.y + (ll)oy * 4294967296LL - (ll)Xp.y;
@@ -85,6 +90,7 @@ __global__ void __launch_bounds__(128) k_delta2d(Geo g, ll np, const uint2 *__re
                     float lb = (fax * fqy - fay * fqx) / D;  // weight of b
                     float lp = 1.0f - la - lb;
                     const ll node = (ll)wrapi((int)(j % n), n) * n + wrapi((int)(i % n), n);
+                    PM_CHK(node >= 0 && node < g.ncell && ida < np && idb < np, 302, continue)
                     for (int f = 0; f < F; ++f) {
                         const float *v = vals + (ll)f * np;
                         mesh[(ll)f * g.ncell + node] = lp * v[p] + la * v[ida] + lb * v[idb];
@@ -346,6 +352,7 @@ __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__rest
             int r = 0;
             while (rowpre[r + 1] <= k) ++r;
             p = rowbeg[r] + (k - rowpre[r]);
+            PM_CHK(p >= 0 && p < np, 303, p = 0)
             const int m = deg[p];
             if (m >= 3) {
                 const uint2 Xp = pos[p];
@@ -377,6 +384,7 @@ __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__rest
             const int jj = j - __shfl_sync(0xffffffffu, excl, src);
             if (j >= T_all) continue;
             // locate the piece inside particle ps
+            PM_CHK(ps >= 0 && ps < np, 304, continue)
             const int m = deg[ps];
             const uint2 Xp = pos[ps];
             const int cxp = cell_of(Xp.x, n), cyp = cell_of(Xp.y, n);
@@ -396,6 +404,7 @@ __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__rest
                 }
             }
             if (!found) continue;
+            PM_CHK(T.a >= 0 && T.a < np && T.b >= 0 && T.b < np, 305, continue)
             const float fci = (float)ci, fcj = (float)cj;
             const float xmin = fminf(T.vx[0], fminf(T.vx[1], T.vx[2])), xmax = fmaxf(T.vx[0], fmaxf(T.vx[1], T.vx[2]));
             const float ymin = fminf(T.vy[0], fminf(T.vy[1], T.vy[2])), ymax = fmaxf(T.vy[0], fmaxf(T.vy[1], T.vy[2]));
@@ -440,6 +449,7 @@ __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__rest
                 const int lx = nx - wx0, ly = ny - wy0;
                 const bool inwin = lx >= 0 && lx < RWIN && ly >= 0 && ly < RWIN;
                 const ll node = (ll)wrapi(ny, n) * n + wrapi(nx, n);
+                PM_CHK(node >= 0 && node < g.ncell, 306, continue)
 #pragma unroll
                 for (int f = 0; f < FF; ++f) {
                     if (f >= F) break;

@@ -133,12 +133,16 @@ def sample_grid_field(f, L, x, y):
     return (f[j0, i0] * (1 - s) * (1 - t) + f[j0, i1] * s * (1 - t) + f[j1, i0] * (1 - s) * t + f[j1, i1] * s * t)
 
 
-def uniform_instance(n, ppc, F=3, seed=16104, L=1.0, slope=-3.0):
+def uniform_instance(n, ppc, F=3, seed=16104, L=1.0, slope=-3.0, field_grid=128):
+    """Uniform random particles, F smooth Gaussian random fields (spectral
+    slope `slope`) generated on a min(n, field_grid)^2 grid and sampled at
+    the particles."""
     g = rng(seed)
     npart = max(16, int(round(ppc * n * n)))
     x = g.uniform(0.0, L, npart).astype(np.float32)
     y = g.uniform(0.0, L, npart).astype(np.float32)
-    vals = np.stack([sample_grid_field(random_phase_field(n, slope, seed * 7 + f, L), L, x, y) for f in range(F)])
+    m = min(n, field_grid)
+    vals = np.stack([sample_grid_field(random_phase_field(m, slope, seed * 7 + f, L), L, x, y) for f in range(F)])
     return Instance(2, n, L, x, y, vals.astype(np.float32), name=f"uniform_n{n}_ppc{ppc}")
 
 

@@ -32,6 +32,10 @@ CASES_2D = [
     ("uniform_n64_ppc7", lambda: W.uniform_instance(64, 7, F=3, seed=103)),
     ("zalesak_n48", lambda: W.zalesak(48, seed=104)),
     ("taylor_green_n33", lambda: W.taylor_green(33, 4, seed=105)),
+    # small, sparse boxes: Voronoi cells reaching far rings (regression: a
+    # star must never keep a virtual bounding point)
+    ("uniform_n24_ppc1", lambda: W.uniform_instance(24, 1, F=2, seed=500)),
+    ("uniform_n17_ppc5", lambda: W.uniform_instance(17, 5, F=2, seed=505)),
 ]
 CASES_1D = [
     ("tophat_128", lambda: W.tophat_1d(128, 128, seed=16101)),
