@@ -60,7 +60,9 @@ typedef enum pm_status {
 
 typedef struct pm_ctx pm_ctx;
 
-enum { PM_WS_DELTA = 0, PM_WS_ZERO = 1, PM_WS_USER = 2 };
+enum { PM_WS_DELTA = 0, PM_WS_ZERO = 1, PM_WS_USER = 2, PM_WS_NET = 3 };
+
+typedef struct pm_net pm_net;
 
 /* Options of the mass solve  M Ab = b  (Sec. 2.4, Eq. phi_def). */
 typedef struct pm_solve_opts {
@@ -69,6 +71,7 @@ typedef struct pm_solve_opts {
     double rtol;     /* stop when ||b - M Ab||_2 <= rtol ||b||_2 (default 1e-6)  */
     int max_iter;    /* iteration cap (default 200)                              */
     const float *x0; /* device [F][n^dim], read when warm_start == PM_WS_USER     */
+    pm_net *net;     /* PM_WS_NET: start from delta + the network's correction    */
 } pm_solve_opts;
 
 /* Per-field report of a mass solve (host memory, one entry per field). */
@@ -182,6 +185,43 @@ pm_status pm_advect_rk2(pm_ctx *ctx, const float *mesh_vel, const float *vel, fl
                         double dt, float *vals, int F, double factor);
 
 /* ---------------------------------------------------------------------------
+ * Learned warm start (no counterpart in the paper: a small network predicts
+ * the mass assignment of Sec. 2.4 from the delta assignment, Eq. delta, and
+ * the FLIP node volume, Eq. FLIP_vol; conjugate gradients then finish the
+ * solve to the requested residual, so the result keeps the solver's
+ * guarantees whatever the network predicts).
+ *
+ * Network: 3x3 periodic convolutions 2 -> 32 -> 32 -> 32 -> 1, bias, ReLU
+ * after the first three; BF16 activations, FP32 accumulation; the 32 -> 32
+ * layers run on the tensor cores. Meshes must be 2D with n a multiple of 128.
+ * Parameters: pm_net_num_params() floats, per layer W [Co][Ci][3][3] then
+ * b [Co], tap (dy, dx) at [dy + 1][dx + 1] reading x[y + dy][x + dx].
+ * ------------------------------------------------------------------------- */
+int pm_net_num_params(void);
+/* Allocate a network for up to max_batch images of up to max_n x max_n. */
+pm_status pm_net_create(pm_net **out, int max_n, int max_batch, void *stream);
+void pm_net_destroy(pm_net *net);
+pm_status pm_net_set_stream(pm_net *net, void *stream);
+/* Checkpoint: parameters, then the two Adam moments (3 * pm_net_num_params()
+ * host floats) and the step count. */
+pm_status pm_net_state(pm_net *net, float *host_out, long long *step);
+/* Restore parameters (and the Adam moments if with_moments) and the step. */
+pm_status pm_net_load(pm_net *net, const float *host_in, int with_moments, long long step);
+/* out [B][n][n] = network(x [B][2][n][n]) (device). */
+pm_status pm_net_forward(pm_net *net, const float *x, int B, int n, float *out);
+/* One Adam step (learning rate lr) on 0.5 mean((network(x) - target)^2);
+ * loss (host, may be NULL) receives the loss before the step and makes the
+ * call wait. */
+pm_status pm_net_train_step(pm_net *net, const float *x, const float *target, int B, int n, float lr, double *loss);
+/* Gradient of the last training step (host, pm_net_num_params() floats). */
+pm_status pm_net_grad(pm_net *net, float *host_out);
+/* Network input of a mass assignment: delta assignment delta_out [F][n^2],
+ * features feat_out [F][2][n^2] (delta / max|A_f|, FLIP node volume / h^2
+ * - 1) and, if scale_out (host, F floats) is given, max|A_f| (waits). */
+pm_status pm_net_features(pm_ctx *ctx, const float *px, const float *py, long long np, const float *vals, int F,
+                          float *delta_out, float *feat_out, float *scale_out);
+
+/* ---------------------------------------------------------------------------
  * Batches of independent instances (no counterpart in the paper: many
  * periodic problems of uneven mesh and particle sizes advanced together).
  * ------------------------------------------------------------------------- */
@@ -249,7 +289,8 @@ enum {
     PM_PH_G2P = 6,
     PM_PH_ADVECT = 7,
     PM_PH_OTHER = 8,
-    PM_NPHASE = 9
+    PM_PH_NET = 9,         /* learned warm start: network inference */
+    PM_NPHASE = 10
 };
 /* When enabled, every phase's kernels are bracketed by CUDA events recorded
  * on the context's stream; pm_profile_read() waits for the stream and returns

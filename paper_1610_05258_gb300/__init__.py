@@ -12,14 +12,14 @@ import ctypes
 import os
 from dataclasses import dataclass
 
-__all__ = ["Context", "Batch", "PMError", "SolveInfo", "load_library", "library_path", "kernel_launches"]
+__all__ = ["Context", "Batch", "Net", "PMError", "SolveInfo", "load_library", "library_path", "kernel_launches"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBPATH = os.environ.get("PM_LIBRARY") or os.path.join(
     _HERE, "_build_checked" if os.environ.get("PM_CHECKED") == "1" else "_build", "libpmt.so")
 _lib = None
 
-PM_WS_DELTA, PM_WS_ZERO, PM_WS_USER = 0, 1, 2
+PM_WS_DELTA, PM_WS_ZERO, PM_WS_USER, PM_WS_NET = 0, 1, 2, 3
 _STATUS = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ENOTCONV", 4: "PM_ETIMEOUT", 5: "PM_EDEGENERATE",
            6: "PM_ECUDA"}
 
@@ -29,8 +29,10 @@ EXPORTS = [
     "pm_mass_solve", "pm_particle_volumes", "pm_triangulate", "pm_sort", "pm_advect_shift", "pm_advect_rotate",
     "pm_advect_rk2", "pm_profile", "pm_profile_read", "pm_phase_name", "pm_kernel_launches",
     "pm_batch_create", "pm_batch_destroy", "pm_batch_last_error", "pm_batch_tuning", "pm_batch_assign_mass",
+    "pm_net_num_params", "pm_net_create", "pm_net_destroy", "pm_net_set_stream", "pm_net_state", "pm_net_load",
+    "pm_net_forward", "pm_net_train_step", "pm_net_grad", "pm_net_features",
 ]
-PHASES = ["sort", "triangulate", "delta", "flip", "rhs", "solve", "g2p", "advect", "other"]
+PHASES = ["sort", "triangulate", "delta", "flip", "rhs", "solve", "g2p", "advect", "other", "net"]
 
 
 class PMError(RuntimeError):
@@ -41,7 +43,7 @@ class PMError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("warm_start", ctypes.c_int), ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("x0", ctypes.c_void_p)]
+                ("x0", ctypes.c_void_p), ("net", ctypes.c_void_p)]
 
 
 class _Info(ctypes.Structure):
@@ -102,6 +104,16 @@ def load_library(path: str | None = None):
         "pm_batch_last_error": [vp],
         "pm_batch_tuning": [vp, ctypes.POINTER(i), ctypes.POINTER(d)],
         "pm_batch_assign_mass": [vp, vp, vp, vp, vp, i, vp, d, i, vp],
+        "pm_net_num_params": [],
+        "pm_net_create": [ctypes.POINTER(vp), i, i, vp],
+        "pm_net_destroy": [vp],
+        "pm_net_set_stream": [vp, vp],
+        "pm_net_state": [vp, vp, ctypes.POINTER(ll)],
+        "pm_net_load": [vp, vp, i, ll],
+        "pm_net_forward": [vp, vp, i, i, vp],
+        "pm_net_train_step": [vp, vp, vp, i, i, ctypes.c_float, ctypes.POINTER(d)],
+        "pm_net_grad": [vp, vp],
+        "pm_net_features": [vp, vp, vp, ll, vp, i, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -111,6 +123,7 @@ def load_library(path: str | None = None):
     lib.pm_phase_name.restype = ctypes.c_char_p
     lib.pm_batch_last_error.restype = ctypes.c_char_p
     lib.pm_batch_destroy.restype = None
+    lib.pm_net_destroy.restype = None
     lib.pm_kernel_launches.restype = ctypes.c_longlong
     lib.pm_ctx_workspace_bytes.restype = ctypes.c_longlong
     lib.pm_ctx_destroy.restype = None
@@ -211,16 +224,18 @@ class Context:
                                             _ptr(node_volume), ctypes.byref(e) if count_empty else None))
         return (out, e.value) if count_empty else out
 
-    def _opts(self, warm_start, rtol, max_iter, x0):
-        ws = {"delta": PM_WS_DELTA, "zero": PM_WS_ZERO, "user": PM_WS_USER}[warm_start]
-        return _Opts(ws, rtol, max_iter, x0.data_ptr() if x0 is not None else None)
+    def _opts(self, warm_start, rtol, max_iter, x0, net=None):
+        ws = {"delta": PM_WS_DELTA, "zero": PM_WS_ZERO, "user": PM_WS_USER, "net": PM_WS_NET}[warm_start]
+        return _Opts(ws, rtol, max_iter, x0.data_ptr() if x0 is not None else None, net.h.value if net else None)
 
     def assign_mass(self, px, py, vals, out=None, warm_start="delta", rtol=1e-6, max_iter=200, x0=None,
-                    info=True):
+                    info=True, net=None):
         px, py, vals, x0 = self._f32(px), self._f32(py), self._f32(vals), self._f32(x0)
         F = vals.numel() // max(1, px.numel())
         out = out if out is not None else self._empty(F, self.nodes)
-        o = self._opts(warm_start, rtol, max_iter, x0)
+        if net is not None:
+            warm_start = "net"
+        o = self._opts(warm_start, rtol, max_iter, x0, net)
         inf = (_Info * F)() if info else None
         self._stream()
         s = self.lib.pm_assign_mass(self.h, _ptr(px), _ptr(py), px.numel(), _ptr(vals), F, _ptr(out),
@@ -230,6 +245,18 @@ class Context:
             return out
         return out, [SolveInfo(x.iters, x.init_rel_resid, x.rel_resid, x.sum_particles, x.sum_mesh, x.cons_err)
                      for x in inf]
+
+    def net_features(self, px, py, vals):
+        """(delta [F, n^2], features [F, 2, n^2], max|A_f| list) for the network."""
+        px, py, vals = self._f32(px), self._f32(py), self._f32(vals)
+        F = vals.numel() // max(1, px.numel())
+        delta = self._empty(F, self.nodes)
+        feat = self._empty(F, 2, self.nodes)
+        scale = (ctypes.c_float * F)()
+        self._stream()
+        self._check(self.lib.pm_net_features(self.h, _ptr(px), _ptr(py), px.numel(), _ptr(vals), F, _ptr(delta),
+                                             _ptr(feat), scale))
+        return delta, feat, list(scale)
 
     def mass_rhs(self, px, py, vals, out=None):
         px, py, vals = self._f32(px), self._f32(py), self._f32(vals)
@@ -364,3 +391,80 @@ class Batch:
             return None
         return [[SolveInfo(x.iters, x.init_rel_resid, x.rel_resid, x.sum_particles, x.sum_mesh, x.cons_err)
                  for x in inf[k * F:(k + 1) * F]] for k in range(K)]
+
+
+class Net:
+    """The learned warm start's network (pm_net_*)."""
+
+    def __init__(self, max_n, max_batch=1, device=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_1610_05258_gb300 needs a CUDA device (no CPU fallback)")
+        self.torch = torch
+        self.lib = load_library()
+        self.device = torch.device(device if device is not None else "cuda")
+        self.num_params = self.lib.pm_net_num_params()
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = torch.cuda.current_stream().cuda_stream
+            s = self.lib.pm_net_create(ctypes.byref(h), max_n, max_batch, ctypes.c_void_p(st))
+        if s != 0:
+            raise PMError(s, "pm_net_create failed")
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.lib is not None:
+            self.lib.pm_net_destroy(self.h)
+            self.h = None
+
+    def _stream(self):
+        self.lib.pm_net_set_stream(self.h, ctypes.c_void_p(self.torch.cuda.current_stream(self.device).cuda_stream))
+
+    def load(self, theta, moments=None, step=0):
+        import numpy as np
+        P = self.num_params
+        buf = np.zeros(3 * P, dtype=np.float32)
+        buf[:P] = np.asarray(theta, dtype=np.float32)
+        if moments is not None:
+            buf[P:] = np.asarray(moments, dtype=np.float32)
+        s = self.lib.pm_net_load(self.h, buf.ctypes.data_as(ctypes.c_void_p), 1 if moments is not None else 0, step)
+        if s != 0:
+            raise PMError(s, "pm_net_load failed")
+
+    def state(self):
+        import numpy as np
+        P = self.num_params
+        buf = np.zeros(3 * P, dtype=np.float32)
+        step = ctypes.c_longlong(0)
+        s = self.lib.pm_net_state(self.h, buf.ctypes.data_as(ctypes.c_void_p), ctypes.byref(step))
+        if s != 0:
+            raise PMError(s, "pm_net_state failed")
+        return buf[:P].copy(), buf[P:].copy(), step.value
+
+    def forward(self, x, out=None):
+        B, _, n, _ = x.shape
+        out = out if out is not None else self.torch.empty(B, n, n, device=self.device)
+        self._stream()
+        s = self.lib.pm_net_forward(self.h, _ptr(x), B, n, _ptr(out))
+        if s != 0:
+            raise PMError(s, "pm_net_forward failed")
+        return out
+
+    def train_step(self, x, target, lr, want_loss=True):
+        B, _, n, _ = x.shape
+        loss = ctypes.c_double(0.0)
+        self._stream()
+        s = self.lib.pm_net_train_step(self.h, _ptr(x), _ptr(target), B, n, ctypes.c_float(lr),
+                                       ctypes.byref(loss) if want_loss else None)
+        if s != 0:
+            raise PMError(s, "pm_net_train_step failed")
+        return loss.value if want_loss else None
+
+    def grad(self):
+        import numpy as np
+        g = np.zeros(self.num_params, dtype=np.float32)
+        s = self.lib.pm_net_grad(self.h, g.ctypes.data_as(ctypes.c_void_p))
+        if s != 0:
+            raise PMError(s, "pm_net_grad failed")
+        return g

@@ -202,6 +202,8 @@ pm_status pm_ctx_create(pm_ctx **out, int dim, int n, double L, long long max_pa
               alloc(c, &w.red, 6LL * PM_MAXF * 4096) && alloc(c, &w.scal, 16LL * PM_MAXF) &&
               alloc(c, &w.bar, 2) && alloc(c, &w.status, 1) && alloc(c, &w.empty, 1) && alloc(c, &w.ntri, 1);
     if (ok && dim == 2) ok = alloc(c, &w.nbr, (ll)PM_MAXDEG * np);
+    if (ok && dim == 2 && n % 128 == 0)
+        ok = alloc(c, &w.feat, 2 * F * nc) && alloc(c, &w.corr, F * nc) && alloc(c, &w.nvol, nc);
     if (ok && cudaMallocHost((void **)&w.hstatus, sizeof(int)) != cudaSuccess) ok = false;
     if (!ok) {
         pm_ctx_destroy(c);
@@ -222,9 +224,9 @@ pm_status pm_ctx_create(pm_ctx **out, int dim, int n, double L, long long max_pa
 void pm_ctx_destroy(pm_ctx *c) {
     if (!c) return;
     Work &w = c->w;
-    void *ptrs[] = {w.fx,  w.key, w.slot, w.count, w.cell_start, w.scan_tmp, w.tmp,  w.perm, w.pos,
-                    w.vals, w.maxabs, w.nbr, w.deg,  w.vol,  w.part,  w.bfix, w.psum, w.r,    w.p,
-                    w.q,   w.b,   w.red,  w.scal,  w.bar,  w.status, w.empty, w.ntri};
+    void *ptrs[] = {w.fx,  w.key, w.slot, w.count, w.cell_start, w.scan_tmp, w.tmp,  w.perm,  w.pos,
+                    w.vals, w.maxabs, w.nbr, w.deg,  w.vol,  w.part,  w.bfix, w.psum, w.r,     w.p,
+                    w.q,   w.b,   w.red,  w.scal,  w.bar,  w.status, w.empty, w.ntri, w.feat, w.corr, w.nvol};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (w.hstatus) cudaFreeHost(w.hstatus);
@@ -304,6 +306,7 @@ static void default_opts(const pm_solve_opts *o, pm_solve_opts &d) {
     d.rtol = 1e-6;
     d.max_iter = 200;
     d.x0 = nullptr;
+    d.net = nullptr;
     if (o) d = *o;
     if (!(d.rtol > 0.0)) d.rtol = 1e-6;
     if (d.max_iter <= 0) d.max_iter = 200;
@@ -344,6 +347,20 @@ static pm_status mass_front(pm_ctx *c, const float *px, const float *py, ll np, 
     if (o.warm_start == PM_WS_DELTA) {
         Phase ph(c, PM_PH_DELTA);
         launch_delta(c->g, c->w, np, F, mesh_out, c->st);
+    } else if (o.warm_start == PM_WS_NET) {
+        {
+            Phase ph(c, PM_PH_DELTA);
+            launch_delta(c->g, c->w, np, F, mesh_out, c->st);
+            launch_flip(c->g, c->w, np, 0, nullptr, c->w.nvol, c->st);
+            launch_features(c->g, c->w, F, mesh_out, c->st);
+        }
+        {
+            Phase ph(c, PM_PH_NET);
+            pm_net_set_stream(o.net, c->st);
+            pm_status s2 = pm_net_forward(o.net, c->w.feat, F, c->g.n, c->w.corr);
+            if (s2) return fail(c, s2, "network forward failed (n must be a multiple of 128 within the net's size)");
+            launch_apply_correction(c->g, c->w, F, mesh_out, c->st);
+        }
     } else if (o.warm_start == PM_WS_USER) {
         cudaMemcpyAsync(mesh_out, o.x0, sizeof(float) * F * c->g.ncell, cudaMemcpyDeviceToDevice, c->st);
     } else {
@@ -370,6 +387,7 @@ pm_status pm_assign_mass(pm_ctx *c, const float *px, const float *py, long long 
     pm_solve_opts o;
     default_opts(opts, o);
     if (o.warm_start == PM_WS_USER && !o.x0) return fail(c, PM_EINVAL, "PM_WS_USER without x0");
+    if (o.warm_start == PM_WS_NET && (!o.net || !c->w.feat)) return fail(c, PM_EINVAL, "PM_WS_NET needs a network and a 2D mesh with n % 128 == 0");
     bool start = true;
     if ((s = mass_front(c, px, py, np, vals, F, mesh_out, o, start))) return s;
     if ((s = mass_solve_launch(c, F, mesh_out, start, o))) return s;
@@ -446,6 +464,29 @@ pm_status pm_triangulate(pm_ctx *c, const float *px, const float *py, long long 
     return s;
 }
 
+pm_status pm_net_features(pm_ctx *c, const float *px, const float *py, long long np, const float *vals, int F,
+                          float *delta_out, float *feat_out, float *scale_out) {
+    pm_status s = check_particles(c, px, py, np, F, vals, 3);
+    if (s) return s;
+    if (!c->w.feat || F < 1 || !delta_out || !feat_out) return fail(c, PM_EINVAL, "bad pm_net_features arguments");
+    if ((s = prepare(c, px, py, np, vals, F, true))) return s;
+    {
+        Phase ph(c, PM_PH_DELTA);
+        launch_delta(c->g, c->w, np, F, delta_out, c->st);
+        launch_flip(c->g, c->w, np, 0, nullptr, c->w.nvol, c->st);
+        launch_features(c->g, c->w, F, delta_out, c->st);
+    }
+    cudaMemcpyAsync(feat_out, c->w.feat, sizeof(float) * 2 * F * c->g.ncell, cudaMemcpyDeviceToDevice, c->st);
+    if (scale_out) {
+        // max|A_f| as float
+        cudaStreamSynchronize(c->st);
+        unsigned m[PM_MAXF];
+        cudaMemcpy(m, c->w.maxabs, sizeof(unsigned) * F, cudaMemcpyDeviceToHost);
+        for (int f = 0; f < F; ++f) memcpy(&scale_out[f], &m[f], sizeof(float));
+    }
+    return check_launch(c, "pm_net_features");
+}
+
 pm_status pm_advect_shift(pm_ctx *c, float *px, float *py, long long np, double dx, double dy) {
     pm_status s = check_particles(c, px, py, np, 0, nullptr, 0);
     if (s) return s;
@@ -503,7 +544,7 @@ pm_status pm_profile_read(pm_ctx *c, double *ms, long long *calls, int reset) {
 
 const char *pm_phase_name(int ph) {
     static const char *names[PM_NPHASE] = {"sort", "triangulate", "delta", "flip", "rhs",
-                                           "solve", "g2p", "advect", "other"};
+                                           "solve", "g2p", "advect", "other", "net"};
     return ph >= 0 && ph < PM_NPHASE ? names[ph] : "?";
 }
 
@@ -666,6 +707,7 @@ pm_status pm_batch_assign_mass(pm_batch *b, const float *const *px, const float 
     o.rtol = rtol > 0.0 ? rtol : 1e-6;
     o.max_iter = max_iter > 0 ? max_iter : 200;
     o.x0 = nullptr;
+    o.net = nullptr;
     std::vector<char> start(b->ninst, 1);
     // the main stream follows the caller's stream
     cudaEventRecord(b->fork, b->user);

@@ -68,6 +68,10 @@ struct Work {
     int *hstatus;          // pinned host mirror
     int *empty;            // empty-node counter
     ll *ntri;              // triangle counter
+    // learned warm start (2D, n a multiple of 128)
+    float *feat;           // [F][2][ncell] network input
+    float *corr;           // [F][ncell] network output
+    float *nvol;           // [ncell] FLIP node volumes
 };
 
 // ---------------------------------------------------------------------------
@@ -170,6 +174,8 @@ int launch_cg(const Geo &g, Work &w, int F, const float *b_float, bool b_from_fi
 void launch_scatter_sorted(ll np, const int *perm, const float *src, float *dst, cudaStream_t st);
 void launch_export_tris(const Geo &g, Work &w, ll np, int *tri, int *off, ll max_tri, cudaStream_t st);
 void launch_psum(const Geo &g, Work &w, ll np, int F, cudaStream_t st);
+void launch_features(const Geo &g, Work &w, int F, const float *delta, cudaStream_t st);
+void launch_apply_correction(const Geo &g, Work &w, int F, float *mesh, cudaStream_t st);
 void launch_advect_shift(const Geo &g, float *px, float *py, ll np, float dx, float dy, cudaStream_t st);
 void launch_advect_rotate(const Geo &g, float *px, float *py, ll np, float cx, float cy, float c, float s,
                           cudaStream_t st);

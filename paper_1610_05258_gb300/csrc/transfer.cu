@@ -548,7 +548,40 @@ __global__ void __launch_bounds__(256) k_psum(ll np, const float *__restrict__ v
     }
 }
 
+// Network input per field f: delta / max|A_f| and FLIP volume / h^2 - 1.
+__global__ void k_features(Geo g, int F, const float *__restrict__ delta, const float *__restrict__ nvol,
+                           const unsigned *__restrict__ maxabs, float *__restrict__ feat) {
+    ll i = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.ncell) return;
+    const float v = nvol[i] / (g.h * g.h) - 1.0f;
+    for (int f = 0; f < F; ++f) {
+        const float s = __uint_as_float(maxabs[f]);
+        const float inv = s > 0.0f ? 1.0f / s : 0.0f;
+        feat[((ll)f * 2 + 0) * g.ncell + i] = delta[(ll)f * g.ncell + i] * inv;
+        feat[((ll)f * 2 + 1) * g.ncell + i] = v;
+    }
+}
+
+// Warm start: mesh = delta + max|A_f| * network output.
+__global__ void k_apply_corr(Geo g, int F, const float *__restrict__ corr, const unsigned *__restrict__ maxabs,
+                             float *__restrict__ mesh) {
+    ll i = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.ncell) return;
+    for (int f = 0; f < F; ++f)
+        mesh[(ll)f * g.ncell + i] += __uint_as_float(maxabs[f]) * corr[(ll)f * g.ncell + i];
+}
+
 }  // namespace
+
+void launch_features(const Geo &g, Work &w, int F, const float *delta, cudaStream_t st) {
+    k_features<<<div_up(g.ncell, 256), 256, 0, st>>>(g, F, delta, w.nvol, w.maxabs, w.feat);
+    count_launches(1);
+}
+
+void launch_apply_correction(const Geo &g, Work &w, int F, float *mesh, cudaStream_t st) {
+    k_apply_corr<<<div_up(g.ncell, 256), 256, 0, st>>>(g, F, w.corr, w.maxabs, mesh);
+    count_launches(1);
+}
 
 void launch_delta(const Geo &g, Work &w, ll np, int F, float *mesh_out, cudaStream_t st) {
     if (g.dim == 2)
