@@ -187,7 +187,10 @@ pm_status pm_advect_rk2(pm_ctx *ctx, const float *mesh_vel, const float *vel, fl
 /* ---------------------------------------------------------------------------
  * Learned warm start (no counterpart in the paper: a small network predicts
  * the mass assignment of Sec. 2.4 from the delta assignment, Eq. delta, and
- * the FLIP node volume, Eq. FLIP_vol; conjugate gradients then finish the
+ * the residual of that start, r = b - M delta (b = int A psi_j, Eq. proj):
+ * the exact correction is M^-1 r, a fixed operator that decays fast for
+ * kappa(M) = 9 and that a local network can approximate; the start is
+ * delta + max|A| / 64 * network output); conjugate gradients then finish the
  * solve to the requested residual, so the result keeps the solver's
  * guarantees whatever the network predicts).
  *
@@ -216,8 +219,10 @@ pm_status pm_net_train_step(pm_net *net, const float *x, const float *target, in
 /* Gradient of the last training step (host, pm_net_num_params() floats). */
 pm_status pm_net_grad(pm_net *net, float *host_out);
 /* Network input of a mass assignment: delta assignment delta_out [F][n^2],
- * features feat_out [F][2][n^2] (delta / max|A_f|, FLIP node volume / h^2
- * - 1) and, if scale_out (host, F floats) is given, max|A_f| (waits). */
+ * features feat_out [F][2][n^2] (delta / max|A_f| and
+ * 64 (b_f - M delta_f) / (h^2 max|A_f|)) and, if scale_out (host, F floats)
+ * is given, max|A_f| (waits). The network's target is
+ * 64 (mass - delta) / max|A_f|. */
 pm_status pm_net_features(pm_ctx *ctx, const float *px, const float *py, long long np, const float *vals, int F,
                           float *delta_out, float *feat_out, float *scale_out);
 

@@ -3,10 +3,10 @@
 A 4-layer fully convolutional network on the periodic mesh: 3x3 convolutions
 2 -> 32 -> 32 -> 32 -> 1 with bias, ReLU after the first three, periodic
 padding (the mesh is a torus). Input channels: the delta assignment of a field
-(Sec. 2.2, Eq. delta) scaled by the field's RMS, and the FLIP node volume
-(Sec. 2.3, Eq. FLIP_vol) over h^2 minus one. Output: the correction added to
-the delta field to predict the mass assignment (Sec. 2.4), used as the start
-of the conjugate-gradient solve.
+(Sec. 2.2, Eq. delta) divided by the field's max |A|, and the residual of that
+start, 64 (b - M delta) / (h^2 max|A|) (b = int A psi_j, Eq. proj). Output: 64
+(mass - delta) / max|A|, the scaled correction that turns the delta field into
+the mass assignment (Sec. 2.4); it starts the conjugate-gradient solve.
 
 Written plainly with numpy (np.roll for the periodic shifts) in float64; the
 backward pass is the adjoint of each forward step, pinned by central finite
@@ -116,6 +116,10 @@ def loss_and_grad(theta, x, target):
     return loss, np.concatenate([q.ravel() for q in grads])
 
 
-def features(delta, node_volume, h, scale):
-    """Network input from the delta field and the FLIP node volumes."""
-    return np.stack([np.asarray(delta, np.float64) / scale, np.asarray(node_volume, np.float64) / (h * h) - 1.0])
+RSCALE = 64.0
+
+
+def features(delta, residual, h, scale):
+    """Network input from the delta field and its residual b - M delta."""
+    return np.stack([np.asarray(delta, np.float64) / scale,
+                     RSCALE * np.asarray(residual, np.float64) / (h * h * scale)])

@@ -203,7 +203,7 @@ pm_status pm_ctx_create(pm_ctx **out, int dim, int n, double L, long long max_pa
               alloc(c, &w.bar, 2) && alloc(c, &w.status, 1) && alloc(c, &w.empty, 1) && alloc(c, &w.ntri, 1);
     if (ok && dim == 2) ok = alloc(c, &w.nbr, (ll)PM_MAXDEG * np);
     if (ok && dim == 2 && n % 128 == 0)
-        ok = alloc(c, &w.feat, 2 * F * nc) && alloc(c, &w.corr, F * nc) && alloc(c, &w.nvol, nc);
+        ok = alloc(c, &w.feat, 2 * F * nc) && alloc(c, &w.corr, F * nc);
     if (ok && cudaMallocHost((void **)&w.hstatus, sizeof(int)) != cudaSuccess) ok = false;
     if (!ok) {
         pm_ctx_destroy(c);
@@ -226,7 +226,7 @@ void pm_ctx_destroy(pm_ctx *c) {
     Work &w = c->w;
     void *ptrs[] = {w.fx,  w.key, w.slot, w.count, w.cell_start, w.scan_tmp, w.tmp,  w.perm,  w.pos,
                     w.vals, w.maxabs, w.nbr, w.deg,  w.vol,  w.part,  w.bfix, w.psum, w.r,     w.p,
-                    w.q,   w.b,   w.red,  w.scal,  w.bar,  w.status, w.empty, w.ntri, w.feat, w.corr, w.nvol};
+                    w.q,   w.b,   w.red,  w.scal,  w.bar,  w.status, w.empty, w.ntri, w.feat, w.corr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (w.hstatus) cudaFreeHost(w.hstatus);
@@ -351,7 +351,6 @@ static pm_status mass_front(pm_ctx *c, const float *px, const float *py, ll np, 
         {
             Phase ph(c, PM_PH_DELTA);
             launch_delta(c->g, c->w, np, F, mesh_out, c->st);
-            launch_flip(c->g, c->w, np, 0, nullptr, c->w.nvol, c->st);
             launch_features(c->g, c->w, F, mesh_out, c->st);
         }
         {
@@ -471,9 +470,12 @@ pm_status pm_net_features(pm_ctx *c, const float *px, const float *py, long long
     if (!c->w.feat || F < 1 || !delta_out || !feat_out) return fail(c, PM_EINVAL, "bad pm_net_features arguments");
     if ((s = prepare(c, px, py, np, vals, F, true))) return s;
     {
+        Phase ph(c, PM_PH_RHS);
+        launch_rhs(c->g, c->w, np, F, c->st);
+    }
+    {
         Phase ph(c, PM_PH_DELTA);
         launch_delta(c->g, c->w, np, F, delta_out, c->st);
-        launch_flip(c->g, c->w, np, 0, nullptr, c->w.nvol, c->st);
         launch_features(c->g, c->w, F, delta_out, c->st);
     }
     cudaMemcpyAsync(feat_out, c->w.feat, sizeof(float) * 2 * F * c->g.ncell, cudaMemcpyDeviceToDevice, c->st);

@@ -9,6 +9,7 @@
 #define PM_MAXW 32     // capacity of the working Voronoi polygon
 #define PM_MAXF 8      // fields per call
 #define PM_RCAP 12     // rings of cells searched by the triangulation
+#define PM_NET_RSCALE 64.0f  // scale of the residual input and of the output of the warm-start network
 
 typedef long long ll;
 typedef unsigned long long ull;
@@ -71,7 +72,6 @@ struct Work {
     // learned warm start (2D, n a multiple of 128)
     float *feat;           // [F][2][ncell] network input
     float *corr;           // [F][ncell] network output
-    float *nvol;           // [ncell] FLIP node volumes
 };
 
 // ---------------------------------------------------------------------------

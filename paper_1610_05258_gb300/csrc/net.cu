@@ -2,7 +2,8 @@
 //
 // A small fully convolutional network on the periodic mesh predicts the mass
 // assignment (Sec. 2.4, Eqs. proj and phi_def) from the delta assignment
-// (Sec. 2.2, Eq. delta) and the FLIP node volume (Sec. 2.3, Eq. FLIP_vol);
+// (Sec. 2.2, Eq. delta) and the lumped-mass solution b / h^2 (b the exact
+// right-hand side of Eq. proj);
 // its prediction starts the conjugate-gradient solve, which still finishes to
 // the requested residual. Layers: 3x3 periodic convolutions 2 -> 32 -> 32 ->
 // 32 -> 1 with bias, ReLU after the first three. Activations are stored in

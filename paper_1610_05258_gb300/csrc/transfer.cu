@@ -548,33 +548,53 @@ __global__ void __launch_bounds__(256) k_psum(ll np, const float *__restrict__ v
     }
 }
 
-// Network input per field f: delta / max|A_f| and FLIP volume / h^2 - 1.
-__global__ void k_features(Geo g, int F, const float *__restrict__ delta, const float *__restrict__ nvol,
+// Network input per field f: delta / max|A_f| and the residual of the delta
+// start, r = b - M delta (b the exact right-hand side from its fixed point,
+// M the bilinear mass stencil), as PM_NET_RSCALE r / (h^2 max|A_f|): the exact
+// correction is M^-1 r, a fixed, fast-decaying linear operator of r.
+__global__ void k_features(Geo g, int F, const float *__restrict__ delta, const ll *__restrict__ bfix,
                            const unsigned *__restrict__ maxabs, float *__restrict__ feat) {
     ll i = (ll)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.ncell) return;
-    const float v = nvol[i] / (g.h * g.h) - 1.0f;
+    const int n = g.n, ix = (int)(i % n), iy = (int)(i / n);
+    const int xm = ix == 0 ? n - 1 : ix - 1, xp = ix + 1 == n ? 0 : ix + 1;
+    const int ym = iy == 0 ? n - 1 : iy - 1, yp = iy + 1 == n ? 0 : iy + 1;
+    const float hd = g.h * g.h;
     for (int f = 0; f < F; ++f) {
         const float s = __uint_as_float(maxabs[f]);
         const float inv = s > 0.0f ? 1.0f / s : 0.0f;
-        feat[((ll)f * 2 + 0) * g.ncell + i] = delta[(ll)f * g.ncell + i] * inv;
-        feat[((ll)f * 2 + 1) * g.ncell + i] = v;
+        const float *d = delta + (ll)f * g.ncell;
+        const float *r0 = d + (ll)ym * n, *r1 = d + (ll)iy * n, *r2 = d + (ll)yp * n;
+        Dot2 acc;
+        acc.add(16.0f * r1[ix]);
+        acc.add(4.0f * r1[xm]);
+        acc.add(4.0f * r1[xp]);
+        acc.add(4.0f * r0[ix]);
+        acc.add(4.0f * r2[ix]);
+        acc.add(r0[xm]);
+        acc.add(r0[xp]);
+        acc.add(r2[xm]);
+        acc.add(r2[xp]);
+        const float b = ldexpf((float)bfix[(ll)f * g.ncell + i], -fix_exp(maxabs, f, hd));
+        const float res = (b - hd * (1.0f / 36.0f) * acc.hi) - hd * (1.0f / 36.0f) * acc.lo;
+        feat[((ll)f * 2 + 0) * g.ncell + i] = d[i] * inv;
+        feat[((ll)f * 2 + 1) * g.ncell + i] = PM_NET_RSCALE * res * inv / hd;
     }
 }
 
-// Warm start: mesh = delta + max|A_f| * network output.
+// Warm start: mesh = delta + (max|A_f| / PM_NET_RSCALE) * network output.
 __global__ void k_apply_corr(Geo g, int F, const float *__restrict__ corr, const unsigned *__restrict__ maxabs,
                              float *__restrict__ mesh) {
     ll i = (ll)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.ncell) return;
     for (int f = 0; f < F; ++f)
-        mesh[(ll)f * g.ncell + i] += __uint_as_float(maxabs[f]) * corr[(ll)f * g.ncell + i];
+        mesh[(ll)f * g.ncell + i] += __uint_as_float(maxabs[f]) * (1.0f / PM_NET_RSCALE) * corr[(ll)f * g.ncell + i];
 }
 
 }  // namespace
 
 void launch_features(const Geo &g, Work &w, int F, const float *delta, cudaStream_t st) {
-    k_features<<<div_up(g.ncell, 256), 256, 0, st>>>(g, F, delta, w.nvol, w.maxabs, w.feat);
+    k_features<<<div_up(g.ncell, 256), 256, 0, st>>>(g, F, delta, w.bfix, w.maxabs, w.feat);
     count_launches(1);
 }
 

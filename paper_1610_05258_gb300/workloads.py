@@ -45,6 +45,34 @@ def rng(seed: int) -> np.random.Generator:
     return np.random.default_rng(seed)
 
 
+def torus_keys(x, y, L):
+    """The library's position convention (x -> floor(frac(fl32(x fl32(1/L))) 2^32),
+    see include/pmt.h) as one 64-bit key per particle; used only to keep the
+    generated particles distinct, which the particle functions require."""
+    invL = np.float32(1.0 / L)
+    def q(v):
+        t = (np.asarray(v, np.float32) * invL).astype(np.float32)
+        f = (t - np.floor(t)).astype(np.float32)
+        f = np.where(f >= np.float32(1.0), np.float32(0.0), f)
+        return (f.astype(np.float64) * 4294967296.0).astype(np.uint64)
+    return (q(x) << np.uint64(32)) | q(y)
+
+
+def redraw_coincident(x, y, L, g, draw):
+    """Redraw particles whose torus coordinates coincide with an earlier one's."""
+    for _ in range(16):
+        k = torus_keys(x, y, L)
+        _, first = np.unique(k, return_index=True)
+        dup = np.ones(k.shape[0], bool)
+        dup[first] = False
+        nd = int(dup.sum())
+        if nd == 0:
+            return x, y
+        nx, ny = draw(nd)
+        x[dup], y[dup] = nx, ny
+    return x, y
+
+
 def tophat_1d(n=128, npart=128, seed=16101, lo=0.25, hi=0.5, L=1.0, regular=False, jitter=0.0):
     g = rng(seed)
     if regular:
@@ -99,6 +127,8 @@ def taylor_green(n=1024, ppc=4, seed=16103):
     y = g.uniform(0.0, L, npart).astype(np.float32)
     x = np.where(x >= np.float32(L), np.float32(0), x)
     y = np.where(y >= np.float32(L), np.float32(0), y)
+    x, y = redraw_coincident(x, y, L, g, lambda k: (g.uniform(0.0, L, k).astype(np.float32),
+                                                    g.uniform(0.0, L, k).astype(np.float32)))
     return Instance(2, n, L, x, y, taylor_green_fields(x, y), name=f"taylor_green_n{n}")
 
 
@@ -141,6 +171,8 @@ def uniform_instance(n, ppc, F=3, seed=16104, L=1.0, slope=-3.0, field_grid=128)
     npart = max(16, int(round(ppc * n * n)))
     x = g.uniform(0.0, L, npart).astype(np.float32)
     y = g.uniform(0.0, L, npart).astype(np.float32)
+    x, y = redraw_coincident(x, y, L, g, lambda k: (g.uniform(0.0, L, k).astype(np.float32),
+                                                    g.uniform(0.0, L, k).astype(np.float32)))
     m = min(n, field_grid)
     vals = np.stack([sample_grid_field(random_phase_field(m, slope, seed * 7 + f, L), L, x, y) for f in range(F)])
     return Instance(2, n, L, x, y, vals.astype(np.float32), name=f"uniform_n{n}_ppc{ppc}")
@@ -186,6 +218,18 @@ def mixture(n=2048, ppc=4, F=4, seed=16105, contrast=10.0, ncomp=8):
     y = np.concatenate(ys)[:npart].astype(np.float32)
     x = np.where(x >= np.float32(L), np.float32(0), x)
     y = np.where(y >= np.float32(L), np.float32(0), y)
+
+    def draw(k):  # a fresh draw from the same density
+        ox, oy = [], []
+        while sum(len(a) for a in ox) < k:
+            cx = g.uniform(0.0, L, 4 * k + 16)
+            cy = g.uniform(0.0, L, 4 * k + 16)
+            acc = g.uniform(0.0, 1.0, cx.shape[0]) < sample_grid_field(rho, L, cx, cy)
+            ox.append(cx[acc])
+            oy.append(cy[acc])
+        return (np.concatenate(ox)[:k].astype(np.float32) % np.float32(L),
+                np.concatenate(oy)[:k].astype(np.float32) % np.float32(L))
+    x, y = redraw_coincident(x, y, L, g, draw)
     vals = [*taylor_green_fields(x, y)]
     for f in range(F - 2):
         grid = random_phase_field(256, -3.0, seed * 11 + f, L)
