@@ -1,20 +1,23 @@
 """Benchmark of the particle <-> mesh transfer hot path on GB300.
 
-One step = one time step of the Taylor-Green experiment (Sec. 3.3) on a
-1024^2 periodic bilinear mesh with 4 uniform random particles per cell
-(4,194,304 particles) and F = 2 fields (u, v):
-    G2P   Abb = sum_i Ab_i psi_i(r)           (pm_interpolate, Eq. delta2)
-    move  midpoint rule with the mesh velocity, viscous decay of the values
-          (pm_advect_rk2)
-    P2G   mass assignment to 1e-6 relative residual (pm_assign_mass: cell sort,
-          periodic Delaunay stars, exact right-hand side, delta warm start,
-          CG on the mass matrix, Eqs. proj and phi_def)
-Metric: particles * fields / s of the whole step. Device-resident inputs;
-the L2 cache (129 MB) is flushed by writing a 512 MB buffer before every timed
-step, and each step is timed with CUDA events on the launching stream.
+Default workload (learned warm start configuration): a 2048^2 periodic
+bilinear mesh on [0, 2 pi)^2 and 16,777,216 particles drawn from a Gaussian
+mixture with 10x density contrast; F = 4 fields (Taylor-Green u, v and two
+random-phase fields). One step = one mass assignment of all particles and
+fields (Sec. 2.4, Eqs. proj and phi_def): cell sort, periodic Delaunay stars,
+exact right-hand side, CG to 1e-6 relative residual. The headline `value` is
+the plain solve (delta warm start); the same step with the learned warm start
+(network correction of the delta start, CG to the same residual) is reported
+under "learned". Metric: particles * fields / s.
 
---impl reference times the FP64 CPU oracle (single thread) on a bounded
-sample of the same workload (a 32^2 Taylor-Green box, 4 particles per cell).
+Other workloads: --workload taylor_green (1024^2, 4.2M particles; one time
+step = G2P + midpoint move + mass assignment) and --workload batched (256
+instances of uneven sizes, one CUDA graph per step).
+
+Inputs are device-resident; the L2 cache (129 MB) is flushed by writing a
+512 MB buffer before every timed step, and every step is timed with CUDA
+events on the launching stream. --impl reference times the FP64 CPU oracle
+(single thread) on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -101,53 +104,43 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(seconds_hint=10.0):
-    """The FP64 oracle as it stands (single-threaded C) on a bounded sample:
-    Taylor-Green 32^2 box, 4 particles per cell, F = 2: G2P + mass assignment."""
-    import numpy as np
-
-    import oracle
+def oracle_sample():
+    """The bounded CPU sample of the default workload: the same mixture
+    recipe on a 32^2 mesh (4096 particles, F = 4)."""
     from paper_1610_05258_gb300 import workloads as W
+    return W.mixture(32, 4, F=4, seed=16105)
 
-    inst = W.taylor_green(32, 4, seed=16103)
-    mesh = oracle.assign_mass(2, inst.n, inst.L, inst.px, inst.py, inst.vals)
+
+def cpu_baseline(seconds_hint=10.0):
+    """The FP64 oracle as it stands (single-threaded C) timed on the bounded
+    sample: one mass assignment per repetition."""
+    import oracle
+
+    inst = oracle_sample()
+    oracle.assign_mass(2, inst.n, inst.L, inst.px, inst.py, inst.vals)
     t0 = time.perf_counter()
     reps = 0
     while True:
-        vel = oracle.interpolate(2, inst.n, inst.L, mesh, inst.px, inst.py)
-        mesh = oracle.assign_mass(2, inst.n, inst.L, inst.px, inst.py, vel * math.exp(-2 * NU * 1e-3))
+        oracle.assign_mass(2, inst.n, inst.L, inst.px, inst.py, inst.vals)
         reps += 1
         if time.perf_counter() - t0 > seconds_hint:
             break
     dt = (time.perf_counter() - t0) / reps
     return {"value": inst.np * inst.F / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"taylor_green 32^2, {inst.np} particles, F=2, {reps} steps of G2P + mass assignment "
-                      f"(FP64, single thread), {dt * 1e3:.1f} ms/step"}
+            "sample": f"mixture 32^2, {inst.np} particles, F={inst.F}, {reps} mass assignments "
+                      f"(FP64, single thread), {dt * 1e3:.1f} ms each"}
 
 
 def run_reference(args):
-    import numpy as np
-
     import oracle
-    from paper_1610_05258_gb300 import workloads as W
 
     if args.world > 1 and args.rank != 0:
         return
-    inst = W.taylor_green(32, 4, seed=16103)
-    mesh = oracle.assign_mass(2, inst.n, inst.L, inst.px, inst.py, inst.vals)
-    px, py = inst.px.copy(), inst.py.copy()
-    dt = 0.5 * (inst.L / inst.n)
+    inst = oracle_sample()
     times = []
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        vel = oracle.interpolate(2, inst.n, inst.L, mesh, px, py)
-        # midpoint rule with the oracle's G2P
-        xm = np.mod(px + 0.5 * dt * vel[0], inst.L).astype(np.float32)
-        ym = np.mod(py + 0.5 * dt * vel[1], inst.L).astype(np.float32)
-        vm = oracle.interpolate(2, inst.n, inst.L, mesh, xm, ym)
-        px = np.mod(px + dt * vm[0], inst.L).astype(np.float32)
-        py = np.mod(py + dt * vm[1], inst.L).astype(np.float32)
-        mesh = oracle.assign_mass(2, inst.n, inst.L, px, py, vel * math.exp(-2 * NU * dt))
+        oracle.assign_mass(2, inst.n, inst.L, inst.px, inst.py, inst.vals)
         if s >= args.warmup:
             times.append(time.perf_counter() - t0)
     t = sum(times) / len(times)
@@ -156,13 +149,168 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "taylor_green_32x32_ppc4_F2 (bounded CPU sample of taylor_green_1024x1024_ppc4_F2)",
+        "config": {"workload": "mixture_32x32_ppc4_F4 (bounded CPU sample of mixture_2048x2048_ppc4_F4)",
                    "particles": inst.np, "fields": inst.F, "mesh": f"{inst.n}x{inst.n}"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"taylor_green 32^2, {inst.np} particles, F=2, G2P + midpoint move + mass "
-                                   f"assignment per step, FP64 single thread"},
+                         "sample": f"mixture 32^2, {inst.np} particles, F={inst.F}, one mass assignment per step, "
+                                   f"FP64 single thread"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+# Roofline of the triangulation (the dominant kernel): it is bound by ALU
+# issue, not by memory. Its algorithmic operation count per launch is the
+# arithmetic of the clipping algorithm on the actual particle set: the kernel's
+# counting build (pm_profile mode 2) counts, over all particles, the candidates
+# examined, the candidates passing the distance bound, the in-circle vertex
+# tests, the clips and the cell sizes after each clip; each is weighted by the
+# FP32/INT32 arithmetic instructions of that step as written (an FMA counts
+# as one): distance test 10, margin set-up 5, vertex test 5, clip with two
+# circumcentres and error bounds 80, radius bound 9 per vertex. Divergence,
+# address arithmetic, loads and stores are not counted.
+DELAUNAY_OP_WEIGHTS = {"candidates": 10, "tested": 5, "vertex_tests": 5, "clips": 80, "cell_size_sum": 9}
+# ALU peak: 152 SMs x 128 FP32 lanes x one instruction per lane per clock.
+ALU_LANES = 152 * 128
+
+
+def alu_roofline(kernel, counts, ms, sm_mhz):
+    ops = float(sum(DELAUNAY_OP_WEIGHTS[k] * counts[k] for k in DELAUNAY_OP_WEIGHTS))
+    achieved = ops / (ms * 1e-3) / 1e12
+    peak = ALU_LANES * sm_mhz * 1e6 / 1e12
+    return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+            "frac": achieved / peak, "traffic": None, "ops_per_launch": ops, "work_counts": counts,
+            "peak_source": f"derived: 152 SMs x 128 lanes x {sm_mhz:.0f} MHz (median SM clock sampled during the "
+                           f"timed region)"}
+
+
+def time_steps(torch, stream, flush, steps, fn):
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        fn()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def run_mixture(args, pm, torch, dist, local):
+    """Learned warm start configuration: one mass assignment of 16.8M mixture
+    particles and 4 fields on a 2048^2 mesh per step, plain (delta start)
+    and learned (network start), both to 1e-6 relative residual."""
+    from paper_1610_05258_gb300 import warmstart as WS
+
+    dev = torch.device("cuda", local)
+    n, F, ppc = args.n, 4, 4
+    L = 2.0 * math.pi
+    px, py, vals = WS.mixture_gpu(torch, n, ppc, F, seed=16105 + 7919 * args.rank, device=dev)
+    N = px.numel()
+    ctx = pm.Context(2, n, L, N, F, device=dev)
+    net = pm.Net(n, F, device=dev)
+    WS.load_weights(net)
+    out = torch.empty(F, n * n, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    arms = {"plain": {"warm_start": "delta"}, "learned": {"net": net}}
+    res = {}
+    clocks = Clocks(local)
+    for name, kw in arms.items():
+        _, info = ctx.assign_mass(px, py, vals, out=out, **kw)
+        for _ in range(args.warmup):
+            ctx.assign_mass(px, py, vals, out=out, info=False, **kw)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ctx.profile_read(reset=True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if name == "plain":
+            clocks.start()
+        l0 = pm.kernel_launches()
+        ms = time_steps(torch, stream, flush, args.steps,
+                        lambda: ctx.assign_mass(px, py, vals, out=out, info=False, **kw))
+        launches = pm.kernel_launches() - l0
+        prof = ctx.profile_read(reset=True)
+        ctx.profile(False)
+        t = sum(ms) / len(ms)
+        if dist:
+            tt = torch.tensor([t], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        res[name] = {"ms": t, "launches": launches, "info": info,
+                     "phase_ms": {k: v[0] / args.steps for k, v in prof.items() if v[0] > 0}}
+    ck = clocks.stop()
+
+    # ---- end to end through the public API: pinned host positions and values
+    # in, converged mesh fields out, every step
+    e2e = None
+    if not args.no_e2e:
+        hpx, hpy, hvals = px.cpu().pin_memory(), py.cpu().pin_memory(), vals.cpu().pin_memory()
+        hout = torch.empty(F, n * n).pin_memory()
+        dpx, dpy, dvals = torch.empty_like(px), torch.empty_like(py), torch.empty_like(vals)
+        bi = (hpx.numel() + hpy.numel() + hvals.numel()) * 4
+        bo = hout.numel() * 4
+
+        def e2e_step():
+            dpx.copy_(hpx, non_blocking=True)
+            dpy.copy_(hpy, non_blocking=True)
+            dvals.copy_(hvals, non_blocking=True)
+            ctx.assign_mass(dpx, dpy, dvals, out=out, info=False)
+            hout.copy_(out, non_blocking=True)
+
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        te = sum(time_steps(torch, stream, flush, args.steps, e2e_step)) / args.steps
+        e2e = {"value": args.world * N * F / (te * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi,
+               "d2h_bytes_per_step": bo, "ms_per_step": te}
+
+    plain, learned = res["plain"], res["learned"]
+    # one untimed pass of the counting build of the triangulation
+    ctx.profile(True, count_work=True)
+    ctx.assign_mass(px, py, vals, out=out, info=False)
+    counts = ctx.work_read()
+    ctx.profile(False)
+    sm = ck.get("sm_mhz") or float(measured_peaks().get("sm_max_mhz", 2070.0))
+    dom = max(plain["phase_ms"], key=plain["phase_ms"].get)
+    roof = alu_roofline("k_delaunay (phase triangulate)", counts, plain["phase_ms"]["triangulate"], sm)
+    roof["dominant_phase"] = dom
+    hbm = float(measured_peaks().get("hbm_gbs", 6800.0))
+    minimal = N * (8 + 4 * F) + n * n * 4 * F  # positions + values in, fields out
+    roof["hbm_minimal_io"] = {"bytes_per_step": minimal, "achieved_gbs": minimal / (plain["ms"] * 1e-3) / 1e9,
+                              "peak_gbs": hbm, "frac": minimal / (plain["ms"] * 1e-3) / 1e9 / hbm}
+
+    def solve_report(info):
+        return {"iters": [i.iters for i in info], "init_rel_resid": [i.init_rel_resid for i in info],
+                "rel_resid": [i.rel_resid for i in info], "cons_err": [i.cons_err for i in info]}
+
+    cpu = cpu_baseline(10.0) if (args.rank == 0 and not args.no_cpu) else None
+    line = {
+        "metric": METRIC, "value": args.world * N * F / (plain["ms"] * 1e-3), "unit": UNIT, "n_gpus": args.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": plain["ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"mixture_{n}x{n}_ppc{ppc}_F{F}: {N} particles by rejection from a 10x-contrast "
+                               f"Gaussian mixture, F={F} (Taylor-Green u, v, two random-phase fields), {n}x{n} "
+                               f"periodic bilinear mesh, L=2pi; step = one mass assignment to 1e-6 relative "
+                               f"residual (delta warm start)",
+                   "l2": "flushed before every timed step (512 MB write)", "parallelism": f"replicas x{args.world}"},
+        "phase_ms_per_step": {k: round(v, 4) for k, v in plain["phase_ms"].items()},
+        "solve": solve_report(plain["info"]),
+        "learned": {"value": args.world * N * F / (learned["ms"] * 1e-3), "ms_per_step": learned["ms"],
+                    "speedup_vs_plain": plain["ms"] / learned["ms"],
+                    "phase_ms_per_step": {k: round(v, 4) for k, v in learned["phase_ms"].items()},
+                    "solve": solve_report(learned["info"]), "gpu_launches": learned["launches"],
+                    "network": "4-layer 3x3 conv 2-32-32-32-1, BF16 tcgen05, shipped weights"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": plain["launches"],
+        "clocks": ck,
+    }
+    if args.rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
 
 
 def run_batched(args, pm, torch, dist, local):
@@ -234,12 +382,14 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="taylor_green", choices=["taylor_green", "mixture", "batched"])
+    ap.add_argument("--workload", default="mixture", choices=["mixture", "taylor_green", "batched"])
     ap.add_argument("--instances", type=int, default=256)
-    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--n", type=int, default=0, help="mesh side (default 2048 mixture, 1024 taylor_green)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
+    if not args.n:
+        args.n = 2048 if args.workload == "mixture" else 1024
     args.rank = int(os.environ.get("RANK", "0"))
     args.world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
@@ -266,6 +416,8 @@ def main():
 
     if args.workload == "batched":
         return run_batched(args, pm, torch, dist, local)
+    if args.workload == "mixture":
+        return run_mixture(args, pm, torch, dist, local)
     inst = workload(args)
     n, L, F, N = inst.n, inst.L, inst.F, inst.np
     h = L / n
@@ -356,30 +508,20 @@ def main():
         e2e = {"value": args.world * N * F / (te * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo, "ms_per_step": te}
 
-    peaks = measured_peaks()
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    # dominant phase and its roofline (algorithmic bytes per launch: see the design doc)
     phase_ms = {k: v[0] / max(1, args.steps) for k, v in prof.items()}
     dom = max(phase_ms, key=phase_ms.get)
-    nn = n * n
-    alg = {
-        # minimal traffic of each phase per launch (bytes)
-        "sort": N * (8 + 4 + 4 + 4 + 4 + 4 + 8 + 4 * F + 4 * F + 4) + nn * 4 * 3,
-        "triangulate": N * (8 + 4 + 4 * 6 + 1 + 4),
-        "rhs": N * (8 + 4 * F + 4 * 6 + 1 + 4) + nn * 8 * F,
-        "delta": N * (8 + 4 * F + 4 * 6 + 1) + nn * 4 * F,
-        "solve": nn * 4 * F * 3,
-        "g2p": N * (8 + 4 * F) + nn * 4 * F,
-        "advect": N * (16 + 8 * F) + nn * 4 * F,
-    }
-    dom_bytes = alg.get(dom, 0)
-    achieved = dom_bytes / (phase_ms[dom] * 1e-3) / 1e9 if phase_ms[dom] > 0 else 0.0
-    roof = {"kernel_phase": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None, "peak_source": "measured" if "fallback" not in peaks else "fallback"}
+    ctx.profile(True, count_work=True)
+    ctx.assign_mass(px, py, vel, out=mesh2, info=False)
+    counts = ctx.work_read()
+    ctx.profile(False)
+    sm = ck.get("sm_mhz") or float(measured_peaks().get("sm_max_mhz", 2070.0))
+    roof = alu_roofline("k_delaunay (phase triangulate)", counts, phase_ms["triangulate"], sm)
+    roof["dominant_phase"] = dom
 
     cpu = None
     if args.rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(10.0)
+        cpu["sample"] += " (mixture sample; the Taylor-Green step has no separate CPU baseline)"
 
     value = args.world * N * F / (t_step * 1e-3)
     line = {

@@ -71,7 +71,9 @@ typedef struct pm_solve_opts {
     double rtol;     /* stop when ||b - M Ab||_2 <= rtol ||b||_2 (default 1e-6)  */
     int max_iter;    /* iteration cap (default 200)                              */
     const float *x0; /* device [F][n^dim], read when warm_start == PM_WS_USER     */
-    pm_net *net;     /* PM_WS_NET: start from delta + the network's correction    */
+    pm_net *net;     /* PM_WS_NET: start from delta + alpha c, c the network's
+                        correction and alpha the step that minimises the 2-norm
+                        of the start's residual (alpha = 0 keeps the delta start) */
 } pm_solve_opts;
 
 /* Per-field report of a mass solve (host memory, one entry per field). */
@@ -303,6 +305,15 @@ enum {
  * PM_NPHASE, either may be NULL), resetting them if `reset`. */
 pm_status pm_profile(pm_ctx *ctx, int enable);
 pm_status pm_profile_read(pm_ctx *ctx, double *ms, long long *calls, int reset);
+/* Work counters of the 2D triangulation (Sec. 3.2 particle functions),
+ * collected while pm_profile(ctx, 2) is in effect: that mode runs a counting
+ * build of the triangulation kernel (same results, slower; not for timing).
+ * counts[0..4] = candidates examined, candidates within the distance bound,
+ * in-circle vertex tests, clips of the Voronoi cell, sum of the cell sizes
+ * after each clip, summed over all particles and calls since the last reset.
+ * Waits for the context's stream. Host array of `ncounts` entries (entries
+ * past 4 are written as 0). PM_EINVAL on a NULL ctx or array. */
+pm_status pm_work_read(pm_ctx *ctx, long long *counts, int ncounts, int reset);
 const char *pm_phase_name(int phase);
 /* Number of kernels this library has launched in the process so far. */
 long long pm_kernel_launches(void);

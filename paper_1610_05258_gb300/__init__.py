@@ -27,11 +27,12 @@ EXPORTS = [
     "pm_ctx_create", "pm_ctx_destroy", "pm_ctx_set_stream", "pm_sync", "pm_last_error", "pm_ctx_workspace_bytes",
     "pm_interpolate", "pm_assign_delta", "pm_assign_flip", "pm_assign_mass", "pm_mass_rhs", "pm_mass_apply",
     "pm_mass_solve", "pm_particle_volumes", "pm_triangulate", "pm_sort", "pm_advect_shift", "pm_advect_rotate",
-    "pm_advect_rk2", "pm_profile", "pm_profile_read", "pm_phase_name", "pm_kernel_launches",
+    "pm_advect_rk2", "pm_profile", "pm_profile_read", "pm_work_read", "pm_phase_name", "pm_kernel_launches",
     "pm_batch_create", "pm_batch_destroy", "pm_batch_last_error", "pm_batch_tuning", "pm_batch_assign_mass",
     "pm_net_num_params", "pm_net_create", "pm_net_destroy", "pm_net_set_stream", "pm_net_state", "pm_net_load",
     "pm_net_forward", "pm_net_train_step", "pm_net_grad", "pm_net_features",
 ]
+WORK_COUNTERS = ["candidates", "tested", "vertex_tests", "clips", "cell_size_sum"]
 PHASES = ["sort", "triangulate", "delta", "flip", "rhs", "solve", "g2p", "advect", "other", "net"]
 
 
@@ -97,6 +98,7 @@ def load_library(path: str | None = None):
         "pm_advect_rk2": [vp, vp, vp, vp, vp, ll, d, vp, i, d],
         "pm_profile": [vp, i],
         "pm_profile_read": [vp, vp, vp, i],
+        "pm_work_read": [vp, vp, i, i],
         "pm_phase_name": [i],
         "pm_kernel_launches": [],
         "pm_batch_create": [ctypes.POINTER(vp), i, vp, vp, vp, i, i, vp],
@@ -333,8 +335,16 @@ class Context:
                                            float(dt), _ptr(vals), F, float(factor)))
 
     # ---------------------------------------------------------- instrumentation
-    def profile(self, enable=True):
-        self._check(self.lib.pm_profile(self.h, 1 if enable else 0))
+    def profile(self, enable=True, count_work=False):
+        """Per-phase CUDA-event timing; with count_work, the triangulation
+        runs its counting build (same results, not for timing)."""
+        self._check(self.lib.pm_profile(self.h, (2 if count_work else 1) if enable else 0))
+
+    def work_read(self, reset=True):
+        """Triangulation work counters collected in counting mode."""
+        c = (ctypes.c_longlong * 8)()
+        self._check(self.lib.pm_work_read(self.h, c, 8, 1 if reset else 0))
+        return dict(zip(WORK_COUNTERS, list(c)[:len(WORK_COUNTERS)]))
 
     def profile_read(self, reset=True):
         ms = (ctypes.c_double * len(PHASES))()

@@ -27,6 +27,7 @@ struct pm_ctx {
     int dev;
     // profiling: CUDA events around every phase, on the context's stream
     bool prof = false;
+    bool count_work = false;  // counting instantiation of the triangulation
     std::vector<PendingEvent> ev;
     size_t nev = 0;
     double acc_ms[PM_NPHASE] = {0};
@@ -155,7 +156,7 @@ pm_status prepare(pm_ctx *c, const float *px, const float *py, ll np, const floa
     if (need_tri) {
         Phase ph(c, PM_PH_TRIANGULATE);
         if (c->g.dim == 2)
-            launch_triangulate(c->g, c->w, np, c->st);
+            launch_triangulate(c->g, c->w, np, c->st, c->count_work);
         else
             launch_volumes_1d(c->g, c->w, np, c->st);
     }
@@ -200,7 +201,8 @@ pm_status pm_ctx_create(pm_ctx **out, int dim, int n, double L, long long max_pa
               alloc(c, &w.psum, 2 * PM_MAXF * (ll)w.nblk_psum) && alloc(c, &w.r, F * nc) &&
               alloc(c, &w.p, F * nc) && alloc(c, &w.q, F * nc) && alloc(c, &w.b, F * nc) &&
               alloc(c, &w.red, 6LL * PM_MAXF * 4096) && alloc(c, &w.scal, 16LL * PM_MAXF) &&
-              alloc(c, &w.bar, 2) && alloc(c, &w.status, 1) && alloc(c, &w.empty, 1) && alloc(c, &w.ntri, 1);
+              alloc(c, &w.bar, 2) && alloc(c, &w.status, 1) && alloc(c, &w.empty, 1) && alloc(c, &w.ntri, 1) &&
+              alloc(c, &w.wsum, 8) && alloc(c, &w.nretry, 1);
     if (ok && dim == 2) ok = alloc(c, &w.nbr, (ll)PM_MAXDEG * np);
     if (ok && dim == 2 && n % 128 == 0)
         ok = alloc(c, &w.feat, 2 * F * nc) && alloc(c, &w.corr, F * nc);
@@ -212,6 +214,7 @@ pm_status pm_ctx_create(pm_ctx **out, int dim, int n, double L, long long max_pa
     }
     cudaMemset(w.status, 0, sizeof(int));
     cudaMemset(w.scal, 0, sizeof(double) * 16 * PM_MAXF);
+    cudaMemset(w.wsum, 0, sizeof(ull) * 8);
     cudaMemset(w.deg, 0, (size_t)(np > 0 ? np : 1));
     if (cudaDeviceSynchronize() != cudaSuccess) {
         pm_ctx_destroy(c);
@@ -226,7 +229,8 @@ void pm_ctx_destroy(pm_ctx *c) {
     Work &w = c->w;
     void *ptrs[] = {w.fx,  w.key, w.slot, w.count, w.cell_start, w.scan_tmp, w.tmp,  w.perm,  w.pos,
                     w.vals, w.maxabs, w.nbr, w.deg,  w.vol,  w.part,  w.bfix, w.psum, w.r,     w.p,
-                    w.q,   w.b,   w.red,  w.scal,  w.bar,  w.status, w.empty, w.ntri, w.feat, w.corr};
+                    w.q,   w.b,   w.red,  w.scal,  w.bar,  w.status, w.empty, w.ntri, w.feat, w.corr,
+                    w.wsum, w.nretry};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (w.hstatus) cudaFreeHost(w.hstatus);
@@ -527,6 +531,19 @@ pm_status pm_profile(pm_ctx *c, int enable) {
     if (!c) return PM_EINVAL;
     if (!enable) resolve_events(c);
     c->prof = enable != 0;
+    c->count_work = enable == 2;
+    return PM_OK;
+}
+
+pm_status pm_work_read(pm_ctx *c, long long *counts, int ncounts, int reset) {
+    if (!c || !counts || ncounts < 0) return PM_EINVAL;
+    ull h[8];
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "pm_work_read");
+    if (cudaMemcpy(h, c->w.wsum, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return cuda_fail(c, cudaGetLastError(), "pm_work_read");
+    for (int k = 0; k < ncounts; ++k) counts[k] = k < 8 ? (long long)h[k] : 0;
+    if (reset && cudaMemset(c->w.wsum, 0, sizeof(h)) != cudaSuccess)
+        return cuda_fail(c, cudaGetLastError(), "pm_work_read");
     return PM_OK;
 }
 

@@ -67,8 +67,11 @@ __device__ __forceinline__ int prio(int enc, const int *__restrict__ perm) {
     return id >= PM_VIRT ? 0x7ffffff0 + (id - PM_VIRT) : __ldg(perm + id);
 }
 
-#define DBLK 64  // threads per block of the triangulation kernel
-#define DMAXW 24 // working polygon capacity (>= PM_MAXDEG)
+#define DBLK 64     // threads per block of the main triangulation pass
+#define DCAP 10     // polygon capacity of the main pass (20 warps per SM)
+#define RBLK 32     // threads per block of the retry pass
+#define RCAP 24     // polygon capacity of the retry pass (= PM_MAXDEG)
+#define ST_OVERFLOW 0x40000000  // internal: the cell outgrew the main pass's capacity
 
 // Float circumcentre c of (0, a, b) and a bound e on the error of each of its
 // components (infinite when the triangle is too flat to bound). Inputs are
@@ -96,55 +99,66 @@ __device__ __forceinline__ void circumcentre(float ax, float ay, float bx, float
     if (!(e < INFINITY) || !(cm < INFINITY)) e = INFINITY;
 }
 
-// Polygon state of one thread: neighbour entry k = (x, y, code, bits of w_k)
-// with w_k = e_k + 8u |c_k| (so that the float test  2 c_k . s > |s|^2  is
-// certain outside the margin  w_k |s| + 4u |s|^2), and vertex k, the
-// circumcentre c_k of (p, q_k, q_k+1).
+// Polygon state of one thread, one column per thread in shared memory:
+// neighbour k, q[k] = (x, y, entry) with entry = sorted index | image code <<
+// 28, and vertex k, v[k] = (c_k, w_k, rr_k): the circumcentre c_k of
+// (p, q_k, q_k+1), the margin w_k = e_k + 8u |c_k| (the float test
+// 2 c_k . s > |s|^2 is certain outside w_k |s| + 4u |s|^2), and rr_k, an
+// upper bound of (|c_k| + w_k)^2 without square roots:
+// (|c| + w)^2 <= |c|^2 + 2 sqrt2 max(|cx|,|cy|) w + w^2 (infinite when the
+// vertex is unbounded).
+template <int NB>
 struct PolyS {
-    int4 (*q)[DBLK];
-    float2 (*v)[DBLK];
+    int4 (*q)[NB];
+    float4 (*v)[NB];
     int t;
 };
 
-__device__ __forceinline__ void set_vertex(PolyS P, int k, float ax, float ay, float bx, float by) {
+template <int NB>
+__device__ __forceinline__ float set_vertex(PolyS<NB> P, int k, float ax, float ay, float bx, float by) {
     float cx, cy, e;
     circumcentre(ax, ay, bx, by, cx, cy, e);
-    P.v[k][P.t] = make_float2(cx, cy);
-    float w = e + 4.8e-7f * fmaxf(fabsf(cx), fabsf(cy)) * 1.5f;
-    P.q[k][P.t].w = __float_as_int(w < INFINITY ? w : INFINITY);
+    const float cm = fmaxf(fabsf(cx), fabsf(cy));
+    float w = e + 4.8e-7f * cm * 1.5f;
+    w = w < INFINITY ? w : INFINITY;
+    float rr = (cx * cx + cy * cy) * 1.000001f + 2.8285f * cm * w + w * w;
+    rr = rr < INFINITY ? rr : INFINITY;
+    P.v[k][P.t] = make_float4(cx, cy, w, rr);
+    return rr;
 }
 
-// Upper bound of the largest (|c_k| + w_k)^2, without square roots:
-// (|c| + w)^2 <= |c|^2 + 2 sqrt2 max(|cx|,|cy|) w + w^2 (infinite if any
-// vertex is unbounded).
-__device__ __forceinline__ float max_radius2(PolyS P, int m) {
-    float R2 = 0.0f;
-    for (int k = 0; k < m; ++k) {
-        const float2 c = P.v[k][P.t];
-        const float w = __int_as_float(P.q[k][P.t].w);
-        const float rr = (c.x * c.x + c.y * c.y) * 1.000001f + 2.8285f * fmaxf(fabsf(c.x), fabsf(c.y)) * w + w * w;
-        if (!(rr < INFINITY)) return INFINITY;
-        R2 = fmaxf(R2, rr);
-    }
-    return R2;
-}
+// Work of one thread, counted by the counting instantiation of the kernel:
+// candidates examined, candidates passing the distance test, vertex tests,
+// clips, and the sum of the cell sizes after each clip.
+struct WorkCount {
+    unsigned cand = 0, tested = 0, vtests = 0, clips = 0, msum = 0;
+};
 
 // Clip the cell of p by the bisector of candidate s (relative position
-// (sx, sy), sorted index sidx, image code). Returns an error bit or 0.
-__device__ __forceinline__ int clip_by(PolyS P, int &m, float &R2, int sx, int sy, int sidx, int code, int p,
-                                       int &pp, const int *__restrict__ perm) {
+// (sx, sy), sorted index sidx, image code). R2 = max_k rr_k is kept up to
+// date: the vertices that survive a clip are those the candidate does not
+// remove, plus the two new ones. Returns an error bit or 0.
+template <int CAP, int NB, bool COUNT>
+__device__ __forceinline__ int clip_by(PolyS<NB> P, int &m, float &R2, int sx, int sy, int sidx, int code, int p,
+                                       int &pp, const int *__restrict__ perm, WorkCount &wc) {
     const float fsx = (float)sx, fsy = (float)sy;
     const float d2 = fsx * fsx + fsy * fsy;
+    if (COUNT) wc.cand++;
     if (d2 > 4.0001f * R2) return 0;  // |s| > 2 max|c|: no vertex can be cut
+    if (COUNT) {
+        wc.tested++;
+        wc.vtests += m;
+    }
     // |s| <= sqrt2 max(|sx|, |sy|) stands in for the norm in the margin
     const float hs = 0.5f * d2, ns = 1.41422f * fmaxf(fabsf(fsx), fabsf(fsy)), mr = 2.4e-7f * d2;
     unsigned mask = 0;
+    float rkeep = 0.0f;
     int ps = -2;
     const int t = P.t;
     for (int k = 0; k < m; ++k) {
-        const float2 c = P.v[k][t];
+        const float4 c = P.v[k][t];
         const float hk = c.x * fsx + c.y * fsy - hs;
-        const float mg = __int_as_float(P.q[k][t].w) * ns + mr;
+        const float mg = c.z * ns + mr;
         int v;
         if (hk > mg) v = 1;
         else if (hk < -mg) v = -1;
@@ -155,6 +169,7 @@ __device__ __forceinline__ int clip_by(PolyS P, int &m, float &R2, int sx, int s
             v = incircle_exact(A.x, A.y, Bq.x, Bq.y, sx, sy, pp, prio(A.z, perm), prio(Bq.z, perm), ps) ? 1 : -1;
         }
         if (v > 0) mask |= 1u << k;
+        else rkeep = fmaxf(rkeep, c.w);
     }
     if (mask == 0) return 0;
     const unsigned full = (1u << m) - 1u;
@@ -164,8 +179,8 @@ __device__ __forceinline__ int clip_by(PolyS P, int &m, float &R2, int sx, int s
     if (cnt >= m || __popc(starts) != 1) return ST_RANGE;
     const int i0 = __ffs(starts) - 1;  // first removed vertex; q_i0 is kept
     const int nd = cnt - 1;            // neighbours q_{i0+1..i0+nd} are removed
-    if (m - nd + 1 > DMAXW) return ST_DEGREE;
-    PM_CHK(m + 1 <= DMAXW, 204, return ST_DEGREE)
+    if (m - nd + 1 > CAP) return CAP < RCAP ? ST_OVERFLOW : ST_DEGREE;
+    PM_CHK(m - nd + 1 <= CAP, 204, return ST_DEGREE)
     const int4 S = make_int4(sx, sy, sidx | (code << 28), 0);
     int ipos;
     if (i0 + nd < m) {
@@ -197,9 +212,13 @@ __device__ __forceinline__ int clip_by(PolyS P, int &m, float &R2, int sx, int s
     }
     const int iprev = ipos == 0 ? m - 1 : ipos - 1, inext = ipos + 1 == m ? 0 : ipos + 1;
     const int4 Q = P.q[iprev][t], Nq = P.q[inext][t];
-    set_vertex(P, iprev, (float)Q.x, (float)Q.y, fsx, fsy);
-    set_vertex(P, ipos, fsx, fsy, (float)Nq.x, (float)Nq.y);
-    R2 = max_radius2(P, m);
+    const float r1 = set_vertex(P, iprev, (float)Q.x, (float)Q.y, fsx, fsy);
+    const float r2 = set_vertex(P, ipos, fsx, fsy, (float)Nq.x, (float)Nq.y);
+    R2 = fmaxf(rkeep, fmaxf(r1, r2));
+    if (COUNT) {
+        wc.clips++;
+        wc.msum += m;
+    }
     return 0;
 }
 
@@ -211,21 +230,42 @@ __device__ __forceinline__ int nb_cell(int cx, int cy, int dx, int dy, int n, in
     return (uy - oy * n) * n + (ux - ox * n);
 }
 
-// The working polygon of every thread lives in shared memory, one column per
-// thread. Candidates are taken ring by ring of cells around p until the cell
-// is certified.
-__global__ void __launch_bounds__(DBLK) k_delaunay(Geo g, ll np, const uint2 *__restrict__ pos,
-                                                   const int *__restrict__ cell_start, const int *__restrict__ perm,
-                                                   int *__restrict__ nbr, unsigned char *__restrict__ deg,
-                                                   float *__restrict__ vol, float vol_scale, int *__restrict__ status) {
-    __shared__ int4 sq[DMAXW][DBLK];
-    __shared__ float2 sv[DMAXW][DBLK];
-    const int t = threadIdx.x;
-    ll pl = (ll)blockIdx.x * blockDim.x + t;
-    if (pl >= np) return;
-    const int p = (int)pl;
+// Squared distance from p (offset (fx, fy) inside its cell, torus units) to
+// the cell (dx, dy) of its neighbourhood, rounded down a little so that a cell
+// is skipped only when every point in it is certainly farther.
+__device__ __forceinline__ float box_dist2(int dx, int dy, float fx, float fy, float cw) {
+    const float gx = dx > 0 ? (float)dx * cw - fx : (dx < 0 ? fx - (float)(dx + 1) * cw : 0.0f);
+    const float gy = dy > 0 ? (float)dy * cw - fy : (dy < 0 ? fy - (float)(dy + 1) * cw : 0.0f);
+    return (gx * gx + gy * gy) * 0.99999f;
+}
+
+__device__ __forceinline__ void cswap(unsigned &a, unsigned &b) {
+    const unsigned lo = min(a, b), hi = max(a, b);
+    a = lo;
+    b = hi;
+}
+
+// Ring-1 slot i (0..7) -> cell offset (dx, dy).
+__device__ __forceinline__ void ring1(int i, int &dx, int &dy) {
+    dx = i < 3 ? i - 1 : (i < 5 ? (i == 3 ? -1 : 1) : i - 6);
+    dy = i < 3 ? -1 : (i < 5 ? 0 : 1);
+}
+
+// The Voronoi cell (star) of one particle p. Candidates are taken ring by
+// ring of cells around p until the cell is certified. A neighbouring cell is
+// skipped when its box is farther than 2 max|c_k| (none of its points can cut
+// the cell: the same test as for a single candidate), and the eight cells of
+// the first ring are visited nearest first, so that the cell shrinks early and
+// later candidates fail the distance test. The visiting order does not change
+// the result: the Voronoi cell is unique and every decision is exact.
+// Returns 0, an error bit, or ST_OVERFLOW when the cell outgrew CAP.
+template <int CAP, int NB, bool COUNT>
+__device__ __forceinline__ int star_of(PolyS<NB> P, int p, const Geo &g, ll np, const uint2 *__restrict__ pos,
+                                       const int *__restrict__ cell_start, const int *__restrict__ perm,
+                                       int *__restrict__ nbr, unsigned char *__restrict__ deg,
+                                       float *__restrict__ vol, float vol_scale, WorkCount &wc) {
+    const int t = P.t;
     const int n = g.n;
-    PolyS P{sq, sv, t};
     int m = 4;
     // Initial cell: the square cut out by four virtual points at distance
     // B = 2^30, the largest coordinate the exact predicates take. A vertex
@@ -235,15 +275,16 @@ __global__ void __launch_bounds__(DBLK) k_delaunay(Geo g, ll np, const uint2 *__
     // ring is reported as ST_SPARSE.
     const int B = 1 << 30;
     const float hb = 0.5f * (float)B;
-    sq[0][t] = make_int4(B, 0, PM_VIRT + 0, 0);
-    sq[1][t] = make_int4(0, B, PM_VIRT + 1, 0);
-    sq[2][t] = make_int4(-B, 0, PM_VIRT + 2, 0);
-    sq[3][t] = make_int4(0, -B, PM_VIRT + 3, 0);
-    sv[0][t] = make_float2(hb, hb);
-    sv[1][t] = make_float2(-hb, hb);
-    sv[2][t] = make_float2(-hb, -hb);
-    sv[3][t] = make_float2(hb, -hb);
-    float R2 = 2.0f * hb * hb;
+    const float rb = 2.0f * hb * hb * 1.0001f;
+    P.q[0][t] = make_int4(B, 0, PM_VIRT + 0, 0);
+    P.q[1][t] = make_int4(0, B, PM_VIRT + 1, 0);
+    P.q[2][t] = make_int4(-B, 0, PM_VIRT + 2, 0);
+    P.q[3][t] = make_int4(0, -B, PM_VIRT + 3, 0);
+    P.v[0][t] = make_float4(hb, hb, 0.0f, rb);
+    P.v[1][t] = make_float4(-hb, hb, 0.0f, rb);
+    P.v[2][t] = make_float4(-hb, -hb, 0.0f, rb);
+    P.v[3][t] = make_float4(hb, -hb, 0.0f, rb);
+    float R2 = rb;
     const uint2 Xp = pos[p];
     const int cx = cell_of(Xp.x, n), cy = cell_of(Xp.y, n);
     const float cw = 4294967296.0f / (float)n;
@@ -254,56 +295,156 @@ __global__ void __launch_bounds__(DBLK) k_delaunay(Geo g, ll np, const uint2 *__
     if (rmax < 0) rmax = 0;
     int err = 0;
     bool done = false;
-    // --- rings 0, 1, 2, ... until certified. Differences of torus coordinates
+    // Candidates of one neighbouring cell. Differences of torus coordinates
     // in 32-bit arithmetic are the minimal-image offsets (all |.| < 2^31).
+    auto scan_cell = [&](int dx, int dy) {
+        if (dx != 0 || dy != 0) {
+            if (box_dist2(dx, dy, fxl, fyl, cw) > 4.0001f * R2) return;
+        }
+        int ox, oy, c = nb_cell(cx, cy, dx, dy, n, ox, oy);
+        const int code = (ox + 1) * 3 + (oy + 1);
+        PM_CHK(c >= 0 && c < g.ncell, 201, return)
+        const int s0 = __ldg(cell_start + c), s1 = __ldg(cell_start + c + 1);
+        PM_CHK(s0 >= 0 && s1 <= np && s0 <= s1, 202, return)
+        for (int s = s0; s < s1; ++s) {
+            if (s == p) continue;
+            const uint2 Xs = __ldg(pos + s);
+            const int rx = (int)(Xs.x - Xp.x), ry = (int)(Xs.y - Xp.y);
+            if ((rx | ry) == 0) { err |= ST_DUP; break; }
+            if (rx > (1 << 30) || rx < -(1 << 30) || ry > (1 << 30) || ry < -(1 << 30)) continue;
+            err |= clip_by<CAP, NB, COUNT>(P, m, R2, rx, ry, s, code, p, pp, perm, wc);
+            if (err) break;
+        }
+    };
     for (int r = 0; r <= rmax && !done && !err; ++r) {
-        const int ncells = r == 0 ? 1 : 8 * r;
-        for (int ci = 0; ci < ncells && !err; ++ci) {
-            int dx, dy;
-            if (r == 0) { dx = 0; dy = 0; }
-            else if (ci < 2 * r + 1) { dx = ci - r; dy = -r; }
-            else if (ci < 4 * r + 2) { dx = ci - (3 * r + 1); dy = r; }
-            else if (ci < 6 * r + 1) { dx = -r; dy = ci - (5 * r + 1); }
-            else { dx = r; dy = ci - (7 * r); }
-            int ox, oy, c = nb_cell(cx, cy, dx, dy, n, ox, oy);
-            const int code = (ox + 1) * 3 + (oy + 1);
-            PM_CHK(c >= 0 && c < g.ncell, 201, continue)
-            const int s0 = __ldg(cell_start + c), s1 = __ldg(cell_start + c + 1);
-            PM_CHK(s0 >= 0 && s1 <= np && s0 <= s1, 202, continue)
-            for (int s = s0; s < s1; ++s) {
-                if (s == p) continue;
-                const uint2 Xs = __ldg(pos + s);
-                const int rx = (int)(Xs.x - Xp.x), ry = (int)(Xs.y - Xp.y);
-                if ((rx | ry) == 0) { err |= ST_DUP; break; }
-                if (rx > (1 << 30) || rx < -(1 << 30) || ry > (1 << 30) || ry < -(1 << 30)) continue;
-                err |= clip_by(P, m, R2, rx, ry, s, code, p, pp, perm);
-                if (err) break;
+        if (r == 0) {
+            scan_cell(0, 0);
+        } else if (r == 1) {
+            // the eight cells of ring 1 ordered by box distance: keys hold the
+            // distance's float bits with the cell's slot in the low 3 bits
+            unsigned k[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                int dx, dy;
+                ring1(i, dx, dy);
+                k[i] = (__float_as_uint(box_dist2(dx, dy, fxl, fyl, cw)) & ~7u) | (unsigned)i;
+            }
+            // Batcher's odd-even merge sort network for 8 keys (19 exchanges)
+            cswap(k[0], k[1]); cswap(k[2], k[3]); cswap(k[4], k[5]); cswap(k[6], k[7]);
+            cswap(k[0], k[2]); cswap(k[1], k[3]); cswap(k[4], k[6]); cswap(k[5], k[7]);
+            cswap(k[1], k[2]); cswap(k[5], k[6]);
+            cswap(k[0], k[4]); cswap(k[1], k[5]); cswap(k[2], k[6]); cswap(k[3], k[7]);
+            cswap(k[2], k[4]); cswap(k[3], k[5]);
+            cswap(k[1], k[2]); cswap(k[3], k[4]); cswap(k[5], k[6]);
+            unsigned order = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) order |= (k[i] & 7u) << (3 * i);
+            for (int i = 0; i < 8 && !err; ++i) {
+                int dx, dy;
+                ring1((order >> (3 * i)) & 7, dx, dy);
+                scan_cell(dx, dy);
+            }
+        } else {
+            const int ncells = 8 * r;
+            for (int ci = 0; ci < ncells && !err; ++ci) {
+                int dx, dy;
+                if (ci < 2 * r + 1) { dx = ci - r; dy = -r; }
+                else if (ci < 4 * r + 2) { dx = ci - (3 * r + 1); dy = r; }
+                else if (ci < 6 * r + 1) { dx = -r; dy = ci - (5 * r + 1); }
+                else { dx = r; dy = ci - (7 * r); }
+                scan_cell(dx, dy);
             }
         }
         const float dmin = edge + (float)r * cw;
         if (4.0001f * R2 < dmin * dmin) done = true;
     }
-    if (!done && !err) err |= ST_SPARSE;
-    for (int k = 0; k < m && !err; ++k)
-        if ((sq[k][t].z & 0x0fffffff) >= PM_VIRT) err |= ST_SPARSE;
-    if (m > PM_MAXDEG) err |= ST_DEGREE;
-    if (err) {
-        atomicOr(status, err);
-        deg[p] = 0;
-        vol[p] = 0.0f;
-        return;
-    }
+    if (err) return err;
+    if (!done) return ST_SPARSE;
+    for (int k = 0; k < m; ++k)
+        if ((P.q[k][t].z & 0x0fffffff) >= PM_VIRT) return ST_SPARSE;
+    if (m > PM_MAXDEG) return ST_DEGREE;
+    PM_CHK(m >= 3 && m <= PM_MAXDEG, 203, return ST_DEGREE)
     ll area2 = 0;
-    PM_CHK(m >= 3 && m <= PM_MAXDEG, 203, return)
-    int4 A = sq[0][t];
+    int4 A = P.q[0][t];
     for (int k = 0; k < m; ++k) {
-        int4 Bq = sq[k + 1 == m ? 0 : k + 1][t];
+        int4 Bq = P.q[k + 1 == m ? 0 : k + 1][t];
         area2 += (ll)A.x * Bq.y - (ll)A.y * Bq.x;
         nbr[(ll)k * np + p] = A.z;
         A = Bq;
     }
     deg[p] = (unsigned char)m;
     vol[p] = (float)area2 * vol_scale;
+    return 0;
+}
+
+template <bool COUNT>
+__device__ __forceinline__ void add_counts(const WorkCount &wc, ull *__restrict__ wsum) {
+    if (!COUNT) return;
+    // warp sums, one atomic per warp and counter
+    unsigned v[5] = {wc.cand, wc.tested, wc.vtests, wc.clips, wc.msum};
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        unsigned x = v[i];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0 && x) atomicAdd(wsum + i, (ull)x);
+    }
+}
+
+// Main pass: one thread per particle, polygon capacity DCAP. A particle whose
+// cell outgrows it is appended to the retry list (no output written).
+template <bool COUNT>
+__global__ void __launch_bounds__(DBLK) k_delaunay(Geo g, ll np, const uint2 *__restrict__ pos,
+                                                   const int *__restrict__ cell_start, const int *__restrict__ perm,
+                                                   int *__restrict__ nbr, unsigned char *__restrict__ deg,
+                                                   float *__restrict__ vol, float vol_scale, int *__restrict__ status,
+                                                   int *__restrict__ retry, int *__restrict__ nretry,
+                                                   ull *__restrict__ wsum) {
+    __shared__ int4 sq[DCAP][DBLK];
+    __shared__ float4 sv[DCAP][DBLK];
+    const ll pl = (ll)blockIdx.x * DBLK + threadIdx.x;
+    WorkCount wc;
+    if (pl < np) {
+        const int p = (int)pl;
+        PolyS<DBLK> P{sq, sv, (int)threadIdx.x};
+        const int err = star_of<DCAP, DBLK, COUNT>(P, p, g, np, pos, cell_start, perm, nbr, deg, vol, vol_scale, wc);
+        if (err == ST_OVERFLOW) {
+            const int k = atomicAdd(nretry, 1);
+            PM_CHK(k >= 0 && k < np, 205, k = -1)
+            if (k >= 0) retry[k] = p;
+        } else if (err) {
+            atomicOr(status, err & ~ST_OVERFLOW);
+            deg[p] = 0;
+            vol[p] = 0.0f;
+        }
+    }
+    add_counts<COUNT>(wc, wsum);
+}
+
+// Retry pass over the listed particles with capacity RCAP (grid-stride).
+template <bool COUNT>
+__global__ void __launch_bounds__(RBLK) k_delaunay_retry(Geo g, ll np, const uint2 *__restrict__ pos,
+                                                         const int *__restrict__ cell_start,
+                                                         const int *__restrict__ perm, int *__restrict__ nbr,
+                                                         unsigned char *__restrict__ deg, float *__restrict__ vol,
+                                                         float vol_scale, int *__restrict__ status,
+                                                         const int *__restrict__ retry, const int *__restrict__ nretry,
+                                                         ull *__restrict__ wsum) {
+    __shared__ int4 sq[RCAP][RBLK];
+    __shared__ float4 sv[RCAP][RBLK];
+    const int cnt = *nretry;
+    WorkCount wc;
+    PolyS<RBLK> P{sq, sv, (int)threadIdx.x};
+    for (ll j = (ll)blockIdx.x * RBLK + threadIdx.x; j < cnt; j += (ll)gridDim.x * RBLK) {
+        const int p = retry[j];
+        PM_CHK(p >= 0 && p < np, 206, continue)
+        const int err = star_of<RCAP, RBLK, COUNT>(P, p, g, np, pos, cell_start, perm, nbr, deg, vol, vol_scale, wc);
+        if (err) {
+            atomicOr(status, (err & ~ST_OVERFLOW) | (err == ST_OVERFLOW ? ST_DEGREE : 0));
+            deg[p] = 0;
+            vol[p] = 0.0f;
+        }
+    }
+    add_counts<COUNT>(wc, wsum);
 }
 
 // 1D: v_mu = half the distance between the two neighbours on the circle.
@@ -341,13 +482,25 @@ __global__ void k_export(ll np, const uint2 *__restrict__ pos, const int *__rest
 
 }  // namespace
 
-void launch_triangulate(const Geo &g, Work &w, ll np, cudaStream_t st) {
+void launch_triangulate(const Geo &g, Work &w, ll np, cudaStream_t st, bool count_work) {
     if (np <= 0) return;
     double u = g.L / 4294967296.0;
     float scale = (float)(u * u / 6.0);
-    k_delaunay<<<div_up(np, DBLK), DBLK, 0, st>>>(g, np, w.pos, w.cell_start, w.perm, w.nbr, w.deg, w.vol, scale,
-                                                   w.status);
-    count_launches(1);
+    cudaMemsetAsync(w.nretry, 0, sizeof(int), st);
+    // w.tmp (caller indices before the canonical cell order) is free after the sort
+    const int rgrid = 4 * 152;
+    if (count_work) {
+        k_delaunay<true><<<div_up(np, DBLK), DBLK, 0, st>>>(g, np, w.pos, w.cell_start, w.perm, w.nbr, w.deg, w.vol,
+                                                             scale, w.status, w.tmp, w.nretry, w.wsum);
+        k_delaunay_retry<true><<<rgrid, RBLK, 0, st>>>(g, np, w.pos, w.cell_start, w.perm, w.nbr, w.deg, w.vol,
+                                                        scale, w.status, w.tmp, w.nretry, w.wsum);
+    } else {
+        k_delaunay<false><<<div_up(np, DBLK), DBLK, 0, st>>>(g, np, w.pos, w.cell_start, w.perm, w.nbr, w.deg,
+                                                              w.vol, scale, w.status, w.tmp, w.nretry, nullptr);
+        k_delaunay_retry<false><<<rgrid, RBLK, 0, st>>>(g, np, w.pos, w.cell_start, w.perm, w.nbr, w.deg, w.vol,
+                                                         scale, w.status, w.tmp, w.nretry, nullptr);
+    }
+    count_launches(2);
 }
 
 void launch_volumes_1d(const Geo &g, Work &w, ll np, cudaStream_t st) {

@@ -72,6 +72,8 @@ struct Work {
     // learned warm start (2D, n a multiple of 128)
     float *feat;           // [F][2][ncell] network input
     float *corr;           // [F][ncell] network output
+    ull *wsum;             // [8] triangulation work counters (counting mode)
+    int *nretry;           // particles handed to the triangulation's retry pass
 };
 
 // ---------------------------------------------------------------------------
@@ -162,7 +164,7 @@ void launch_sort(const Geo &g, Work &w, const float *px, const float *py, ll np,
                  cudaStream_t st);
 void launch_g2p(const Geo &g, const float *mesh, int F, const float *px, const float *py, ll np, float *out,
                 int *status, cudaStream_t st);
-void launch_triangulate(const Geo &g, Work &w, ll np, cudaStream_t st);
+void launch_triangulate(const Geo &g, Work &w, ll np, cudaStream_t st, bool count_work = false);
 void launch_volumes_1d(const Geo &g, Work &w, ll np, cudaStream_t st);
 void launch_delta(const Geo &g, Work &w, ll np, int F, float *mesh_out, cudaStream_t st);
 void launch_flip(const Geo &g, Work &w, ll np, int F, float *mesh_out, float *node_vol, cudaStream_t st);

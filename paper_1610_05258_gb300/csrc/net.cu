@@ -110,18 +110,32 @@ __global__ void __launch_bounds__(256) k_first(const float *__restrict__ x, int 
 
 __global__ void __launch_bounds__(256) k_last(const bf16 *__restrict__ a, int B, int n, const float *__restrict__ w3,
                                               const float *__restrict__ b3, float *__restrict__ out) {
-    __shared__ float sw[289];
-    for (int i = threadIdx.x; i < 289; i += blockDim.x) sw[i] = i < 288 ? w3[i] : b3[0];
+    // weights transposed to [tap][channel] so that one tap's 32 weights are
+    // contiguous (broadcast reads)
+    __shared__ float sw[9 * 32 + 1];
+    for (int i = threadIdx.x; i < 289; i += blockDim.x) sw[i] = i < 288 ? w3[(i % 32) * 9 + i / 32] : b3[0];
     __syncthreads();
     ll p = (ll)blockIdx.x * blockDim.x + threadIdx.x;
     const ll npx = (ll)n * n;
     if (p >= npx * B) return;
     const int img = (int)(p / npx), yx = (int)(p % npx), y = yx / n, xx = yx % n;
     float s = sw[288];
+#pragma unroll 1
     for (int t = 0; t < 9; ++t) {
         int yy = wrapn(y + t / 3 - 1, n), xs = wrapn(xx + t % 3 - 1, n);
-        const bf16 *v = a + ((ll)img * npx + (ll)yy * n + xs) * 32;
-        for (int c = 0; c < 32; ++c) s = fmaf(sw[c * 9 + t], __bfloat162float(v[c]), s);
+        const uint4 *v = (const uint4 *)(a + ((ll)img * npx + (ll)yy * n + xs) * 32);
+        const float *wt = sw + t * 32;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint4 u = __ldg(v + q);
+            const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float lo = __uint_as_float(w4[j] << 16), hi = __uint_as_float(w4[j] & 0xffff0000u);
+                s = fmaf(wt[q * 8 + 2 * j], lo, s);
+                s = fmaf(wt[q * 8 + 2 * j + 1], hi, s);
+            }
+        }
     }
     out[p] = s;
 }

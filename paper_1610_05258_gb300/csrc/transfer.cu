@@ -582,13 +582,70 @@ __global__ void k_features(Geo g, int F, const float *__restrict__ delta, const 
     }
 }
 
-// Warm start: mesh = delta + (max|A_f| / PM_NET_RSCALE) * network output.
+// Step length of the network's correction. With r0 = b - M delta (feature
+// channel 1 times max|A| h^2 / PM_NET_RSCALE) and the correction
+// c = (max|A| / PM_NET_RSCALE) corr, the start delta + alpha c has residual
+// r0 - alpha M c, smallest in the 2-norm for
+//   alpha = <r0, M c> / <M c, M c> = 36 <feat1, S corr> / <S corr, S corr>
+// (M = h^2/36 S, S the 9-point stencil 1-4-1 x 1-4-1). alpha = 0 keeps the
+// delta start, so the network can never make the start worse than delta in
+// this norm. Per-block FP64 partials, then one fixed-order reduction.
+#define ALPHA_BLOCKS 608
+__global__ void __launch_bounds__(256) k_alpha_partial(Geo g, int F, const float *__restrict__ feat,
+                                                        const float *__restrict__ corr, double *__restrict__ part) {
+    __shared__ double sh[2 * PM_MAXF][8];
+    const int n = g.n;
+    double acc[2 * PM_MAXF];
+    for (int k = 0; k < 2 * F; ++k) acc[k] = 0.0;
+    for (ll i = (ll)blockIdx.x * blockDim.x + threadIdx.x; i < g.ncell; i += (ll)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % n), iy = (int)(i / n);
+        const int xm = ix == 0 ? n - 1 : ix - 1, xp = ix + 1 == n ? 0 : ix + 1;
+        const int ym = iy == 0 ? n - 1 : iy - 1, yp = iy + 1 == n ? 0 : iy + 1;
+        for (int f = 0; f < F; ++f) {
+            const float *c = corr + (ll)f * g.ncell;
+            const float *r0 = c + (ll)ym * n, *r1 = c + (ll)iy * n, *r2 = c + (ll)yp * n;
+            const float z = 16.0f * r1[ix] + 4.0f * (r1[xm] + r1[xp] + r0[ix] + r2[ix]) +
+                            (r0[xm] + r0[xp] + r2[xm] + r2[xp]);
+            const float f1 = feat[((ll)f * 2 + 1) * g.ncell + i];
+            acc[2 * f] += (double)f1 * (double)z;
+            acc[2 * f + 1] += (double)z * (double)z;
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = 0; k < 2 * F; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[k][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * F) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += sh[threadIdx.x][w];
+        part[(ll)threadIdx.x * gridDim.x + blockIdx.x] = v;
+    }
+}
+
+__global__ void k_alpha_final(int F, int nblk, const double *__restrict__ part, double *__restrict__ alpha) {
+    const int f = threadIdx.x;
+    if (f >= F) return;
+    double num = 0.0, den = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+        num += part[(ll)(2 * f) * nblk + b];
+        den += part[(ll)(2 * f + 1) * nblk + b];
+    }
+    const double a = den > 0.0 ? 36.0 * num / den : 0.0;
+    alpha[f] = isfinite(a) ? a : 0.0;
+}
+
+// Warm start: mesh = delta + alpha_f (max|A_f| / PM_NET_RSCALE) * network output.
 __global__ void k_apply_corr(Geo g, int F, const float *__restrict__ corr, const unsigned *__restrict__ maxabs,
-                             float *__restrict__ mesh) {
+                             const double *__restrict__ alpha, float *__restrict__ mesh) {
     ll i = (ll)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.ncell) return;
-    for (int f = 0; f < F; ++f)
-        mesh[(ll)f * g.ncell + i] += __uint_as_float(maxabs[f]) * (1.0f / PM_NET_RSCALE) * corr[(ll)f * g.ncell + i];
+    for (int f = 0; f < F; ++f) {
+        const float k = (float)alpha[f] * __uint_as_float(maxabs[f]) * (1.0f / PM_NET_RSCALE);
+        mesh[(ll)f * g.ncell + i] += k * corr[(ll)f * g.ncell + i];
+    }
 }
 
 }  // namespace
@@ -599,8 +656,12 @@ void launch_features(const Geo &g, Work &w, int F, const float *delta, cudaStrea
 }
 
 void launch_apply_correction(const Geo &g, Work &w, int F, float *mesh, cudaStream_t st) {
-    k_apply_corr<<<div_up(g.ncell, 256), 256, 0, st>>>(g, F, w.corr, w.maxabs, mesh);
-    count_launches(1);
+    // scratch: the solver's reduction buffer (the solve has not started yet)
+    double *part = w.red, *alpha = w.red + 2LL * PM_MAXF * ALPHA_BLOCKS;
+    k_alpha_partial<<<ALPHA_BLOCKS, 256, 0, st>>>(g, F, w.feat, w.corr, part);
+    k_alpha_final<<<1, 32, 0, st>>>(F, ALPHA_BLOCKS, part, alpha);
+    k_apply_corr<<<div_up(g.ncell, 256), 256, 0, st>>>(g, F, w.corr, w.maxabs, alpha, mesh);
+    count_launches(3);
 }
 
 void launch_delta(const Geo &g, Work &w, ll np, int F, float *mesh_out, cudaStream_t st) {

@@ -240,3 +240,65 @@ def test_nonfinite_and_coincident_positions(built):
     px, py, vals = dev(inst)
     out, info = c.assign_mass(px, py, vals)
     assert info[0].rel_resid <= 1e-6
+
+
+# ---------------------------------------------------------------------------
+# high-degree particles: the working Voronoi cell outgrows the main pass's
+# capacity and the particle goes through the retry pass
+# ---------------------------------------------------------------------------
+def flowers(petals, n=32, ppc=2, seed=77):
+    """Uniform background with "flowers": a centre particle ringed by k
+    particles at 0.3 cell widths (angles jittered), so that the centre's
+    Delaunay degree is k."""
+    g = np.random.default_rng(seed)
+    h = 1.0 / n
+    rho = 0.3 * h
+    cen = [((i + 0.5) / len(petals) * 0.9 + 0.05, 0.5 + 0.3 * ((-1) ** i)) for i in range(len(petals))]
+    pts = []
+    for (cx, cy), k in zip(cen, petals):
+        pts.append((cx, cy))
+        ang = 2 * np.pi * (np.arange(k) + 0.2 * g.uniform(-1, 1, k)) / k
+        pts += list(zip(cx + rho * np.cos(ang), cy + rho * np.sin(ang)))
+    bg = g.uniform(0.0, 1.0, (ppc * n * n, 2))
+    keep = np.ones(len(bg), bool)
+    for cx, cy in cen:
+        d = np.hypot((bg[:, 0] - cx + 0.5) % 1.0 - 0.5, (bg[:, 1] - cy + 0.5) % 1.0 - 0.5)
+        keep &= d > 2.5 * rho
+    pts = np.concatenate([np.array(pts), bg[keep]])
+    return pts[:, 0].astype(np.float32), pts[:, 1].astype(np.float32)
+
+
+def test_triangulation_high_degree_retry(built):
+    from paper_1610_05258_gb300 import Context
+    px, py = flowers([11, 12, 14, 16, 20, 23])
+    c = Context(2, 32, 1.0, px.size, 1)
+    dpx, dpy = to_dev(torch, px, py)
+    tri, off = c.triangulate(dpx, dpy)
+    got = canon_tris(tri.cpu().numpy(), off.cpu().numpy())
+    t, o, _ = oracle.triangulate(1.0, px, py)
+    assert got == canon_tris(t, o)
+    # the centres have the planted degrees
+    deg = np.bincount(np.asarray(t).ravel(), minlength=px.size)
+    assert sorted(deg[[0, 12, 25, 40, 57, 78]].tolist()) == [11, 12, 14, 16, 20, 23]
+    vals = np.ones((1, px.size), np.float32)
+    (dv,) = to_dev(torch, vals)
+    out, info = c.assign_mass(dpx, dpy, dv)
+    assert np.abs(out.cpu().numpy() - 1.0).max() <= 1e-5
+
+
+def test_triangulation_degree_above_capacity(built):
+    """A particle with more than 24 Delaunay neighbours is reported, never a fault."""
+    from paper_1610_05258_gb300 import Context, PMError
+    px, py = flowers([30])
+    c = Context(2, 32, 1.0, px.size, 1)
+    dpx, dpy = to_dev(torch, px, py)
+    vals = torch.ones(1, px.size, device="cuda")
+    with pytest.raises(PMError) as e:
+        c.assign_mass(dpx, dpy, vals)
+    assert e.value.status == 5
+    # the context stays usable
+    qx, qy = flowers([16])
+    c2 = Context(2, 32, 1.0, qx.size, 1)
+    a, b = to_dev(torch, qx, qy)
+    out, info = c2.assign_mass(a, b, torch.ones(1, qx.size, device="cuda"))
+    assert info[0].rel_resid <= 1e-6
