@@ -212,6 +212,7 @@ pm_status pm_ctx_create(pm_ctx **out, int dim, int n, double L, long long max_pa
         cudaGetLastError();
         return PM_ENOMEM;
     }
+    rhs_prepare_device();
     cudaMemset(w.status, 0, sizeof(int));
     cudaMemset(w.scal, 0, sizeof(double) * 16 * PM_MAXF);
     cudaMemset(w.wsum, 0, sizeof(ull) * 8);

@@ -168,6 +168,7 @@ void launch_triangulate(const Geo &g, Work &w, ll np, cudaStream_t st, bool coun
 void launch_volumes_1d(const Geo &g, Work &w, ll np, cudaStream_t st);
 void launch_delta(const Geo &g, Work &w, ll np, int F, float *mesh_out, cudaStream_t st);
 void launch_flip(const Geo &g, Work &w, ll np, int F, float *mesh_out, float *node_vol, cudaStream_t st);
+void rhs_prepare_device();
 void launch_rhs(const Geo &g, Work &w, ll np, int F, cudaStream_t st);
 void launch_rhs_to_float(const Geo &g, Work &w, int F, float *b_out, cudaStream_t st);
 void launch_mass_apply(const Geo &g, const float *x, int F, float *y, cudaStream_t st);

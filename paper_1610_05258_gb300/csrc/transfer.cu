@@ -303,25 +303,46 @@ __device__ __forceinline__ bool owned_tri(int p, int m, int k, uint2 Xp, float u
     return true;
 }
 
+// Exact 64-bit accumulation with native 32-bit shared-memory atomics: the
+// low word returns its old value, the carry out of it goes into the high word
+// together with the high half of the addend (sums modulo 2^64, any order).
+__device__ __forceinline__ void add64_split(unsigned *lo, unsigned *hi, ull v) {
+    const unsigned vl = (unsigned)v, vh = (unsigned)(v >> 32);
+    const unsigned old = atomicAdd(lo, vl);
+    const unsigned carry = (unsigned)(old + vl < old);
+    if (vh + carry) atomicAdd(hi, vh + carry);
+}
+
+#define RTAB 24  // owned-triangle table entries per particle (>= PM_MAXDEG)
+
 // One block per tile of RTS x RTS cells. The (triangle, cell) pieces of the
 // triangles owned by the tile's particles are spread evenly over the lanes of
 // each warp (prefix sum of per-particle piece counts, then every lane takes
 // one piece per round), integrated exactly, and their four corner integrals
 // go to a shared window of nodes (64-bit fixed point, order-free integer
-// sums) or, outside the window, straight to global memory.
+// sums) or, outside the window, straight to global memory. While counting,
+// every lane records its owned triangles (star slot, running piece count) so
+// that a piece finds its triangle without walking the star again.
 template <int FF>
 __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__restrict__ pos,
                                                const int *__restrict__ cell_start, const int *__restrict__ nbr,
                                                const unsigned char *__restrict__ deg, const float *__restrict__ vals,
                                                int F, const unsigned *__restrict__ maxabs, ll *__restrict__ bfix,
                                                int tiles_x) {
-    __shared__ ull acc[FF][RWIN * RWIN];
+    // dynamic shared memory: acc_lo, acc_hi [FF][RWIN^2], tab [RTAB][256]
+    extern __shared__ unsigned rhs_smem[];
+    unsigned(*acc_lo)[RWIN * RWIN] = (unsigned(*)[RWIN * RWIN])rhs_smem;
+    unsigned(*acc_hi)[RWIN * RWIN] = (unsigned(*)[RWIN * RWIN])(rhs_smem + FF * RWIN * RWIN);
+    unsigned(*tab)[256] = (unsigned(*)[256])(rhs_smem + 2 * FF * RWIN * RWIN);  // (star slot << 16) | pieces so far
     __shared__ int rowpre[RTS + 1];
     __shared__ int rowbeg[RTS];
     const int n = g.n;
     const int tx0 = (blockIdx.x % tiles_x) * RTS, ty0 = (blockIdx.x / tiles_x) * RTS;
     const int wx0 = tx0 - RHALO, wy0 = ty0 - RHALO;
-    for (int i = threadIdx.x; i < FF * RWIN * RWIN; i += blockDim.x) (&acc[0][0])[i] = 0ull;
+    for (int i = threadIdx.x; i < FF * RWIN * RWIN; i += blockDim.x) {
+        (&acc_lo[0][0])[i] = 0u;
+        (&acc_hi[0][0])[i] = 0u;
+    }
     if (threadIdx.x == 0) {
         int tot = 0;
         const int xe = min(tx0 + RTS, n);
@@ -344,8 +365,9 @@ __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__rest
     for (int f = 0; f < FF; ++f) E[f] = f < F ? fix_exp(maxabs, f, hd) : 0;
     const int total = rowpre[RTS];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int tcol = threadIdx.x;
     for (int base = wid * 32; base < total; base += nw * 32) {
-        // this lane's particle and its number of pieces
+        // this lane's particle, its owned triangles and its number of pieces
         const int k = base + lane;
         int p = -1, cnt = 0;
         if (k < total) {
@@ -357,13 +379,19 @@ __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__rest
             if (m >= 3) {
                 const uint2 Xp = pos[p];
                 const float up = frac_f(Xp.x, n), wp = frac_f(Xp.y, n);
+                int nt = 0;
                 for (int kk = 0; kk < m; ++kk) {
                     Tri T;
-                    if (owned_tri(p, m, kk, Xp, up, wp, sc, pos, nbr, np, T))
+                    if (owned_tri(p, m, kk, Xp, up, wp, sc, pos, nbr, np, T)) {
                         cnt += (T.i1 - T.i0 + 1) * (T.j1 - T.j0 + 1);
+                        PM_CHK(nt < RTAB, 307, break)
+                        tab[nt][tcol] = ((unsigned)kk << 16) | (unsigned)cnt;
+                        ++nt;
+                    }
                 }
             }
         }
+        __syncwarp();
         int incl = cnt;
         for (int o = 1; o < 32; o <<= 1) {
             int v = __shfl_up_sync(0xffffffffu, incl, o);
@@ -383,27 +411,26 @@ __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__rest
             const int ps = __shfl_sync(0xffffffffu, p, src);
             const int jj = j - __shfl_sync(0xffffffffu, excl, src);
             if (j >= T_all) continue;
-            // locate the piece inside particle ps
+            // locate the piece: the owner's table gives the star slot
             PM_CHK(ps >= 0 && ps < np, 304, continue)
+            const int scol = (tcol & ~31) + src;
+            int e = 0, prev = 0;
+            unsigned te = tab[0][scol];
+            while ((int)(te & 0xffffu) <= jj) {
+                prev = (int)(te & 0xffffu);
+                ++e;
+                PM_CHK(e < RTAB, 308, break)
+                te = tab[e][scol];
+            }
+            const int kk = (int)(te >> 16), rem = jj - prev;
             const int m = deg[ps];
             const uint2 Xp = pos[ps];
             const int cxp = cell_of(Xp.x, n), cyp = cell_of(Xp.y, n);
             const float up = frac_f(Xp.x, n), wp = frac_f(Xp.y, n);
             Tri T;
-            int rem = jj, ci = 0, cj = 0;
-            bool found = false;
-            for (int kk = 0; kk < m && !found; ++kk) {
-                if (!owned_tri(ps, m, kk, Xp, up, wp, sc, pos, nbr, np, T)) continue;
-                const int w = T.i1 - T.i0 + 1, c = w * (T.j1 - T.j0 + 1);
-                if (rem < c) {
-                    ci = T.i0 + rem % w;
-                    cj = T.j0 + rem / w;
-                    found = true;
-                } else {
-                    rem -= c;
-                }
-            }
-            if (!found) continue;
+            if (!owned_tri(ps, m, kk, Xp, up, wp, sc, pos, nbr, np, T)) continue;
+            const int wdt = T.i1 - T.i0 + 1;
+            const int ci = T.i0 + rem % wdt, cj = T.j0 + rem / wdt;
             PM_CHK(T.a >= 0 && T.a < np && T.b >= 0 && T.b < np, 305, continue)
             const float fci = (float)ci, fcj = (float)cj;
             const float xmin = fminf(T.vx[0], fminf(T.vx[1], T.vx[2])), xmax = fmaxf(T.vx[0], fmaxf(T.vx[1], T.vx[2]));
@@ -457,19 +484,20 @@ __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__rest
                     const ll iv = __float2ll_rn(ldexpf(val, E[f]));
                     if (!iv) continue;
                     if (inwin)
-                        atomicAdd(&acc[f][ly * RWIN + lx], (ull)iv);
+                        add64_split(&acc_lo[f][ly * RWIN + lx], &acc_hi[f][ly * RWIN + lx], (ull)iv);
                     else
                         atomicAdd((ull *)&bfix[(ll)f * g.ncell + node], (ull)iv);
                 }
             }
         }
+        __syncwarp();
     }
     __syncthreads();
     for (int i = threadIdx.x; i < RWIN * RWIN; i += blockDim.x) {
         const int lx = i % RWIN, ly = i / RWIN;
         const ll node = (ll)wrapi(wy0 + ly, n) * n + wrapi(wx0 + lx, n);
         for (int f = 0; f < F && f < FF; ++f) {
-            ull v = acc[f][i];
+            const ull v = ((ull)acc_hi[f][i] << 32) | (ull)acc_lo[f][i];
             if (v) atomicAdd((ull *)&bfix[(ll)f * g.ncell + node], v);
         }
     }
@@ -684,18 +712,37 @@ void launch_flip(const Geo &g, Work &w, ll np, int F, float *mesh_out, float *no
     count_launches(2);
 }
 
+template <int FF>
+static size_t rhs2d_smem() {
+    return sizeof(unsigned) * (2 * FF * RWIN * RWIN + RTAB * 256);
+}
+
+// Raise the dynamic shared-memory limit of the RHS kernels on the current
+// device (called when a context is created, outside any stream capture).
+void rhs_prepare_device() {
+    cudaFuncSetAttribute(k_rhs2d<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs2d_smem<2>());
+    cudaFuncSetAttribute(k_rhs2d<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs2d_smem<4>());
+    cudaFuncSetAttribute(k_rhs2d<PM_MAXF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)rhs2d_smem<PM_MAXF>());
+}
+
+template <int FF>
+static void launch_rhs2d(const Geo &g, Work &w, ll np, int F, int nt, int tx, cudaStream_t st) {
+    const size_t bytes = rhs2d_smem<FF>();
+    k_rhs2d<FF><<<nt, 256, bytes, st>>>(g, np, w.pos, w.cell_start, w.nbr, w.deg, w.vals, F, w.maxabs, w.bfix, tx);
+}
+
 void launch_rhs(const Geo &g, Work &w, ll np, int F, cudaStream_t st) {
     cudaMemsetAsync(w.bfix, 0, sizeof(ll) * g.ncell * F, st);
     if (np <= 0) return;
     if (g.dim == 2) {
         const int tx = div_up(g.n, RTS), nt = tx * tx;
         if (F <= 2)
-            k_rhs2d<2><<<nt, 256, 0, st>>>(g, np, w.pos, w.cell_start, w.nbr, w.deg, w.vals, F, w.maxabs, w.bfix, tx);
+            launch_rhs2d<2>(g, w, np, F, nt, tx, st);
         else if (F <= 4)
-            k_rhs2d<4><<<nt, 256, 0, st>>>(g, np, w.pos, w.cell_start, w.nbr, w.deg, w.vals, F, w.maxabs, w.bfix, tx);
+            launch_rhs2d<4>(g, w, np, F, nt, tx, st);
         else
-            k_rhs2d<PM_MAXF><<<nt, 256, 0, st>>>(g, np, w.pos, w.cell_start, w.nbr, w.deg, w.vals, F, w.maxabs, w.bfix,
-                                                 tx);
+            launch_rhs2d<PM_MAXF>(g, w, np, F, nt, tx, st);
     } else
         k_rhs1d<<<div_up(np, 128), 128, 0, st>>>(g, np, w.pos, w.vals, F, w.maxabs, w.bfix);
     count_launches(1);
