@@ -361,6 +361,321 @@ __global__ void __launch_bounds__(256) k_cg(CG a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// 2D solve on quads of 4 consecutive nodes of a row (n % 4 == 0): the same
+// algorithm and the same per-node arithmetic as k_cg<2>, with 16-byte loads
+// and stores so that enough bytes are in flight to stream the vectors at HBM
+// speed from a persistent grid.
+// ---------------------------------------------------------------------------
+struct Q4 {
+    float v[4];
+};
+
+__device__ __forceinline__ Q4 ld4(const float *p) {
+    const float4 t = *(const float4 *)p;
+    return Q4{{t.x, t.y, t.z, t.w}};
+}
+__device__ __forceinline__ void st4(float *p, const Q4 &q) { *(float4 *)p = make_float4(q.v[0], q.v[1], q.v[2], q.v[3]); }
+
+// Compensated stencil sums (hi, lo) of the 4 nodes starting at flat index i0
+// (i0 % 4 == 0), in the same addition order as stencil<2>.
+__device__ __forceinline__ void stencil4(const float *__restrict__ xf, int n, ll i0, float hi[4], float lo[4],
+                                         float ctr[4]) {
+    const int ix = (int)(i0 % n), iy = (int)(i0 / n);
+    const int ym = iy == 0 ? n - 1 : iy - 1, yp = iy + 1 == n ? 0 : iy + 1;
+    const int xl = ix == 0 ? n - 1 : ix - 1, xr = ix + 4 == n ? 0 : ix + 4;
+    const float *R0 = xf + (ll)ym * n, *R1 = xf + (ll)iy * n, *R2 = xf + (ll)yp * n;
+    const Q4 a = ld4(R0 + ix), b = ld4(R1 + ix), c = ld4(R2 + ix);
+    const float a_l = R0[xl], a_r = R0[xr], b_l = R1[xl], b_r = R1[xr], c_l = R2[xl], c_r = R2[xr];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float am = j == 0 ? a_l : a.v[j - 1], ap = j == 3 ? a_r : a.v[j + 1];
+        const float bm = j == 0 ? b_l : b.v[j - 1], bp = j == 3 ? b_r : b.v[j + 1];
+        const float cm = j == 0 ? c_l : c.v[j - 1], cp = j == 3 ? c_r : c.v[j + 1];
+        Dot2 acc;
+        acc.add(16.0f * b.v[j]);
+        acc.add(4.0f * bm);
+        acc.add(4.0f * bp);
+        acc.add(4.0f * a.v[j]);
+        acc.add(4.0f * c.v[j]);
+        acc.add(am);
+        acc.add(ap);
+        acc.add(cm);
+        acc.add(cp);
+        hi[j] = acc.hi;
+        lo[j] = acc.lo;
+        ctr[j] = b.v[j];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_cg2v(CG a) {
+    const Geo g = a.g;
+    const int F = a.F, n = g.n;
+    const ll nn = g.ncell, nq = nn / 4;
+    const ll tid = (ll)blockIdx.x * blockDim.x + threadIdx.x, nth = (ll)gridDim.x * blockDim.x;
+    const float c = g.h * g.h / 36.0f;
+    const double hd = (double)g.h * g.h;
+    double v[PM_MAXF], w[PM_MAXF];
+    double bb[PM_MAXF], rr[PM_MAXF], alpha[PM_MAXF], beta[PM_MAXF];
+    bool act[PM_MAXF];
+    int it_f[PM_MAXF];
+    float *__restrict__ X = a.x;
+    float *__restrict__ R = a.r;
+    float *__restrict__ P = a.p;
+    float *__restrict__ Qv = a.q;
+    float *__restrict__ B = a.b;
+    // --- phase 0: right-hand side as float, its sum and norm, sum of start
+    for (int f = 0; f < F; ++f) {
+        Dot2 sb, s2, sx;
+        const float hd32 = g.h * g.h;
+        int E = 0;
+        if (a.bfix) {
+            float m = __uint_as_float(a.maxabs[f]) * hd32;
+            if (m > 0.0f) { frexpf(m, &E); E = 60 - E; }
+        }
+        for (ll qd = tid; qd < nq; qd += nth) {
+            const ll o = (ll)f * nn + qd * 4;
+            Q4 bv;
+            if (a.bfix) {
+                const longlong2 u = *(const longlong2 *)(a.bfix + o), w2 = *(const longlong2 *)(a.bfix + o + 2);
+                bv.v[0] = ldexpf((float)u.x, -E);
+                bv.v[1] = ldexpf((float)u.y, -E);
+                bv.v[2] = ldexpf((float)w2.x, -E);
+                bv.v[3] = ldexpf((float)w2.y, -E);
+            } else {
+                bv = ld4(a.bsrc + o);
+            }
+            st4(B + o, bv);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                sb.add(bv.v[j]);
+                s2.fma_acc(bv.v[j], bv.v[j]);
+            }
+            if (a.has_start) {
+                const Q4 xv = ld4(X + o);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) sx.add(xv.v[j]);
+            }
+        }
+        v[f] = (double)sb.hi + (double)sb.lo;
+        w[f] = (double)s2.hi + (double)s2.lo;
+        alpha[f] = (double)sx.hi + (double)sx.lo;
+    }
+    block_partial(v, F, a.red, 0);
+    block_partial(w, F, a.red, 1);
+    block_partial(alpha, F, a.red, 2);
+    if (!grid_sync(a.bar, a.status)) return;
+    double sumb[PM_MAXF], sumx[PM_MAXF];
+    grid_total(a.red, F, 0, sumb);
+    grid_total(a.red, F, 1, bb);
+    grid_total(a.red, F, 2, sumx);
+    // exact mean mode: mean(x) = sum b / (nn h^2)
+    for (int f = 0; f < F; ++f) {
+        const double shift = sumb[f] / ((double)nn * hd) - (a.has_start ? sumx[f] / (double)nn : 0.0);
+        const float sh = (float)shift;
+        for (ll qd = tid; qd < nq; qd += nth) {
+            const ll o = (ll)f * nn + qd * 4;
+            Q4 xv = a.has_start ? ld4(X + o) : Q4{{0.0f, 0.0f, 0.0f, 0.0f}};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) xv.v[j] += sh;
+            st4(X + o, xv);
+        }
+    }
+    if (!grid_sync(a.bar, a.status)) return;
+    // --- r = b - M x, p = r
+    for (int f = 0; f < F; ++f) {
+        Dot2 s;
+        const float *xf = X + (ll)f * nn;
+        for (ll qd = tid; qd < nq; qd += nth) {
+            const ll o = (ll)f * nn + qd * 4;
+            float hi[4], lo[4], ct[4];
+            stencil4(xf, n, qd * 4, hi, lo, ct);
+            const Q4 bv = ld4(B + o);
+            Q4 rv;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                rv.v[j] = fmaf(-c, hi[j], bv.v[j]) - c * lo[j];
+                s.fma_acc(rv.v[j], rv.v[j]);
+            }
+            st4(R + o, rv);
+            st4(P + o, rv);
+        }
+        v[f] = (double)s.hi + (double)s.lo;
+    }
+    block_partial(v, F, a.red, 0);
+    if (!grid_sync(a.bar, a.status)) return;
+    grid_total(a.red, F, 0, rr);
+    const double tol2 = a.rtol * a.rtol;
+    for (int f = 0; f < F; ++f) {
+        act[f] = rr[f] > tol2 * bb[f] && bb[f] > 0.0;
+        it_f[f] = 0;
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            a.scal[f * 16 + S_INIT] = bb[f] > 0.0 ? sqrt(rr[f] / bb[f]) : 0.0;
+    }
+    // squared true residual of field f (and optionally restart r = p = it)
+    auto true_resid = [&](int f, bool restart) {
+        Dot2 s;
+        const float *xf = X + (ll)f * nn;
+        for (ll qd = tid; qd < nq; qd += nth) {
+            const ll o = (ll)f * nn + qd * 4;
+            float hi[4], lo[4], ct[4];
+            stencil4(xf, n, qd * 4, hi, lo, ct);
+            const Q4 bv = ld4(B + o);
+            Q4 rv;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                rv.v[j] = fmaf(-c, hi[j], bv.v[j]) - c * lo[j];
+                s.fma_acc(rv.v[j], rv.v[j]);
+            }
+            if (restart) {
+                st4(R + o, rv);
+                st4(P + o, rv);
+            }
+        }
+        return (double)s.hi + (double)s.lo;
+    };
+    int restarts = 0;
+    for (int it = 0; it < a.max_iter; ++it) {
+        bool any = false;
+        for (int f = 0; f < F; ++f) any |= act[f];
+        if (!any) {
+            // recursive residuals converged: check the true residual once
+            for (int f = 0; f < F; ++f) v[f] = true_resid(f, false);
+            block_partial(v, F, a.red, 0);
+            if (!grid_sync(a.bar, a.status)) return;
+            double tr[PM_MAXF];
+            grid_total(a.red, F, 0, tr);
+            bool again = false;
+            for (int f = 0; f < F; ++f)
+                if (bb[f] > 0.0 && tr[f] > tol2 * bb[f]) { act[f] = true; again = true; }
+            if (!again || restarts >= 3) break;
+            ++restarts;
+            // restart the drifted fields from their true residual
+            for (int f = 0; f < F; ++f) v[f] = act[f] ? true_resid(f, true) : 0.0;
+            block_partial(v, F, a.red, 0);
+            if (!grid_sync(a.bar, a.status)) return;
+            grid_total(a.red, F, 0, w);
+            for (int f = 0; f < F; ++f)
+                if (act[f]) rr[f] = w[f];
+        }
+        // q = M p, (p, q)
+        for (int f = 0; f < F; ++f) {
+            v[f] = 0.0;
+            if (!act[f]) continue;
+            Dot2 s;
+            const float *pf = P + (ll)f * nn;
+            for (ll qd = tid; qd < nq; qd += nth) {
+                float hi[4], lo[4], ct[4];
+                stencil4(pf, n, qd * 4, hi, lo, ct);
+                Q4 qv;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    qv.v[j] = fmaf(c, hi[j], c * lo[j]);
+                    s.fma_acc(ct[j], qv.v[j]);
+                }
+                st4(Qv + (ll)f * nn + qd * 4, qv);
+            }
+            v[f] = (double)s.hi + (double)s.lo;
+        }
+        block_partial(v, F, a.red, 0);
+        if (!grid_sync(a.bar, a.status)) return;
+        grid_total(a.red, F, 0, w);
+        // x += alpha p, r -= alpha q, (r, r)
+        for (int f = 0; f < F; ++f) {
+            v[f] = 0.0;
+            if (!act[f]) continue;
+            alpha[f] = rr[f] / w[f];
+            const float al = (float)alpha[f];
+            Dot2 s;
+            for (ll qd = tid; qd < nq; qd += nth) {
+                const ll o = (ll)f * nn + qd * 4;
+                Q4 xv = ld4(X + o), pv = ld4(P + o), qv = ld4(Qv + o), rv = ld4(R + o);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    xv.v[j] = fmaf(al, pv.v[j], xv.v[j]);
+                    rv.v[j] = fmaf(-al, qv.v[j], rv.v[j]);
+                    s.fma_acc(rv.v[j], rv.v[j]);
+                }
+                st4(X + o, xv);
+                st4(R + o, rv);
+            }
+            v[f] = (double)s.hi + (double)s.lo;
+        }
+        block_partial(v, F, a.red, 0);
+        if (!grid_sync(a.bar, a.status)) return;
+        grid_total(a.red, F, 0, w);
+        for (int f = 0; f < F; ++f) {
+            if (!act[f]) continue;
+            beta[f] = w[f] / rr[f];
+            rr[f] = w[f];
+            ++it_f[f];
+            if (rr[f] <= tol2 * bb[f]) act[f] = false;
+        }
+        // p = r + beta p
+        for (int f = 0; f < F; ++f) {
+            if (!act[f]) continue;
+            const float be = (float)beta[f];
+            for (ll qd = tid; qd < nq; qd += nth) {
+                const ll o = (ll)f * nn + qd * 4;
+                Q4 pv = ld4(P + o);
+                const Q4 rv = ld4(R + o);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) pv.v[j] = fmaf(be, pv.v[j], rv.v[j]);
+                st4(P + o, pv);
+            }
+        }
+        if (!grid_sync(a.bar, a.status)) return;
+    }
+    // --- report: true residual and sum of the mesh field
+    for (int f = 0; f < F; ++f) {
+        Dot2 s, sx;
+        const float *xf = X + (ll)f * nn;
+        for (ll qd = tid; qd < nq; qd += nth) {
+            const ll o = (ll)f * nn + qd * 4;
+            float hi[4], lo[4], ct[4];
+            stencil4(xf, n, qd * 4, hi, lo, ct);
+            const Q4 bv = ld4(B + o);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float rv = fmaf(-c, hi[j], bv.v[j]) - c * lo[j];
+                s.fma_acc(rv, rv);
+                sx.add(ct[j]);
+            }
+        }
+        v[f] = (double)s.hi + (double)s.lo;
+        w[f] = (double)sx.hi + (double)sx.lo;
+    }
+    block_partial(v, F, a.red, 0);
+    block_partial(w, F, a.red, 1);
+    if (!grid_sync(a.bar, a.status)) return;
+    double tr[PM_MAXF], sx[PM_MAXF];
+    grid_total(a.red, F, 0, tr);
+    grid_total(a.red, F, 1, sx);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        bool bad = false;
+        for (int f = 0; f < F; ++f) {
+            double res = bb[f] > 0.0 ? sqrt(tr[f] / bb[f]) : 0.0;
+            a.scal[f * 16 + S_ITERS] = it_f[f];
+            a.scal[f * 16 + S_RESID] = res;
+            a.scal[f * 16 + S_SUMMESH] = sx[f] * hd;
+            if (a.psum) {
+                double s1 = 0, s2 = 0;
+                for (int k = 0; k < a.nblk_psum; ++k) {
+                    s1 += a.psum[(ll)(2 * f) * a.nblk_psum + k];
+                    s2 += a.psum[(ll)(2 * f + 1) * a.nblk_psum + k];
+                }
+                a.scal[f * 16 + S_SUMPART] = s1;
+                a.scal[f * 16 + S_SUMABS] = s2;
+            } else {
+                a.scal[f * 16 + S_SUMPART] = sumb[f];
+                a.scal[f * 16 + S_SUMABS] = 0.0;
+            }
+            if (res > a.rtol) bad = true;
+        }
+        if (bad) atomicOr(a.status, ST_NOTCONV);
+    }
+}
+
 template <int DIM>
 __global__ void k_mass_apply(Geo g, const float *__restrict__ x, int F, float *__restrict__ y) {
     ll i = (ll)blockIdx.x * blockDim.x + threadIdx.x;
@@ -373,7 +688,7 @@ __global__ void k_mass_apply(Geo g, const float *__restrict__ x, int F, float *_
     }
 }
 
-int g_cg_grid[2] = {0, 0};
+int g_cg_grid[3] = {0, 0, 0};
 
 }  // namespace
 
@@ -408,19 +723,21 @@ int launch_cg(const Geo &g, Work &w, int F, const float *b_float, bool b_from_fi
     a.has_start = x_has_start ? 1 : 0;
     a.psum = b_from_fix ? w.psum : nullptr;
     a.nblk_psum = w.nblk_psum;
-    const int di = g.dim - 1;
-    void (*kern)(CG) = g.dim == 1 ? k_cg<1> : k_cg<2>;
+    // 2D meshes with n % 4 == 0 take the quad kernel (16-byte accesses)
+    const bool quad = g.dim == 2 && g.n % 4 == 0;
+    const int di = quad ? 2 : g.dim - 1;
+    void (*kern)(CG) = quad ? k_cg2v : (g.dim == 1 ? k_cg<1> : k_cg<2>);
     if (!g_cg_grid[di]) {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, 0);
         if (per < 1) per = 1;
-        if (per > 2) per = 2;
+        if (per > (quad ? 4 : 2)) per = quad ? 4 : 2;
         g_cg_grid[di] = sms * per;
     }
     int grid = g_cg_grid[di];
-    ll need = (g.ncell + 255) / 256;
+    ll need = ((quad ? g.ncell / 4 : g.ncell) + 255) / 256;
     if (need < grid) grid = (int)(need < 1 ? 1 : need);
     cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st);
     void *args[] = {&a};
