@@ -44,26 +44,75 @@ __device__ __forceinline__ int fix_exp(const unsigned *maxabs, int f, float hd) 
 }
 
 // Sign of orient(U, V, Q) with Q perturbed by (eps, eps^2) (ties never zero).
-__device__ __forceinline__ int orient_pert(ll ux, ll uy, ll vx, ll vy, ll qx, ll qy) {
+__device__ __noinline__ int orient_pert_exact(ll ux, ll uy, ll vx, ll vy, ll qx, ll qy) {
     i128 o = (i128)(vx - ux) * (qy - uy) - (i128)(vy - uy) * (qx - ux);
     if (o != 0) return o > 0 ? 1 : -1;
     if (vy != uy) return vy > uy ? -1 : 1;
     return vx > ux ? 1 : -1;
 }
 
+// The same sign, decided in float when the float value clears a rigorous
+// bound: with d1..d4 the exact integer differences, each converted with
+// relative error <= u = 2^-24, the products carry <= 3.01u and the
+// subtraction u, so |o_f - o| <= 4.1u (|t1| + |t2|); 8u is used. Otherwise
+// (in particular for exact ties) the 128-bit evaluation decides.
+__device__ __forceinline__ int orient_pert(ll ux, ll uy, ll vx, ll vy, ll qx, ll qy) {
+    const float t1 = (float)(vx - ux) * (float)(qy - uy);
+    const float t2 = (float)(vy - uy) * (float)(qx - ux);
+    const float o = t1 - t2, bound = 4.77e-7f * (fabsf(t1) + fabsf(t2));
+    if (o > bound) return 1;
+    if (o < -bound) return -1;
+    return orient_pert_exact(ux, uy, vx, vy, qx, qy);
+}
+
 // ---------------------------------------------------------------------------
 // delta assignment
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_delta2d(Geo g, ll np, const uint2 *__restrict__ pos,
+// Nodes inside the triangle (p, a, b) (relative torus coordinates of a and b
+// given; p at Xp) get the linear interpolant of the particle values, Eq.
+// delta. A node is inside when all three orientations are non-negative with
+// the node perturbed by (eps, eps^2), so that every node belongs to exactly
+// one triangle.
+__device__ __forceinline__ void delta_tri(const Geo &g, ll np, int p, int ida, int idb, uint2 Xp, ll ax, ll ay,
+                                          ll bx, ll by, const float *__restrict__ vals, int F,
+                                          float *__restrict__ mesh) {
+    const int n = g.n;
+    const ll Xn = (ll)Xp.x * n, Yn = (ll)Xp.y * n;
+    const float sc = (float)n * 2.3283064365386963e-10f;  // torus units -> cell units
+    const ll Ax = ax * n, Ay = ay * n, Bx = bx * n, By = by * n;
+    ll xlo = min(0LL, min(Ax, Bx)) + Xn, xhi = max(0LL, max(Ax, Bx)) + Xn;
+    ll ylo = min(0LL, min(Ay, By)) + Yn, yhi = max(0LL, max(Ay, By)) + Yn;
+    ll i0 = -((-xlo) >> 32), i1 = xhi >> 32, j0 = -((-ylo) >> 32), j1 = yhi >> 32;
+    if (i0 > i1 || j0 > j1) return;
+    const float fax = (float)ax * sc, fay = (float)ay * sc, fbx = (float)bx * sc, fby = (float)by * sc;
+    const float D = fax * fby - fay * fbx;
+    for (ll j = j0; j <= j1; ++j)
+        for (ll i = i0; i <= i1; ++i) {
+            const ll qx = i * 4294967296LL - Xn, qy = j * 4294967296LL - Yn;
+            if (orient_pert(Ax, Ay, Bx, By, qx, qy) < 0) continue;
+            if (orient_pert(Bx, By, 0, 0, qx, qy) < 0) continue;
+            if (orient_pert(0, 0, Ax, Ay, qx, qy) < 0) continue;
+            const float fqx = (float)qx * 2.3283064365386963e-10f, fqy = (float)qy * 2.3283064365386963e-10f;
+            float la = (fqx * fby - fqy * fbx) / D;  // weight of a
+            float lb = (fax * fqy - fay * fqx) / D;  // weight of b
+            float lp = 1.0f - la - lb;
+            const ll node = (ll)wrapi((int)(j % n), n) * n + wrapi((int)(i % n), n);
+            PM_CHK(node >= 0 && node < g.ncell && ida < np && idb < np, 302, continue)
+            for (int f = 0; f < F; ++f) {
+                const float *v = vals + (ll)f * np;
+                mesh[(ll)f * g.ncell + node] = lp * v[p] + la * v[ida] + lb * v[idb];
+            }
+        }
+}
+
+__global__ void __launch_bounds__(128, 8) k_delta2d(Geo g, ll np, const uint2 *__restrict__ pos,
                                                  const int *__restrict__ nbr, const unsigned char *__restrict__ deg,
                                                  const float *__restrict__ vals, int F, float *__restrict__ mesh) {
     ll pl = (ll)blockIdx.x * blockDim.x + threadIdx.x;
     if (pl >= np) return;
-    const int p = (int)pl, n = g.n, m = deg[p];
+    const int p = (int)pl, m = deg[p];
     if (m < 3) return;
     const uint2 Xp = pos[p];
-    const ll Xn = (ll)Xp.x * n, Yn = (ll)Xp.y * n;
-    const float sc = (float)n * 2.3283064365386963e-10f;  // torus units -> cell units
     int ida;
     ll ax, ay;
     rel_of(nbr[(ll)(m - 1) * np + p], Xp, pos, ida, ax, ay);
@@ -72,31 +121,7 @@ __global__ void __launch_bounds__(128) k_delta2d(Geo g, ll np, const uint2 *__re
         ll bx, by;
         rel_of(nbr[(ll)k * np + p], Xp, pos, idb, bx, by);
         // triangle (p, a, b) with a = q_{k-1}, b = q_k; owned by its lowest sorted index
-        if (ida > p && idb > p) {
-            const ll Ax = ax * n, Ay = ay * n, Bx = bx * n, By = by * n;
-            ll xlo = min(0LL, min(Ax, Bx)) + Xn, xhi = max(0LL, max(Ax, Bx)) + Xn;
-            ll ylo = min(0LL, min(Ay, By)) + Yn, yhi = max(0LL, max(Ay, By)) + Yn;
-            ll i0 = -((-xlo) >> 32), i1 = xhi >> 32, j0 = -((-ylo) >> 32), j1 = yhi >> 32;
-            const float fax = (float)ax * sc, fay = (float)ay * sc, fbx = (float)bx * sc, fby = (float)by * sc;
-            const float D = fax * fby - fay * fbx;
-            for (ll j = j0; j <= j1; ++j)
-                for (ll i = i0; i <= i1; ++i) {
-                    const ll qx = i * 4294967296LL - Xn, qy = j * 4294967296LL - Yn;
-                    if (orient_pert(Ax, Ay, Bx, By, qx, qy) < 0) continue;
-                    if (orient_pert(Bx, By, 0, 0, qx, qy) < 0) continue;
-                    if (orient_pert(0, 0, Ax, Ay, qx, qy) < 0) continue;
-                    const float fqx = (float)qx * 2.3283064365386963e-10f, fqy = (float)qy * 2.3283064365386963e-10f;
-                    float la = (fqx * fby - fqy * fbx) / D;  // weight of a
-                    float lb = (fax * fqy - fay * fqx) / D;  // weight of b
-                    float lp = 1.0f - la - lb;
-                    const ll node = (ll)wrapi((int)(j % n), n) * n + wrapi((int)(i % n), n);
-                    PM_CHK(node >= 0 && node < g.ncell && ida < np && idb < np, 302, continue)
-                    for (int f = 0; f < F; ++f) {
-                        const float *v = vals + (ll)f * np;
-                        mesh[(ll)f * g.ncell + node] = lp * v[p] + la * v[ida] + lb * v[idb];
-                    }
-                }
-        }
+        if (ida > p && idb > p) delta_tri(g, np, p, ida, idb, Xp, ax, ay, bx, by, vals, F, mesh);
         ida = idb;
         ax = bx;
         ay = by;
@@ -719,11 +744,15 @@ static size_t rhs2d_smem() {
 
 // Raise the dynamic shared-memory limit of the RHS kernels on the current
 // device (called when a context is created, outside any stream capture).
+template <int FF>
+static void rhs_attr() {
+    cudaFuncSetAttribute(k_rhs2d<FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs2d_smem<FF>());
+}
+
 void rhs_prepare_device() {
-    cudaFuncSetAttribute(k_rhs2d<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs2d_smem<2>());
-    cudaFuncSetAttribute(k_rhs2d<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs2d_smem<4>());
-    cudaFuncSetAttribute(k_rhs2d<PM_MAXF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)rhs2d_smem<PM_MAXF>());
+    rhs_attr<2>();
+    rhs_attr<4>();
+    rhs_attr<PM_MAXF>();
 }
 
 template <int FF>
