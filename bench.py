@@ -183,6 +183,15 @@ def alu_roofline(kernel, counts, ms, sm_mhz):
                            f"timed region)"}
 
 
+def max_over_ranks(torch, dist, value, device):
+    """The slowest rank's value (the job's time); the value itself on one rank."""
+    if not dist:
+        return value
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def time_steps(torch, stream, flush, steps, fn):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for k in range(steps):
@@ -233,10 +242,7 @@ def run_mixture(args, pm, torch, dist, local):
         prof = ctx.profile_read(reset=True)
         ctx.profile(False)
         t = sum(ms) / len(ms)
-        if dist:
-            tt = torch.tensor([t], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
+        t = max_over_ranks(torch, dist, t, dev)
         res[name] = {"ms": t, "launches": launches, "info": info,
                      "phase_ms": {k: v[0] / args.steps for k, v in prof.items() if v[0] > 0}}
     ck = clocks.stop()
@@ -351,10 +357,7 @@ def run_batched(args, pm, torch, dist, local):
     launches = pm.kernel_launches() - l0
     ck = clocks.stop()
     t = sum(a.elapsed_time(c) for a, c in ev) / args.steps
-    if dist:
-        tt = torch.tensor([t], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = max_over_ranks(torch, dist, t, dev)
     S, tune_ms = b.tuning()
     flat = [x for row in info for x in row]
     line = {
@@ -472,10 +475,7 @@ def main():
     ctx.profile(False)
     # accuracy of the last step: solve report
     _, info = ctx.assign_mass(px, py, vel, out=mesh2)
-    if dist:
-        t = torch.tensor([t_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step = float(t.item())
+    t_step = max_over_ranks(torch, dist, t_step, dev)
 
     # ---- end to end through the public API with pinned host buffers
     e2e = None

@@ -302,3 +302,22 @@ def test_triangulation_degree_above_capacity(built):
     a, b = to_dev(torch, qx, qy)
     out, info = c2.assign_mass(a, b, torch.ones(1, qx.size, device="cuda"))
     assert info[0].rel_resid <= 1e-6
+
+
+def test_delta_degenerate_lattice(built):
+    """Perfect lattice whose mesh nodes fall exactly on triangle edges and
+    vertices: the orientation tests reach their exact ties, which the
+    (eps, eps^2) node perturbation must resolve as in the oracle."""
+    from paper_1610_05258_gb300 import Context
+    m = 64
+    i = (np.arange(m) + 0.5) / m
+    xx, yy = np.meshgrid(i, i, indexing="xy")
+    px, py = xx.ravel().astype(np.float32), yy.ravel().astype(np.float32)
+    g = np.random.default_rng(11)
+    vals = g.standard_normal((2, px.size)).astype(np.float32)
+    for n in (32, 64, 128):
+        c = Context(2, n, 1.0, px.size, 2)
+        dpx, dpy, dv = to_dev(torch, px, py, vals)
+        got = c.assign_delta(dpx, dpy, dv).cpu().numpy()
+        want = oracle.delta(2, n, 1.0, px, py, vals)
+        assert rel_l2(got, want) <= TOL, n
