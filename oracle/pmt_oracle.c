@@ -863,3 +863,174 @@ double or_sum_weighted(const double *w, const double *a, ll m) {
     for (ll i = 0; i < m; ++i) s += (w ? w[i] : 1.0) * a[i];
     return s;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Mesh -> particle projections other than delta (Table 1, right column):    */
+/*   c_mu = int Ab psi_mu   with Ab(r) = sum_i Ab_i psi_i(r) (mesh interpolant) */
+/*   lumped:    Abb_mu = c_mu / v_mu                 (Eq. lumped)             */
+/*   full mass: sum_nu m_{mu nu} Abb_nu = c_mu, m_{mu nu} = int psi_mu psi_nu */
+/*              (Eq. proj2 with phi_mu from Eq. phi_def on the particles)      */
+/* ------------------------------------------------------------------------ */
+
+/* 1D: c_mu over the merged breakpoints of particles and nodes; on each piece
+ * the integrand (linear x linear) is integrated by Simpson's rule (exact). */
+int or1_g2p_int(int n, double L, const float *px, ll np, const double *mesh, int F, double *c) {
+    xi1 *o; double *g;
+    int st = order1d(px, np, L, &o, &g);
+    if (st) return st;
+    const double h = L / n, u = L / TWO32;
+    for (ll i = 0; i < (ll)F * np; ++i) c[i] = 0.0;
+    for (ll k = 0; k < np; ++k) {
+        ll k1 = (k + 1) % np;
+        double xa = (double)o[k].X * u, xb = xa + g[k] * u;
+        if (g[k] == 0.0) continue;
+        ll e = cell_of(o[k].X, n);
+        double cur = xa;
+        while (cur < xb) {
+            double end = (double)(e + 1) * h < xb ? (double)(e + 1) * h : xb;
+            int left = wrapi(e, n), right = wrapi(e + 1, n);
+            double pts[3] = {cur, 0.5 * (cur + end), end}, wts[3] = {1, 4, 1};
+            for (int q = 0; q < 3; ++q) {
+                double x = pts[q];
+                double la = (xb - x) / (xb - xa);    /* psi of particle k at x */
+                double sl = (x - (double)e * h) / h; /* local coordinate in element */
+                double wq = wts[q] * (end - cur) / 6.0;
+                for (int f = 0; f < F; ++f) {
+                    double Ab = mesh[(ll)f * n + left] * (1 - sl) + mesh[(ll)f * n + right] * sl;
+                    c[f * np + o[k].idx] += wq * Ab * la;
+                    c[f * np + o[k1].idx] += wq * Ab * (1 - la);
+                }
+            }
+            cur = end;
+            ++e;
+        }
+    }
+    free(o); free(g);
+    return OR_OK;
+}
+
+/* 2D: c_mu by clipping every particle triangle against every cell and
+ * integrating Ab psi_mu (bilinear x linear, degree 3) with the
+ * Hammer-Marlowe-Stroud rule on a fan of each clipped polygon. */
+int or2_g2p_int(int n, double L, const float *px, const float *py, ll np, const double *mesh, int F,
+                const ll *tri, const int *off, ll ntri, double *c) {
+    const ll nn = (ll)n * n;
+    const double h = L / n;
+    for (ll i = 0; i < (ll)F * np; ++i) c[i] = 0.0;
+    uint32_t *X = malloc(sizeof(uint32_t) * np), *Y = malloc(sizeof(uint32_t) * np);
+    if (!X || !Y) { free(X); free(Y); return OR_ENOMEM; }
+    or_fixed_coords(px, np, L, X);
+    or_fixed_coords(py, np, L, Y);
+    for (ll t = 0; t < ntri; ++t) {
+        double x[3], y[3];
+        tri_coords(L, X, Y, tri, off, t, x, y);
+        double xmin = fmin(x[0], fmin(x[1], x[2])), xmax = fmax(x[0], fmax(x[1], x[2]));
+        double ymin = fmin(y[0], fmin(y[1], y[2])), ymax = fmax(y[0], fmax(y[1], y[2]));
+        for (ll cy = (ll)floor(ymin / h); cy * h < ymax; ++cy)
+            for (ll cx = (ll)floor(xmin / h); cx * h < xmax; ++cx) {
+                double ax[16], ay[16], bx[16], by[16];
+                int m = 3;
+                for (int k = 0; k < 3; ++k) { ax[k] = x[k]; ay[k] = y[k]; }
+                m = clip_half(ax, ay, m, -1, 0, -(double)cx * h, bx, by);
+                m = clip_half(bx, by, m, 1, 0, (double)(cx + 1) * h, ax, ay);
+                m = clip_half(ax, ay, m, 0, -1, -(double)cy * h, bx, by);
+                m = clip_half(bx, by, m, 0, 1, (double)(cy + 1) * h, ax, ay);
+                if (m < 3) continue;
+                ll nd[4] = {(ll)wrapi(cy, n) * n + wrapi(cx, n), (ll)wrapi(cy, n) * n + wrapi(cx + 1, n),
+                            (ll)wrapi(cy + 1, n) * n + wrapi(cx, n), (ll)wrapi(cy + 1, n) * n + wrapi(cx + 1, n)};
+                for (int k = 1; k + 1 < m; ++k) {
+                    double fx[3] = {ax[0], ax[k], ax[k + 1]}, fy[3] = {ay[0], ay[k], ay[k + 1]};
+                    double area = 0.5 * fabs((fx[1] - fx[0]) * (fy[2] - fy[0]) - (fx[2] - fx[0]) * (fy[1] - fy[0]));
+                    for (int q = 0; q < 4; ++q) {
+                        double qx = HMS_L[q][0] * fx[0] + HMS_L[q][1] * fx[1] + HMS_L[q][2] * fx[2];
+                        double qy = HMS_L[q][0] * fy[0] + HMS_L[q][1] * fy[1] + HMS_L[q][2] * fy[2];
+                        double l[3];
+                        bary(x, y, qx, qy, l);
+                        double s = (qx - cx * h) / h, tt = (qy - cy * h) / h;
+                        double psi[4] = {(1 - s) * (1 - tt), s * (1 - tt), (1 - s) * tt, s * tt};
+                        double w = area * HMS_W[q];
+                        for (int f = 0; f < F; ++f) {
+                            double Ab = 0;
+                            for (int cc = 0; cc < 4; ++cc) Ab += mesh[f * nn + nd[cc]] * psi[cc];
+                            for (int k2 = 0; k2 < 3; ++k2) c[f * np + tri[3 * t + k2]] += w * Ab * l[k2];
+                        }
+                    }
+                }
+            }
+    }
+    free(X); free(Y);
+    return OR_OK;
+}
+
+/* Particle mass matrix applied to x ([F][np]):
+ *   1D: on each gap g between ordered particles a, b the element matrix
+ *       (g/6) [[2, 1], [1, 2]];
+ *   2D: on each triangle T the P1 element matrix (|T|/12)(1 + delta_ab). */
+int or_particle_mass_apply(int dim, double L, const float *px, const float *py, ll np, const ll *tri,
+                           const int *off, ll ntri, const double *x, int F, double *y) {
+    for (ll i = 0; i < (ll)F * np; ++i) y[i] = 0.0;
+    if (dim == 1) {
+        xi1 *o; double *g;
+        int st = order1d(px, np, L, &o, &g);
+        if (st) return st;
+        const double u = L / TWO32;
+        for (ll k = 0; k < np; ++k) {
+            ll a = o[k].idx, b = o[(k + 1) % np].idx;
+            double e = g[k] * u / 6.0;
+            for (int f = 0; f < F; ++f) {
+                y[f * np + a] += e * (2 * x[f * np + a] + x[f * np + b]);
+                y[f * np + b] += e * (x[f * np + a] + 2 * x[f * np + b]);
+            }
+        }
+        free(o); free(g);
+        return OR_OK;
+    }
+    uint32_t *X = malloc(sizeof(uint32_t) * np), *Y = malloc(sizeof(uint32_t) * np);
+    if (!X || !Y) { free(X); free(Y); return OR_ENOMEM; }
+    or_fixed_coords(px, np, L, X);
+    or_fixed_coords(py, np, L, Y);
+    for (ll t = 0; t < ntri; ++t) {
+        double xs[3], ys[3];
+        tri_coords(L, X, Y, tri, off, t, xs, ys);
+        double area = 0.5 * fabs((xs[1] - xs[0]) * (ys[2] - ys[0]) - (xs[2] - xs[0]) * (ys[1] - ys[0]));
+        for (int f = 0; f < F; ++f) {
+            double s = 0;
+            for (int k = 0; k < 3; ++k) s += x[f * np + tri[3 * t + k]];
+            for (int k = 0; k < 3; ++k) y[f * np + tri[3 * t + k]] += area / 12.0 * (s + x[f * np + tri[3 * t + k]]);
+        }
+    }
+    free(X); free(Y);
+    return OR_OK;
+}
+
+/* Solve M_p x = c (all F fields) by conjugate gradients in FP64 to relative
+ * residual rtol, from x = 0. Returns the iterations taken (or < 0). */
+int or_particle_mass_solve(int dim, double L, const float *px, const float *py, ll np, const ll *tri,
+                           const int *off, ll ntri, const double *c, int F, double rtol, int max_iter, double *x) {
+    double *r = malloc(sizeof(double) * np), *p = malloc(sizeof(double) * np), *q = malloc(sizeof(double) * np);
+    if (!r || !p || !q) { free(r); free(p); free(q); return -OR_ENOMEM; }
+    int worst = 0;
+    for (int f = 0; f < F; ++f) {
+        double *xf = x + (ll)f * np;
+        const double *cf = c + (ll)f * np;
+        double bb = 0;
+        for (ll i = 0; i < np; ++i) { xf[i] = 0; r[i] = cf[i]; p[i] = cf[i]; bb += cf[i] * cf[i]; }
+        double rr = bb;
+        int it = 0;
+        while (it < max_iter && rr > rtol * rtol * bb && bb > 0) {
+            int st = or_particle_mass_apply(dim, L, px, py, np, tri, off, ntri, p, 1, q);
+            if (st) { free(r); free(p); free(q); return -st; }
+            double pq = 0;
+            for (ll i = 0; i < np; ++i) pq += p[i] * q[i];
+            double al = rr / pq, rn = 0;
+            for (ll i = 0; i < np; ++i) { xf[i] += al * p[i]; r[i] -= al * q[i]; rn += r[i] * r[i]; }
+            double be = rn / rr;
+            rr = rn;
+            for (ll i = 0; i < np; ++i) p[i] = r[i] + be * p[i];
+            ++it;
+        }
+        if (it > worst) worst = it;
+    }
+    free(r); free(p); free(q);
+    return worst;
+}

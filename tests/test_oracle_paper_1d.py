@@ -31,7 +31,10 @@ def _run(method, jitter):
         else:
             m = oracle.assign_mass(1, n, L, px, None, a)
         x = np.mod(x + dt, L)
-        a = oracle.interpolate(1, n, L, m, x.astype(np.float32))[0]
+        if method == "full_mass":  # Eq. proj2 back to the particles
+            a = oracle.interpolate_mass(1, n, L, m, x.astype(np.float32))[0]
+        else:
+            a = oracle.interpolate(1, n, L, m, x.astype(np.float32))[0]
     v = oracle.particle_volumes(1, L, x.astype(np.float32))
     return {"E1": 100 * ((v * a).sum() / (v0 * a0).sum() - 1),
             "E2": 100 * ((v * a * a).sum() / (v0 * a0 * a0).sum() - 1),
@@ -53,3 +56,20 @@ def test_paper_1d_table(case, jitter):
         # Sec. 3.1: for the regular arrangement FLIP is equivalent to delta
         d, f = _run("delta", 0.0), _run("flip", 0.0)
         assert abs(d["E2"] - f["E2"]) < 1e-4 and abs(d["L2"] - f["L2"]) < 1e-4  # float32 positions
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("case,jitter", [("regular", 0.0), ("distorted", 0.4)])
+def test_paper_1d_full_mass(case, jitter):
+    """Full mass (mass assignment both ways). The paper's regular row gives
+    E1 = 0 and L2 = 10%; it states that E2 decreases for every method and
+    that full mass is the most accurate."""
+    tol = GOLD["tolerance_percentage_points"]
+    got = _run("full_mass", jitter)
+    assert abs(got["E1"]) < 1e-6  # conservative to rounding with the exact integrals
+    assert got["E2"] <= 0.0       # stability (Eq. stab)
+    if case == "regular":
+        assert abs(got["L2"] - GOLD[case]["full_mass"]["L2"]) <= tol
+    md = _run("mass", jitter)
+    d = _run("delta", jitter)
+    assert got["L2"] < md["L2"] < d["L2"]

@@ -503,3 +503,99 @@ def test_2d_appendix_b_reading_exact_for_affine_particles():
     b0 = oracle.rhs(2, inst.n, inst.L, inst.px, inst.py, a, 0, tri=tri)[0].reshape(12, 12)
     b1 = oracle.rhs(2, inst.n, inst.L, inst.px, inst.py, a, 1, tri=tri)[0].reshape(12, 12)
     np.testing.assert_allclose(b1[3:9, 3:9], b0[3:9, 3:9], atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# mesh -> particle projections (Table 1 right column: lumped, full mass)
+# ---------------------------------------------------------------------------
+def _proj_case(dim, seed):
+    from paper_1610_05258_gb300 import workloads as W
+    if dim == 1:
+        inst = W.tophat_1d(48, 61, seed=seed)
+        return inst.n, inst.L, inst.px, None
+    inst = W.uniform_instance(10, 3, F=1, seed=seed)
+    return inst.n, inst.L, inst.px, inst.py
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_g2p_integral_is_the_transpose_of_the_rhs(dim):
+    """<c(Ab), A> = int Ab A = <Ab, b(A)> for any particle values A and mesh
+    values Ab: the mesh->particle integral is the adjoint of the (pinned)
+    right-hand side."""
+    n, L, px, py = _proj_case(dim, 31)
+    g = np.random.default_rng(5)
+    A = g.standard_normal((3, px.size))
+    Ab = g.standard_normal((3, n ** dim))
+    c = oracle.g2p_integral(dim, n, L, Ab, px, py)
+    b = oracle.rhs(dim, n, L, px, py, A)
+    for f in range(3):
+        assert np.dot(c[f], A[f]) == pytest.approx(np.dot(Ab[f], b[f]), rel=1e-12, abs=1e-14)
+    # partition of unity of the particle functions: sum_mu c_mu = int Ab
+    h = L / n
+    assert c.sum(axis=1) == pytest.approx(h ** dim * Ab.sum(axis=1), rel=1e-12, abs=1e-14)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_particle_mass_matrix(dim):
+    n, L, px, py = _proj_case(dim, 32)
+    g = np.random.default_rng(6)
+    v = oracle.particle_volumes(dim, L, px, py)
+    ones = np.ones((1, px.size))
+    # row sums are the particle volumes (sum_nu m_mu_nu = v_mu)
+    assert oracle.particle_mass_apply(dim, L, px, py, ones)[0] == pytest.approx(v, rel=1e-12)
+    x, y = g.standard_normal((2, px.size))
+    Mx = oracle.particle_mass_apply(dim, L, px, py, x)[0]
+    My = oracle.particle_mass_apply(dim, L, px, py, y)[0]
+    assert np.dot(Mx, y) == pytest.approx(np.dot(x, My), rel=1e-12)
+    # <x, M x> = int (sum_nu x_nu psi_nu)^2, by an exact rule independent of
+    # the element matrix: edge midpoints (2D, exact for degree 2) or Simpson (1D)
+    X = oracle.fixed_coords(px, L).astype(np.float64) * (L / 2 ** 32)
+    if dim == 1:
+        o = np.argsort(X, kind="stable")
+        gaps = np.diff(np.append(X[o], X[o[0]] + L))
+        a, b = x[o], np.roll(x[o], -1)
+        want = np.sum(gaps / 6.0 * (a * a + 4 * ((a + b) / 2) ** 2 + b * b))
+    else:
+        Y = oracle.fixed_coords(py, L).astype(np.float64) * (L / 2 ** 32)
+        t, off, _ = oracle.triangulate(L, px, py)
+        xs = np.stack([X[t[:, 0]], X[t[:, 1]] + off[:, 0] * L, X[t[:, 2]] + off[:, 2] * L], 1)
+        ys = np.stack([Y[t[:, 0]], Y[t[:, 1]] + off[:, 1] * L, Y[t[:, 2]] + off[:, 3] * L], 1)
+        area = 0.5 * np.abs((xs[:, 1] - xs[:, 0]) * (ys[:, 2] - ys[:, 0]) - (xs[:, 2] - xs[:, 0]) * (ys[:, 1] - ys[:, 0]))
+        xv = x[t]
+        mids = 0.5 * (xv + np.roll(xv, -1, axis=1))
+        want = np.sum(area / 3.0 * (mids ** 2).sum(axis=1))
+    assert np.dot(x, Mx) == pytest.approx(want, rel=1e-11)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_full_mass_projection(dim):
+    """Full mass (Eq. proj2): M_p Abb = c solved (checked against scipy's sparse
+    direct solver on the assembled matrix), conservative and stable; constant
+    fields are kept."""
+    sp = pytest.importorskip("scipy.sparse")
+    spl = pytest.importorskip("scipy.sparse.linalg")
+    n, L, px, py = _proj_case(dim, 33)
+    g = np.random.default_rng(7)
+    Ab = g.standard_normal((2, n ** dim))
+    x = oracle.interpolate_mass(dim, n, L, Ab, px, py)
+    c = oracle.g2p_integral(dim, n, L, Ab, px, py)
+    # assemble M_p column by column through the apply, then a direct solve
+    N = px.size
+    cols = oracle.particle_mass_apply(dim, L, px, py, np.eye(N))
+    M = sp.csc_matrix(cols.T)
+    for f in range(2):
+        xs = spl.spsolve(M, c[f])
+        assert np.linalg.norm(x[f] - xs) <= 1e-10 * np.linalg.norm(xs)
+    v = oracle.particle_volumes(dim, L, px, py)
+    h = L / n
+    # conservation: sum v Abb = int Ab
+    assert (v * x).sum(axis=1) == pytest.approx(h ** dim * Ab.sum(axis=1), rel=1e-10, abs=1e-13)
+    # stability: int (sum Abb psi_mu)^2 <= int Ab^2
+    for f in range(2):
+        e_p = np.dot(x[f], oracle.particle_mass_apply(dim, L, px, py, x[f])[0])
+        e_m = np.dot(Ab[f], oracle.mass_apply(dim, n, L, Ab[f:f + 1])[0])
+        assert e_p <= e_m * (1 + 1e-12)
+    # constants are reproduced by full mass and lumped
+    k = np.full((1, n ** dim), 2.5)
+    assert oracle.interpolate_mass(dim, n, L, k, px, py)[0] == pytest.approx(2.5, rel=1e-10)
+    assert oracle.interpolate_lumped(dim, n, L, k, px, py)[0] == pytest.approx(2.5, rel=1e-12)
