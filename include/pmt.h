@@ -135,6 +135,39 @@ pm_status pm_assign_flip(pm_ctx *ctx, const float *px, const float *py, long lon
 pm_status pm_assign_mass(pm_ctx *ctx, const float *px, const float *py, long long np, const float *vals, int F,
                          float *mesh_out, const pm_solve_opts *opts, pm_solve_info *info);
 
+/* Lumped assignment (Table 1, "lumped" row; Sec. 2.4 remarks, Eq. lumped
+ * with v_i = sum_j m_ij = h^dim):  mesh_out[f][i] = int A_f psi_i / h^dim,
+ * the exact right-hand side of the mass assignment divided by the node
+ * volume (no solve). Layouts, ownership and errors as pm_assign_mass. */
+pm_status pm_assign_lumped(pm_ctx *ctx, const float *px, const float *py, long long np, const float *vals, int F,
+                           float *mesh_out);
+
+/* Mesh -> particle projections other than delta (Table 1, right column).
+ * With the mesh interpolant Ab(r) = sum_i mesh[f][i] psi_i(r) and the particle
+ * functions psi_mu (P1 on the periodic Delaunay triangulation in 2D, hats in
+ * 1D), c_mu = int Ab psi_mu is integrated exactly (clipped triangle-cell
+ * pieces by Green's theorem in 2D, Simpson on the merged breakpoints in 1D)
+ * and
+ *   pm_interpolate_lumped: out[f][mu] = c_mu / v_mu          (Eq. lumped)
+ *   pm_interpolate_mass:   sum_nu m_{mu nu} out[f][nu] = c_mu (Eq. proj2, the
+ *                          "full mass" projection), m_{mu nu} = int psi_mu
+ *                          psi_nu applied matrix-free from the stars;
+ *                          conjugate gradients with the Jacobi preconditioner
+ *                          from the lumped start, FP64 reductions, to
+ *                          ||c - M_p x|| <= rtol ||c|| (opts->rtol, max_iter;
+ *                          warm_start ignored; opts may be NULL for 1e-6/200).
+ * Both conserve the integral: sum_mu v_mu out_mu = int Ab (exactly for the
+ * lumped one, to the residual for the full mass one). mesh [F][n^dim],
+ * px/py [np] (np >= 3 in 2D, >= 2 in 1D), out [F][np] caller order, device
+ * pointers. info (host, F entries, may be NULL): iters, start and final
+ * relative residual, sum_mesh = int Ab, sum_particles = sum v_mu out_mu,
+ * cons_err relative to sum |c_mu|; passing it makes the call wait. Errors as
+ * pm_assign_mass (PM_ENOTCONV when the iteration cap is reached). */
+pm_status pm_interpolate_lumped(pm_ctx *ctx, const float *mesh, int F, const float *px, const float *py, long long np,
+                                float *out);
+pm_status pm_interpolate_mass(pm_ctx *ctx, const float *mesh, int F, const float *px, const float *py, long long np,
+                              float *out, const pm_solve_opts *opts, pm_solve_info *info);
+
 /* Mass right-hand side alone: b_out[f][j] = int A_f(r) psi_j(r) dr (Sec. 2.4,
  * Eq. proj), exact. Asynchronous. */
 pm_status pm_mass_rhs(pm_ctx *ctx, const float *px, const float *py, long long np, const float *vals, int F,

@@ -25,7 +25,7 @@ _STATUS = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ENOTCONV", 4: "PM_
 
 EXPORTS = [
     "pm_ctx_create", "pm_ctx_destroy", "pm_ctx_set_stream", "pm_sync", "pm_last_error", "pm_ctx_workspace_bytes",
-    "pm_interpolate", "pm_assign_delta", "pm_assign_flip", "pm_assign_mass", "pm_mass_rhs", "pm_mass_apply",
+    "pm_interpolate", "pm_interpolate_lumped", "pm_interpolate_mass", "pm_assign_lumped", "pm_assign_delta", "pm_assign_flip", "pm_assign_mass", "pm_mass_rhs", "pm_mass_apply",
     "pm_mass_solve", "pm_particle_volumes", "pm_triangulate", "pm_sort", "pm_advect_shift", "pm_advect_rotate",
     "pm_advect_rk2", "pm_profile", "pm_profile_read", "pm_work_read", "pm_phase_name", "pm_kernel_launches",
     "pm_batch_create", "pm_batch_destroy", "pm_batch_last_error", "pm_batch_tuning", "pm_batch_assign_mass",
@@ -84,6 +84,9 @@ def load_library(path: str | None = None):
         "pm_last_error": [vp],
         "pm_ctx_workspace_bytes": [vp],
         "pm_interpolate": [vp, vp, i, vp, vp, ll, vp],
+        "pm_interpolate_lumped": [vp, vp, i, vp, vp, ll, vp],
+        "pm_interpolate_mass": [vp, vp, i, vp, vp, ll, vp, ctypes.POINTER(_Opts), vp],
+        "pm_assign_lumped": [vp, vp, vp, ll, vp, i, vp],
         "pm_assign_delta": [vp, vp, vp, ll, vp, i, vp],
         "pm_assign_flip": [vp, vp, vp, ll, vp, i, vp, vp, ctypes.POINTER(ll)],
         "pm_assign_mass": [vp, vp, vp, ll, vp, i, vp, ctypes.POINTER(_Opts), vp],
@@ -206,6 +209,39 @@ class Context:
         out = out if out is not None else self._empty(F, px.numel())
         self._stream()
         self._check(self.lib.pm_interpolate(self.h, _ptr(mesh), F, _ptr(px), _ptr(py), px.numel(), _ptr(out)))
+        return out
+
+    def interpolate_lumped(self, mesh, px, py=None, out=None):
+        """Lumped mesh -> particle projection, c_mu / v_mu (pm_interpolate_lumped)."""
+        mesh, px, py = self._f32(mesh), self._f32(px), self._f32(py)
+        F = mesh.numel() // self.nodes
+        out = out if out is not None else self._empty(F, px.numel())
+        self._stream()
+        self._check(self.lib.pm_interpolate_lumped(self.h, _ptr(mesh), F, _ptr(px), _ptr(py), px.numel(), _ptr(out)))
+        return out
+
+    def interpolate_mass(self, mesh, px, py=None, out=None, rtol=1e-6, max_iter=200, info=True):
+        """Full mass mesh -> particle projection (pm_interpolate_mass)."""
+        mesh, px, py = self._f32(mesh), self._f32(px), self._f32(py)
+        F = mesh.numel() // self.nodes
+        out = out if out is not None else self._empty(F, px.numel())
+        o = self._opts("delta", rtol, max_iter, None)
+        inf = (_Info * F)() if info else None
+        self._stream()
+        self._check(self.lib.pm_interpolate_mass(self.h, _ptr(mesh), F, _ptr(px), _ptr(py), px.numel(), _ptr(out),
+                                                 ctypes.byref(o), inf))
+        if not info:
+            return out
+        return out, [SolveInfo(x.iters, x.init_rel_resid, x.rel_resid, x.sum_particles, x.sum_mesh, x.cons_err)
+                     for x in inf]
+
+    def assign_lumped(self, px, py, vals, out=None):
+        """Lumped assignment, int A psi_i / h^dim (pm_assign_lumped)."""
+        px, py, vals = self._f32(px), self._f32(py), self._f32(vals)
+        F = vals.numel() // max(1, px.numel())
+        out = out if out is not None else self._empty(F, self.nodes)
+        self._stream()
+        self._check(self.lib.pm_assign_lumped(self.h, _ptr(px), _ptr(py), px.numel(), _ptr(vals), F, _ptr(out)))
         return out
 
     def assign_delta(self, px, py, vals, out=None):

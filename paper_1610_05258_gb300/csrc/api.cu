@@ -192,7 +192,7 @@ pm_status pm_ctx_create(pm_ctx **out, int dim, int n, double L, long long max_pa
     w.np_max = max_particles;
     w.F_max = max_fields;
     const ll np = max_particles, nc = g.ncell, F = max_fields;
-    w.nblk_psum = 256;
+    w.nblk_psum = 4 * 152;  // enough loads in flight to stream the particle arrays
     bool ok = alloc(c, &w.fx, np) && alloc(c, &w.key, np) && alloc(c, &w.slot, np) && alloc(c, &w.count, nc) &&
               alloc(c, &w.cell_start, nc + 1) && alloc(c, &w.scan_tmp, nc / 4096 + 2) && alloc(c, &w.tmp, np) &&
               alloc(c, &w.perm, np) && alloc(c, &w.pos, np) && alloc(c, &w.vals, np * F) &&
@@ -202,7 +202,10 @@ pm_status pm_ctx_create(pm_ctx **out, int dim, int n, double L, long long max_pa
               alloc(c, &w.p, F * nc) && alloc(c, &w.q, F * nc) && alloc(c, &w.b, F * nc) &&
               alloc(c, &w.red, 6LL * PM_MAXF * 4096) && alloc(c, &w.scal, 16LL * PM_MAXF) &&
               alloc(c, &w.bar, 2) && alloc(c, &w.status, 1) && alloc(c, &w.empty, 1) && alloc(c, &w.ntri, 1) &&
-              alloc(c, &w.wsum, 8) && alloc(c, &w.nretry, 1);
+              alloc(c, &w.wsum, 8) && alloc(c, &w.nretry, 1) && alloc(c, &w.meshmax, PM_MAXF) &&
+              alloc(c, &w.pc, F * np) && alloc(c, &w.px, F * np) && alloc(c, &w.pq, F * np) &&
+              alloc(c, &w.prp, 2 * F * np);
+    w.cfix = (ll *)w.prp;
     if (ok && dim == 2) ok = alloc(c, &w.nbr, (ll)PM_MAXDEG * np);
     if (ok && dim == 2 && n % 128 == 0)
         ok = alloc(c, &w.feat, 2 * F * nc) && alloc(c, &w.corr, F * nc);
@@ -231,7 +234,7 @@ void pm_ctx_destroy(pm_ctx *c) {
     void *ptrs[] = {w.fx,  w.key, w.slot, w.count, w.cell_start, w.scan_tmp, w.tmp,  w.perm,  w.pos,
                     w.vals, w.maxabs, w.nbr, w.deg,  w.vol,  w.part,  w.bfix, w.psum, w.r,     w.p,
                     w.q,   w.b,   w.red,  w.scal,  w.bar,  w.status, w.empty, w.ntri, w.feat, w.corr,
-                    w.wsum, w.nretry};
+                    w.wsum, w.nretry, w.meshmax, w.pc, w.px, w.pq, w.prp};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (w.hstatus) cudaFreeHost(w.hstatus);
@@ -397,6 +400,77 @@ pm_status pm_assign_mass(pm_ctx *c, const float *px, const float *py, long long 
     if ((s = mass_solve_launch(c, F, mesh_out, start, o))) return s;
     if (info) return fill_info(c, F, info);
     return PM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Mesh -> particle projections other than delta, and the lumped assignment
+// (Table 1): c_mu = int Ab psi_mu, then c/v (lumped) or M_p^-1 c (full mass).
+// ---------------------------------------------------------------------------
+static pm_status proj_front(pm_ctx *c, const float *mesh, int F, const float *px, const float *py, ll np,
+                            float *out) {
+    pm_status s = check_particles(c, px, py, np, 0, nullptr, c && c->g.dim == 2 ? 3 : 2);
+    if (s) return s;
+    if (F < 1 || F > c->w.F_max) return fail(c, PM_EINVAL, "field count out of range");
+    if (!mesh || !out) return fail(c, PM_EINVAL, "null mesh or output array");
+    if ((s = prepare(c, px, py, np, nullptr, 0, true))) return s;
+    {
+        Phase ph(c, PM_PH_RHS);
+        launch_g2p_integral(c->g, c->w, np, F, mesh, c->w.pc, c->st);
+    }
+    return check_launch(c, "mesh-to-particle integral");
+}
+
+static void unsort_fields(pm_ctx *c, ll np, int F, const float *src, float *out) {
+    for (int f = 0; f < F; ++f) launch_scatter_sorted(np, c->w.perm, src + (ll)f * np, out + (ll)f * np, c->st);
+}
+
+pm_status pm_interpolate_lumped(pm_ctx *c, const float *mesh, int F, const float *px, const float *py, long long np,
+                                float *out) {
+    pm_status s = proj_front(c, mesh, F, px, py, np, out);
+    if (s) return s;
+    {
+        Phase ph(c, PM_PH_G2P);
+        launch_div_vol(np, F, c->w.vol, c->w.pc, c->st);
+        unsort_fields(c, np, F, c->w.pc, out);
+    }
+    return check_launch(c, "pm_interpolate_lumped");
+}
+
+pm_status pm_interpolate_mass(pm_ctx *c, const float *mesh, int F, const float *px, const float *py, long long np,
+                              float *out, const pm_solve_opts *opts, pm_solve_info *info) {
+    pm_solve_opts o = opts ? *opts : pm_solve_opts{PM_WS_DELTA, 1e-6, 200, nullptr, nullptr};
+    if (!(o.rtol > 0.0) || o.max_iter < 0) return fail(c, PM_EINVAL, "bad solve options");
+    pm_status s = proj_front(c, mesh, F, px, py, np, out);
+    if (s) return s;
+    int e;
+    {
+        Phase ph(c, PM_PH_SOLVE);
+        e = launch_pcg(c->g, c->w, np, F, c->w.pc, c->w.px, o.rtol, o.max_iter, c->st);
+    }
+    if (e) return cuda_fail(c, (cudaError_t)e, "pm_interpolate_mass solve launch");
+    {
+        Phase ph(c, PM_PH_G2P);
+        unsort_fields(c, np, F, c->w.px, out);
+    }
+    if ((s = check_launch(c, "pm_interpolate_mass"))) return s;
+    if (info) return fill_info(c, F, info);
+    return PM_OK;
+}
+
+pm_status pm_assign_lumped(pm_ctx *c, const float *px, const float *py, long long np, const float *vals, int F,
+                           float *mesh_out) {
+    pm_status s = check_particles(c, px, py, np, F, vals, c && c->g.dim == 2 ? 3 : 2);
+    if (s) return s;
+    if (F < 1 || !mesh_out) return fail(c, PM_EINVAL, "null output or no field");
+    if ((s = prepare(c, px, py, np, vals, F, true))) return s;
+    {
+        Phase ph(c, PM_PH_RHS);
+        launch_rhs(c->g, c->w, np, F, c->st);
+        launch_rhs_to_float(c->g, c->w, F, mesh_out, c->st);
+        const double hd = c->g.dim == 2 ? (double)c->g.h * c->g.h : (double)c->g.h;
+        launch_scale((ll)F * c->g.ncell, (float)(1.0 / hd), mesh_out, c->st);
+    }
+    return check_launch(c, "pm_assign_lumped");
 }
 
 pm_status pm_mass_rhs(pm_ctx *c, const float *px, const float *py, long long np, const float *vals, int F,

@@ -488,7 +488,7 @@ void launch_triangulate(const Geo &g, Work &w, ll np, cudaStream_t st, bool coun
     float scale = (float)(u * u / 6.0);
     cudaMemsetAsync(w.nretry, 0, sizeof(int), st);
     // w.tmp (caller indices before the canonical cell order) is free after the sort
-    const int rgrid = 4 * 152;
+    const int rgrid = 16 * 152;  // about one listed particle per thread
     if (count_work) {
         k_delaunay<true><<<div_up(np, DBLK), DBLK, 0, st>>>(g, np, w.pos, w.cell_start, w.perm, w.nbr, w.deg, w.vol,
                                                              scale, w.status, w.tmp, w.nretry, w.wsum);

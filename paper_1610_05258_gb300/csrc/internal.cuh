@@ -74,6 +74,11 @@ struct Work {
     float *corr;           // [F][ncell] network output
     ull *wsum;             // [8] triangulation work counters (counting mode)
     int *nretry;           // particles handed to the triangulation's retry pass
+    // mesh -> particle projections (particle-sized, sorted order)
+    unsigned *meshmax;     // [PM_MAXF] max |Ab| bit patterns
+    float *pc, *px, *pq;   // [F][np] right-hand side c, solution, M_p p
+    float *prp;            // [2][F][np] residual and search direction (r, then p)
+    ll *cfix;              // = (ll *)prp: fixed-point c before conversion
 };
 
 // ---------------------------------------------------------------------------
@@ -169,6 +174,12 @@ void launch_volumes_1d(const Geo &g, Work &w, ll np, cudaStream_t st);
 void launch_delta(const Geo &g, Work &w, ll np, int F, float *mesh_out, cudaStream_t st);
 void launch_flip(const Geo &g, Work &w, ll np, int F, float *mesh_out, float *node_vol, cudaStream_t st);
 void rhs_prepare_device();
+void launch_g2p_integral(const Geo &g, Work &w, ll np, int F, const float *mesh, float *c, cudaStream_t st);
+void launch_div_vol(ll np, int F, const float *vol, float *c, cudaStream_t st);
+void launch_scale(ll m, float s, float *x, cudaStream_t st);
+// Full-mass mesh -> particle solve M_p x = c (sorted order); 0 or a CUDA error.
+int launch_pcg(const Geo &g, Work &w, ll np, int F, const float *c, float *x, double rtol, int max_iter,
+               cudaStream_t st);
 void launch_rhs(const Geo &g, Work &w, ll np, int F, cudaStream_t st);
 void launch_rhs_to_float(const Geo &g, Work &w, int F, float *b_out, cudaStream_t st);
 void launch_mass_apply(const Geo &g, const float *x, int F, float *y, cudaStream_t st);

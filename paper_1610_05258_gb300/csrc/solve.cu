@@ -110,6 +110,26 @@ __device__ void grid_total(const double *red, int F, int slot, double out[PM_MAX
     __syncthreads();
 }
 
+// Totals of the per-block particle sums (sum v A, sum v |A|) of every field:
+// warp f sums field f's partials (lanes stride, fixed shuffle tree), so the
+// result is the same on every run. Called by all threads of one block.
+__device__ void particle_sums(const double *psum, int nblk, int F, double s1[PM_MAXF], double s2[PM_MAXF]) {
+    __shared__ double tot[2 * PM_MAXF];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = wid; k < 2 * F; k += (int)(blockDim.x >> 5)) {
+        const double *src = psum + (ll)k * nblk;
+        double s = 0;
+        for (int i = lane; i < nblk; i += 32) s += src[i];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) tot[k] = s;
+    }
+    __syncthreads();
+    for (int f = 0; f < F; ++f) {
+        s1[f] = tot[2 * f];
+        s2[f] = tot[2 * f + 1];
+    }
+}
+
 // Compensated M x at node i of field array xf; returns (hi, lo) of the
 // unscaled stencil sum; the caller multiplies by c = h/6 or h^2/36.
 template <int DIM>
@@ -336,6 +356,8 @@ __global__ void __launch_bounds__(256) k_cg(CG a) {
     double tr[PM_MAXF], sx[PM_MAXF];
     grid_total(a.red, F, 0, tr);
     grid_total(a.red, F, 1, sx);
+    double ps1[PM_MAXF], ps2[PM_MAXF];
+    if (blockIdx.x == 0 && a.psum) particle_sums(a.psum, a.nblk_psum, F, ps1, ps2);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         bool bad = false;
         for (int f = 0; f < F; ++f) {
@@ -344,13 +366,8 @@ __global__ void __launch_bounds__(256) k_cg(CG a) {
             a.scal[f * 16 + S_RESID] = res;
             a.scal[f * 16 + S_SUMMESH] = sx[f] * hd;
             if (a.psum) {
-                double s1 = 0, s2 = 0;
-                for (int k = 0; k < a.nblk_psum; ++k) {
-                    s1 += a.psum[(ll)(2 * f) * a.nblk_psum + k];
-                    s2 += a.psum[(ll)(2 * f + 1) * a.nblk_psum + k];
-                }
-                a.scal[f * 16 + S_SUMPART] = s1;
-                a.scal[f * 16 + S_SUMABS] = s2;
+                a.scal[f * 16 + S_SUMPART] = ps1[f];
+                a.scal[f * 16 + S_SUMABS] = ps2[f];
             } else {
                 a.scal[f * 16 + S_SUMPART] = sumb[f];
                 a.scal[f * 16 + S_SUMABS] = 0.0;
@@ -651,6 +668,8 @@ __global__ void __launch_bounds__(256) k_cg2v(CG a) {
     double tr[PM_MAXF], sx[PM_MAXF];
     grid_total(a.red, F, 0, tr);
     grid_total(a.red, F, 1, sx);
+    double ps1[PM_MAXF], ps2[PM_MAXF];
+    if (blockIdx.x == 0 && a.psum) particle_sums(a.psum, a.nblk_psum, F, ps1, ps2);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         bool bad = false;
         for (int f = 0; f < F; ++f) {
@@ -659,13 +678,8 @@ __global__ void __launch_bounds__(256) k_cg2v(CG a) {
             a.scal[f * 16 + S_RESID] = res;
             a.scal[f * 16 + S_SUMMESH] = sx[f] * hd;
             if (a.psum) {
-                double s1 = 0, s2 = 0;
-                for (int k = 0; k < a.nblk_psum; ++k) {
-                    s1 += a.psum[(ll)(2 * f) * a.nblk_psum + k];
-                    s2 += a.psum[(ll)(2 * f + 1) * a.nblk_psum + k];
-                }
-                a.scal[f * 16 + S_SUMPART] = s1;
-                a.scal[f * 16 + S_SUMABS] = s2;
+                a.scal[f * 16 + S_SUMPART] = ps1[f];
+                a.scal[f * 16 + S_SUMABS] = ps2[f];
             } else {
                 a.scal[f * 16 + S_SUMPART] = sumb[f];
                 a.scal[f * 16 + S_SUMABS] = 0.0;
@@ -688,7 +702,239 @@ __global__ void k_mass_apply(Geo g, const float *__restrict__ x, int F, float *_
     }
 }
 
+// ---------------------------------------------------------------------------
+// Full-mass mesh -> particle projection (Eq. proj2): solve M_p x = c with
+// (M_p)_{mu nu} = int psi_mu psi_nu, applied matrix-free from the Delaunay
+// stars (2D: each triangle T of p's star contributes |T|/12 (2 x_p + x_a +
+// x_b)) or from the sorted order (1D: gaps g give g/6 (x_left + 2 x_p) and
+// g/6 (2 x_p + x_right)). Conjugate gradients with the Jacobi preconditioner
+// (diagonal v/2 in 2D, 2v/3 in 1D), from the lumped start c/v, in one
+// persistent cooperative kernel with the same fixed-order FP64 reductions as
+// the mesh solve.
+// ---------------------------------------------------------------------------
+struct PCG {
+    Geo g;
+    int F;
+    ll np;
+    const float *c, *vol;
+    const uint2 *pos;
+    const int *nbr;
+    const unsigned char *deg;
+    float *x, *r, *p, *q;
+    double *red, *scal;
+    unsigned *bar;
+    int *status;
+    double rtol;
+    int max_iter;
+    float unit;  // L / 2^32: torus units -> length
+};
+
+template <int DIM>
+__device__ __forceinline__ float pmass_apply(const PCG &a, const float *__restrict__ xf, ll s) {
+    if (DIM == 1) {
+        const ll np = a.np;
+        const uint32_t X = a.pos[s].x;
+        const ll sl = s == 0 ? np - 1 : s - 1, sr = s + 1 == np ? 0 : s + 1;
+        const float u = a.unit * (1.0f / 6.0f);
+        const float gl = (float)(uint32_t)(X - a.pos[sl].x) * u, gr = (float)(uint32_t)(a.pos[sr].x - X) * u;
+        const float xs = xf[s];
+        KSum acc;
+        acc.add(gl * xf[sl]);
+        acc.add(2.0f * (gl + gr) * xs);
+        acc.add(gr * xf[sr]);
+        return acc.get();
+    }
+    const ll np = a.np;
+    const int m = a.deg[s];
+    const uint2 Xp = a.pos[s];
+    const float k12 = a.unit * a.unit * (1.0f / 24.0f);  // |T|/12 = area2 u^2 / 24
+    const float xs = xf[s];
+    KSum acc;
+    int e = a.nbr[(ll)(m - 1) * np + s];
+    int ida = e & 0x0fffffff, ca = (unsigned)e >> 28;
+    ll ax = (ll)a.pos[ida].x + (ll)(ca / 3 - 1) * 4294967296LL - (ll)Xp.x;
+    ll ay = (ll)a.pos[ida].y + (ll)(ca % 3 - 1) * 4294967296LL - (ll)Xp.y;
+    float xa = xf[ida];
+    for (int k = 0; k < m; ++k) {
+        const int eb = a.nbr[(ll)k * np + s];
+        const int idb = eb & 0x0fffffff, cb = (unsigned)eb >> 28;
+        PM_CHK(idb >= 0 && idb < np, 402, break)
+        const ll bx = (ll)a.pos[idb].x + (ll)(cb / 3 - 1) * 4294967296LL - (ll)Xp.x;
+        const ll by = (ll)a.pos[idb].y + (ll)(cb % 3 - 1) * 4294967296LL - (ll)Xp.y;
+        const float xb = xf[idb];
+        const float w = (float)(ax * by - ay * bx) * k12;
+        acc.add(w * (2.0f * xs + xa + xb));
+        ax = bx;
+        ay = by;
+        xa = xb;
+    }
+    return acc.get();
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_pcg(PCG a) {
+    const int F = a.F;
+    const ll np = a.np;
+    const ll tid = (ll)blockIdx.x * blockDim.x + threadIdx.x, nth = (ll)gridDim.x * blockDim.x;
+    const float dfac = DIM == 2 ? 0.5f : 2.0f / 3.0f;  // Jacobi diagonal = dfac v
+    double v[PM_MAXF], w[PM_MAXF], cc[PM_MAXF], rz[PM_MAXF];
+    bool act[PM_MAXF];
+    int it_f[PM_MAXF];
+    // --- lumped start x = c / v; norms and sums of c
+    double ab[PM_MAXF];
+    for (int f = 0; f < F; ++f) {
+        Dot2 s2, s1, sa;
+        for (ll s = tid; s < np; s += nth) {
+            const float cv = a.c[(ll)f * np + s], vv = a.vol[s];
+            a.x[(ll)f * np + s] = vv > 0.0f ? cv / vv : 0.0f;
+            s2.fma_acc(cv, cv);
+            s1.add(cv);
+            sa.add(fabsf(cv));
+        }
+        v[f] = (double)s2.hi + (double)s2.lo;
+        w[f] = (double)s1.hi + (double)s1.lo;
+        ab[f] = (double)sa.hi + (double)sa.lo;
+    }
+    block_partial(v, F, a.red, 0);
+    block_partial(w, F, a.red, 1);
+    block_partial(ab, F, a.red, 2);
+    if (!grid_sync(a.bar, a.status)) return;
+    double sumc[PM_MAXF], sumabs[PM_MAXF];
+    grid_total(a.red, F, 0, cc);
+    grid_total(a.red, F, 1, sumc);
+    grid_total(a.red, F, 2, sumabs);
+    // --- r = c - M x, z = r / d, p = z; (r, r), (r, z)
+    for (int f = 0; f < F; ++f) {
+        Dot2 s2, sz;
+        const float *xf = a.x + (ll)f * np;
+        for (ll s = tid; s < np; s += nth) {
+            const float rv = a.c[(ll)f * np + s] - pmass_apply<DIM>(a, xf, s);
+            const float d = dfac * a.vol[s];
+            const float zv = d > 0.0f ? rv / d : 0.0f;
+            a.r[(ll)f * np + s] = rv;
+            a.p[(ll)f * np + s] = zv;
+            s2.fma_acc(rv, rv);
+            sz.fma_acc(rv, zv);
+        }
+        v[f] = (double)s2.hi + (double)s2.lo;
+        w[f] = (double)sz.hi + (double)sz.lo;
+    }
+    block_partial(v, F, a.red, 0);
+    block_partial(w, F, a.red, 1);
+    if (!grid_sync(a.bar, a.status)) return;
+    double rr[PM_MAXF];
+    grid_total(a.red, F, 0, rr);
+    grid_total(a.red, F, 1, rz);
+    const double tol2 = a.rtol * a.rtol;
+    for (int f = 0; f < F; ++f) {
+        act[f] = cc[f] > 0.0 && rr[f] > tol2 * cc[f];
+        it_f[f] = 0;
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            a.scal[f * 16 + S_INIT] = cc[f] > 0.0 ? sqrt(rr[f] / cc[f]) : 0.0;
+    }
+    for (int it = 0; it < a.max_iter; ++it) {
+        bool any = false;
+        for (int f = 0; f < F; ++f) any |= act[f];
+        if (!any) break;
+        // q = M p, (p, q)
+        for (int f = 0; f < F; ++f) {
+            v[f] = 0.0;
+            if (!act[f]) continue;
+            Dot2 s;
+            const float *pf = a.p + (ll)f * np;
+            for (ll i = tid; i < np; i += nth) {
+                const float qv = pmass_apply<DIM>(a, pf, i);
+                a.q[(ll)f * np + i] = qv;
+                s.fma_acc(pf[i], qv);
+            }
+            v[f] = (double)s.hi + (double)s.lo;
+        }
+        block_partial(v, F, a.red, 0);
+        if (!grid_sync(a.bar, a.status)) return;
+        grid_total(a.red, F, 0, w);
+        // x += alpha p, r -= alpha q; (r, r), (r, z) with z = r / d
+        double rz_new[PM_MAXF];
+        for (int f = 0; f < F; ++f) {
+            v[f] = 0.0;
+            rz_new[f] = 0.0;
+            if (!act[f]) continue;
+            const float al = (float)(rz[f] / w[f]);
+            Dot2 s2, sz;
+            for (ll i = tid; i < np; i += nth) {
+                const ll o = (ll)f * np + i;
+                a.x[o] = fmaf(al, a.p[o], a.x[o]);
+                const float rv = fmaf(-al, a.q[o], a.r[o]);
+                a.r[o] = rv;
+                const float d = dfac * a.vol[i];
+                const float zv = d > 0.0f ? rv / d : 0.0f;
+                s2.fma_acc(rv, rv);
+                sz.fma_acc(rv, zv);
+            }
+            v[f] = (double)s2.hi + (double)s2.lo;
+            rz_new[f] = (double)sz.hi + (double)sz.lo;
+        }
+        block_partial(v, F, a.red, 0);
+        block_partial(rz_new, F, a.red, 1);
+        if (!grid_sync(a.bar, a.status)) return;
+        grid_total(a.red, F, 0, rr);
+        grid_total(a.red, F, 1, rz_new);
+        double beta[PM_MAXF];
+        for (int f = 0; f < F; ++f) {
+            beta[f] = 0.0;
+            if (!act[f]) continue;
+            beta[f] = rz_new[f] / rz[f];
+            rz[f] = rz_new[f];
+            ++it_f[f];
+            if (rr[f] <= tol2 * cc[f]) act[f] = false;
+        }
+        // p = z + beta p
+        for (int f = 0; f < F; ++f) {
+            if (!act[f]) continue;
+            const float be = (float)beta[f];
+            for (ll i = tid; i < np; i += nth) {
+                const ll o = (ll)f * np + i;
+                const float d = dfac * a.vol[i];
+                const float zv = d > 0.0f ? a.r[o] / d : 0.0f;
+                a.p[o] = fmaf(be, a.p[o], zv);
+            }
+        }
+        if (!grid_sync(a.bar, a.status)) return;
+    }
+    // --- report: true residual, sum v x (= sum c for the exact solution)
+    for (int f = 0; f < F; ++f) {
+        Dot2 s2, sv;
+        const float *xf = a.x + (ll)f * np;
+        for (ll s = tid; s < np; s += nth) {
+            const float rv = a.c[(ll)f * np + s] - pmass_apply<DIM>(a, xf, s);
+            s2.fma_acc(rv, rv);
+            sv.fma_acc(a.vol[s], xf[s]);
+        }
+        v[f] = (double)s2.hi + (double)s2.lo;
+        w[f] = (double)sv.hi + (double)sv.lo;
+    }
+    block_partial(v, F, a.red, 0);
+    block_partial(w, F, a.red, 1);
+    if (!grid_sync(a.bar, a.status)) return;
+    double tr[PM_MAXF], svx[PM_MAXF];
+    grid_total(a.red, F, 0, tr);
+    grid_total(a.red, F, 1, svx);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        bool bad = false;
+        for (int f = 0; f < F; ++f) {
+            const double res = cc[f] > 0.0 ? sqrt(tr[f] / cc[f]) : 0.0;
+            a.scal[f * 16 + S_ITERS] = it_f[f];
+            a.scal[f * 16 + S_RESID] = res;
+            a.scal[f * 16 + S_SUMMESH] = sumc[f];  // int Ab = sum_mu c_mu
+            a.scal[f * 16 + S_SUMPART] = svx[f];   // sum_mu v_mu Abb_mu
+            a.scal[f * 16 + S_SUMABS] = sumabs[f]; // sum_mu |c_mu|: scale of the conservation error
+            if (res > a.rtol) bad = true;
+        }
+        if (bad) atomicOr(a.status, ST_NOTCONV);
+    }
+}
+
 int g_cg_grid[3] = {0, 0, 0};
+int g_pcg_grid[2] = {0, 0};
 
 }  // namespace
 
@@ -738,6 +984,49 @@ int launch_cg(const Geo &g, Work &w, int F, const float *b_float, bool b_from_fi
     }
     int grid = g_cg_grid[di];
     ll need = ((quad ? g.ncell / 4 : g.ncell) + 255) / 256;
+    if (need < grid) grid = (int)(need < 1 ? 1 : need);
+    cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st);
+    void *args[] = {&a};
+    cudaError_t e = cudaLaunchCooperativeKernel((void *)kern, dim3(grid), dim3(256), args, 0, st);
+    count_launches(1);
+    return (int)e;
+}
+
+int launch_pcg(const Geo &g, Work &w, ll np, int F, const float *c, float *x, double rtol, int max_iter,
+               cudaStream_t st) {
+    PCG a;
+    a.g = g;
+    a.F = F;
+    a.np = np;
+    a.c = c;
+    a.vol = w.vol;
+    a.pos = w.pos;
+    a.nbr = w.nbr;
+    a.deg = w.deg;
+    a.x = x;
+    a.r = w.prp;
+    a.p = w.prp + (ll)w.F_max * w.np_max;
+    a.q = w.pq;
+    a.red = w.red;
+    a.scal = w.scal;
+    a.bar = w.bar;
+    a.status = w.status;
+    a.rtol = rtol;
+    a.max_iter = max_iter;
+    a.unit = (float)(g.L / 4294967296.0);
+    const int di = g.dim - 1;
+    void (*kern)(PCG) = g.dim == 1 ? k_pcg<1> : k_pcg<2>;
+    if (!g_pcg_grid[di]) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, 0);
+        if (per < 1) per = 1;
+        if (per > 4) per = 4;
+        g_pcg_grid[di] = sms * per;
+    }
+    int grid = g_pcg_grid[di];
+    const ll need = (np + 255) / 256;
     if (need < grid) grid = (int)(need < 1 ? 1 : need);
     cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st);
     void *args[] = {&a};

@@ -348,12 +348,19 @@ __device__ __forceinline__ void add64_split(unsigned *lo, unsigned *hi, ull v) {
 // sums) or, outside the window, straight to global memory. While counting,
 // every lane records its owned triangles (star slot, running piece count) so
 // that a piece finds its triangle without walking the star again.
-template <int FF>
+//
+// MODE 1 runs the same pieces the other way (mesh -> particles): it integrates
+// the bilinear mesh interpolant Ab against the three particle functions of
+// the triangle, c_mu = int Ab psi_mu, and adds the results to the particles'
+// 64-bit fixed-point sums cfix (global atomics; order-free integer sums).
+// maxabs then holds max|Ab| per field, and the fixed-point scale keeps 10
+// bits of headroom for particle volumes up to 1024 h^2.
+template <int FF, int MODE>
 __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__restrict__ pos,
                                                const int *__restrict__ cell_start, const int *__restrict__ nbr,
                                                const unsigned char *__restrict__ deg, const float *__restrict__ vals,
                                                int F, const unsigned *__restrict__ maxabs, ll *__restrict__ bfix,
-                                               int tiles_x) {
+                                               int tiles_x, const float *__restrict__ mesh, ll *__restrict__ cfix) {
     // dynamic shared memory: acc_lo, acc_hi [FF][RWIN^2], tab [RTAB][256]
     extern __shared__ unsigned rhs_smem[];
     unsigned(*acc_lo)[RWIN * RWIN] = (unsigned(*)[RWIN * RWIN])rhs_smem;
@@ -387,7 +394,7 @@ __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__rest
     const float hd = g.h * g.h;
     const float sc = (float)n * 2.3283064365386963e-10f;
     int E[FF];
-    for (int f = 0; f < FF; ++f) E[f] = f < F ? fix_exp(maxabs, f, hd) : 0;
+    for (int f = 0; f < FF; ++f) E[f] = f < F ? fix_exp(maxabs, f, hd) - (MODE == 1 ? 10 : 0) : 0;
     const int total = rowpre[RTS];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int tcol = threadIdx.x;
@@ -476,6 +483,49 @@ __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__rest
             const float idet = 1.0f / (e1x * e2y - e1y * e2x);
             const float dsx = ox + fci - up, dty = oy + fcj - wp;
             const int gcx = cxp + ci, gcy = cyp + cj;  // unwrapped cell
+            if (MODE == 1) {
+                // W_k[f] = sum over corners of Ab_c * (K0, K1, K2)_c
+                float W0[FF], W1[FF], W2[FF];
+#pragma unroll
+                for (int f = 0; f < FF; ++f) W0[f] = W1[f] = W2[f] = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float A1 = (c & 1) ? ox : 1.0f - ox, B1 = (c & 1) ? 1.0f : -1.0f;
+                    const float A2 = (c & 2) ? oy : 1.0f - oy, B2 = (c & 2) ? 1.0f : -1.0f;
+                    const float aa = A1 * A2, ab = A1 * B2, ba = B1 * A2, bb = B1 * B2;
+                    const float K0 = aa * M00 + ab * M01 + ba * M10 + bb * M11;
+                    const float K1 = aa * M10 + ab * M11 + ba * M20 + bb * M21;
+                    const float K2 = aa * M01 + ab * M02 + ba * M11 + bb * M12;
+                    const int nx = gcx + (c & 1), ny = gcy + ((c >> 1) & 1);
+                    const ll node = (ll)wrapi(ny, n) * n + wrapi(nx, n);
+                    PM_CHK(node >= 0 && node < g.ncell, 309, continue)
+#pragma unroll
+                    for (int f = 0; f < FF; ++f) {
+                        if (f >= F) break;
+                        const float ab_c = __ldg(mesh + (ll)f * g.ncell + node);
+                        W0[f] = fmaf(ab_c, K0, W0[f]);
+                        W1[f] = fmaf(ab_c, K1, W1[f]);
+                        W2[f] = fmaf(ab_c, K2, W2[f]);
+                    }
+                }
+                // barycentric functions about the local origin: lambda = l0 + lx X' + ly Y'
+                const float l0a = (dsx * e2y - dty * e2x) * idet, lxa = e2y * idet, lya = -e2x * idet;
+                const float l0b = (e1x * dty - e1y * dsx) * idet, lxb = -e1y * idet, lyb = e1x * idet;
+                const float l0p = 1.0f - l0a - l0b, lxp = -(lxa + lxb), lyp = -(lya + lyb);
+                const int who[3] = {ps, T.a, T.b};
+                const float L0[3] = {l0p, l0a, l0b}, LX[3] = {lxp, lxa, lxb}, LY[3] = {lyp, lya, lyb};
+#pragma unroll
+                for (int v = 0; v < 3; ++v) {
+#pragma unroll
+                    for (int f = 0; f < FF; ++f) {
+                        if (f >= F) break;
+                        const float val = (L0[v] * W0[f] + LX[v] * W1[f] + LY[v] * W2[f]) * hd;
+                        const ll iv = __float2ll_rn(ldexpf(val, E[f]));
+                        if (iv) atomicAdd((ull *)&cfix[(ll)f * np + who[v]], (ull)iv);
+                    }
+                }
+                continue;
+            }
             float al[FF], gx[FF], gy[FF];
 #pragma unroll
             for (int f = 0; f < FF; ++f) {
@@ -517,6 +567,7 @@ __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__rest
         }
         __syncwarp();
     }
+    if (MODE == 1) return;
     __syncthreads();
     for (int i = threadIdx.x; i < RWIN * RWIN; i += blockDim.x) {
         const int lx = i % RWIN, ly = i / RWIN;
@@ -572,16 +623,35 @@ __global__ void k_fix_to_float(Geo g, int F, const ll *__restrict__ bfix, const 
     out[i] = ldexpf((float)bfix[i], -fix_exp(maxabs, f, hd));
 }
 
-// Per-block sums of v_mu A_mu and v_mu |A_mu| (FP64 across threads).
+// Per-block sums of v_mu A_mu and v_mu |A_mu| (FP64 across threads). Each
+// thread takes 4 consecutive particles per step (16-byte loads when the
+// arrays allow it) so that enough loads are in flight.
 __global__ void __launch_bounds__(256) k_psum(ll np, const float *__restrict__ vals, const float *__restrict__ vol,
                                               int F, double *__restrict__ out, int nblk) {
     __shared__ double sh[2 * PM_MAXF][8];
+    const ll tid = (ll)blockIdx.x * blockDim.x + threadIdx.x, nth = (ll)gridDim.x * blockDim.x;
+    const bool vec = (np & 3) == 0;
     for (int f = 0; f < F; ++f) {
         Dot2 a, b;
-        for (ll s = (ll)blockIdx.x * blockDim.x + threadIdx.x; s < np; s += (ll)gridDim.x * blockDim.x) {
-            float v = vol[s], x = vals[(ll)f * np + s];
-            a.fma_acc(v, x);
-            b.fma_acc(v, fabsf(x));
+        const float *x = vals + (ll)f * np;
+        if (vec) {
+            for (ll q = tid; q < np / 4; q += nth) {
+                const float4 v = ((const float4 *)vol)[q], y = ((const float4 *)x)[q];
+                a.fma_acc(v.x, y.x);
+                a.fma_acc(v.y, y.y);
+                a.fma_acc(v.z, y.z);
+                a.fma_acc(v.w, y.w);
+                b.fma_acc(v.x, fabsf(y.x));
+                b.fma_acc(v.y, fabsf(y.y));
+                b.fma_acc(v.z, fabsf(y.z));
+                b.fma_acc(v.w, fabsf(y.w));
+            }
+        } else {
+            for (ll s = tid; s < np; s += nth) {
+                const float v = vol[s], y = x[s];
+                a.fma_acc(v, y);
+                b.fma_acc(v, fabsf(y));
+            }
         }
         double da = (double)a.hi + (double)a.lo, db = (double)b.hi + (double)b.lo;
         for (int o = 16; o > 0; o >>= 1) {
@@ -701,6 +771,75 @@ __global__ void k_apply_corr(Geo g, int F, const float *__restrict__ corr, const
     }
 }
 
+// ---------------------------------------------------------------------------
+// mesh -> particle integrals c_mu = int Ab psi_mu (Table 1, right column)
+// ---------------------------------------------------------------------------
+// max |Ab| of every field (non-negative float bits order like unsigned ints)
+__global__ void k_mesh_max(ll nn, int F, const float *__restrict__ mesh, unsigned *__restrict__ out) {
+    for (int f = 0; f < F; ++f) {
+        float m = 0.0f;
+        for (ll i = (ll)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (ll)gridDim.x * blockDim.x)
+            m = fmaxf(m, fabsf(__ldg(mesh + (ll)f * nn + i)));
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(out + f, __float_as_uint(m));
+    }
+}
+
+// fixed-point particle sums -> float (the scale of the mesh->particle mode)
+__global__ void k_fixc_to_float(ll np, int F, const ll *__restrict__ cfix, const unsigned *__restrict__ meshmax,
+                                float hd, float *__restrict__ c) {
+    ll i = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np * F) return;
+    const int f = (int)(i / np);
+    c[i] = ldexpf((float)cfix[i], -(fix_exp(meshmax, f, hd) - 10));
+}
+
+// 1D: particle s (sorted by position) gathers its own integral over the two
+// intervals beside it, cut at the mesh nodes; Simpson's rule is exact on each
+// piece (linear x linear). Coordinates in cell units relative to s's cell.
+__device__ __forceinline__ float ab1(const float *__restrict__ m, int n, int cx, float u) {
+    const float fe = floorf(u);
+    const float t = u - fe;
+    const int e = cx + (int)fe;
+    return __ldg(m + wrapi(e, n)) * (1.0f - t) + __ldg(m + wrapi(e + 1, n)) * t;
+}
+
+__global__ void k_g2pint1d(Geo g, ll np, const uint2 *__restrict__ pos, const float *__restrict__ mesh, int F,
+                           float *__restrict__ c) {
+    ll s = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= np) return;
+    const int n = g.n;
+    const uint32_t X = pos[s].x;
+    const uint32_t Xl = pos[s == 0 ? np - 1 : s - 1].x, Xr = pos[s + 1 == np ? 0 : s + 1].x;
+    const float sc = (float)n * 2.3283064365386963e-10f;
+    const float dl = np > 1 ? (float)(uint32_t)(X - Xl) * sc : (float)n, dr = np > 1 ? (float)(uint32_t)(Xr - X) * sc
+                                                                                   : (float)n;
+    const int cx = cell_of(X, n);
+    const float fs = frac_f(X, n);
+    for (int f = 0; f < F; ++f) {
+        const float *m = mesh + (ll)f * n;
+        KSum acc;
+        // left interval [fs - dl, fs]: psi rises from 0 to 1
+        for (int side = 0; side < 2; ++side) {
+            const float a = side == 0 ? fs - dl : fs, b = side == 0 ? fs : fs + dr, len = side == 0 ? dl : dr;
+            if (!(len > 0.0f)) continue;
+            float cur = a;
+            while (cur < b) {
+                const float nxt = fminf(floorf(cur) + 1.0f, b);
+                const float mid = 0.5f * (cur + nxt);
+                const float pa = side == 0 ? (cur - a) / len : (b - cur) / len;
+                const float pm = side == 0 ? (mid - a) / len : (b - mid) / len;
+                const float pb = side == 0 ? (nxt - a) / len : (b - nxt) / len;
+                const float q = (nxt - cur) * (1.0f / 6.0f) *
+                                (ab1(m, n, cx, cur) * pa + 4.0f * ab1(m, n, cx, mid) * pm + ab1(m, n, cx, nxt) * pb);
+                acc.add(q);
+                cur = nxt;
+            }
+        }
+        c[(ll)f * np + s] = acc.get() * g.h;
+    }
+}
+
 }  // namespace
 
 void launch_features(const Geo &g, Work &w, int F, const float *delta, cudaStream_t st) {
@@ -746,7 +885,8 @@ static size_t rhs2d_smem() {
 // device (called when a context is created, outside any stream capture).
 template <int FF>
 static void rhs_attr() {
-    cudaFuncSetAttribute(k_rhs2d<FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs2d_smem<FF>());
+    cudaFuncSetAttribute(k_rhs2d<FF, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs2d_smem<FF>());
+    cudaFuncSetAttribute(k_rhs2d<FF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs2d_smem<FF>());
 }
 
 void rhs_prepare_device() {
@@ -758,7 +898,16 @@ void rhs_prepare_device() {
 template <int FF>
 static void launch_rhs2d(const Geo &g, Work &w, ll np, int F, int nt, int tx, cudaStream_t st) {
     const size_t bytes = rhs2d_smem<FF>();
-    k_rhs2d<FF><<<nt, 256, bytes, st>>>(g, np, w.pos, w.cell_start, w.nbr, w.deg, w.vals, F, w.maxabs, w.bfix, tx);
+    k_rhs2d<FF, 0><<<nt, 256, bytes, st>>>(g, np, w.pos, w.cell_start, w.nbr, w.deg, w.vals, F, w.maxabs, w.bfix,
+                                           tx, nullptr, nullptr);
+}
+
+template <int FF>
+static void launch_g2pint2d(const Geo &g, Work &w, ll np, int F, const float *mesh, int nt, int tx,
+                            cudaStream_t st) {
+    const size_t bytes = rhs2d_smem<FF>();
+    k_rhs2d<FF, 1><<<nt, 256, bytes, st>>>(g, np, w.pos, w.cell_start, w.nbr, w.deg, nullptr, F, w.meshmax,
+                                           nullptr, tx, mesh, w.cfix);
 }
 
 void launch_rhs(const Geo &g, Work &w, ll np, int F, cudaStream_t st) {
@@ -779,6 +928,58 @@ void launch_rhs(const Geo &g, Work &w, ll np, int F, cudaStream_t st) {
 
 void launch_rhs_to_float(const Geo &g, Work &w, int F, float *b_out, cudaStream_t st) {
     k_fix_to_float<<<div_up(g.ncell * F, 256), 256, 0, st>>>(g, F, w.bfix, w.maxabs, b_out);
+    count_launches(1);
+}
+
+// c_mu = int Ab psi_mu for every (sorted) particle and field -> c [F][np].
+void launch_g2p_integral(const Geo &g, Work &w, ll np, int F, const float *mesh, float *c, cudaStream_t st) {
+    if (np <= 0) return;
+    cudaMemsetAsync(w.meshmax, 0, sizeof(unsigned) * PM_MAXF, st);
+    k_mesh_max<<<2 * 152, 256, 0, st>>>(g.ncell, F, mesh, w.meshmax);
+    if (g.dim == 1) {
+        k_g2pint1d<<<div_up(np, 256), 256, 0, st>>>(g, np, w.pos, mesh, F, c);
+        count_launches(2);
+        return;
+    }
+    cudaMemsetAsync(w.cfix, 0, sizeof(ll) * np * F, st);
+    const int tx = div_up(g.n, RTS), nt = tx * tx;
+    if (F <= 2)
+        launch_g2pint2d<2>(g, w, np, F, mesh, nt, tx, st);
+    else if (F <= 4)
+        launch_g2pint2d<4>(g, w, np, F, mesh, nt, tx, st);
+    else
+        launch_g2pint2d<PM_MAXF>(g, w, np, F, mesh, nt, tx, st);
+    k_fixc_to_float<<<div_up(np * F, 256), 256, 0, st>>>(np, F, w.cfix, w.meshmax, g.h * g.h, c);
+    count_launches(3);
+}
+
+namespace {
+// Lumped mesh -> particle values: c_mu / v_mu (in place, sorted order).
+__global__ void k_div_vol(ll np, int F, const float *__restrict__ vol, float *__restrict__ c) {
+    ll i = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np * F) return;
+    const float v = vol[i % np];
+    c[i] = v > 0.0f ? c[i] / v : 0.0f;
+}
+}  // namespace
+
+void launch_div_vol(ll np, int F, const float *vol, float *c, cudaStream_t st) {
+    if (np <= 0) return;
+    k_div_vol<<<div_up(np * F, 256), 256, 0, st>>>(np, F, vol, c);
+    count_launches(1);
+}
+
+namespace {
+// Lumped particle -> mesh values: b_i / h^dim (in place).
+__global__ void k_scale(ll m, float s, float *__restrict__ x) {
+    ll i = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) x[i] *= s;
+}
+}  // namespace
+
+void launch_scale(ll m, float s, float *x, cudaStream_t st) {
+    if (m <= 0) return;
+    k_scale<<<div_up(m, 256), 256, 0, st>>>(m, s, x);
     count_launches(1);
 }
 
