@@ -272,6 +272,29 @@ def run_mixture(args, pm, torch, dist, local):
                "d2h_bytes_per_step": bo, "ms_per_step": te}
 
     plain, learned = res["plain"], res["learned"]
+    # mesh -> particle projections of the assigned fields back onto the same
+    # particles: full mass (Eq. proj2, CG to 1e-6) and lumped (Eq. lumped)
+    mesh_fields = out.clone()
+    back = torch.empty(F, N, device=dev)
+    _, pinfo = ctx.interpolate_mass(mesh_fields, px, py, out=back)
+    proj = {}
+    for name, fn in (("full_mass", lambda: ctx.interpolate_mass(mesh_fields, px, py, out=back, info=False)),
+                     ("lumped", lambda: ctx.interpolate_lumped(mesh_fields, px, py, out=back)),
+                     ("delta", lambda: ctx.interpolate(mesh_fields, px, py, out=back))):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ctx.profile_read(reset=True)
+        ms = time_steps(torch, stream, flush, args.steps, fn)
+        prof = ctx.profile_read(reset=True)
+        ctx.profile(False)
+        t = max_over_ranks(torch, dist, sum(ms) / len(ms), dev)
+        proj[name] = {"ms_per_step": t, "value": args.world * N * F / (t * 1e-3),
+                      "phase_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[0] > 0}}
+    proj["full_mass"]["solve"] = {"iters": [i.iters for i in pinfo], "rel_resid": [i.rel_resid for i in pinfo],
+                                  "cons_err": [i.cons_err for i in pinfo],
+                                  "init_rel_resid": [i.init_rel_resid for i in pinfo]}
     # one untimed pass of the counting build of the triangulation
     ctx.profile(True, count_work=True)
     ctx.assign_mass(px, py, vals, out=out, info=False)
@@ -307,6 +330,9 @@ def run_mixture(args, pm, torch, dist, local):
                     "phase_ms_per_step": {k: round(v, 4) for k, v in learned["phase_ms"].items()},
                     "solve": solve_report(learned["info"]), "gpu_launches": learned["launches"],
                     "network": "4-layer 3x3 conv 2-32-32-32-1, BF16 tcgen05, shipped weights"},
+        "mesh_to_particle": {"what": "the step's mesh fields projected back onto the same particles; each entry is "
+                                     "one call per step (full mass includes the sort and triangulation)",
+                             **proj},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -206,7 +206,7 @@ pm_status pm_ctx_create(pm_ctx **out, int dim, int n, double L, long long max_pa
               alloc(c, &w.pc, F * np) && alloc(c, &w.px, F * np) && alloc(c, &w.pq, F * np) &&
               alloc(c, &w.prp, 2 * F * np);
     w.cfix = (ll *)w.prp;
-    if (ok && dim == 2) ok = alloc(c, &w.nbr, (ll)PM_MAXDEG * np);
+    if (ok && dim == 2) ok = alloc(c, &w.nbr, (ll)PM_MAXDEG * np) && alloc(c, &w.pcoef, (ll)PM_MAXDEG * np);
     if (ok && dim == 2 && n % 128 == 0)
         ok = alloc(c, &w.feat, 2 * F * nc) && alloc(c, &w.corr, F * nc);
     if (ok && cudaMallocHost((void **)&w.hstatus, sizeof(int)) != cudaSuccess) ok = false;
@@ -234,7 +234,7 @@ void pm_ctx_destroy(pm_ctx *c) {
     void *ptrs[] = {w.fx,  w.key, w.slot, w.count, w.cell_start, w.scan_tmp, w.tmp,  w.perm,  w.pos,
                     w.vals, w.maxabs, w.nbr, w.deg,  w.vol,  w.part,  w.bfix, w.psum, w.r,     w.p,
                     w.q,   w.b,   w.red,  w.scal,  w.bar,  w.status, w.empty, w.ntri, w.feat, w.corr,
-                    w.wsum, w.nretry, w.meshmax, w.pc, w.px, w.pq, w.prp};
+                    w.wsum, w.nretry, w.meshmax, w.pc, w.px, w.pq, w.prp, w.pcoef};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (w.hstatus) cudaFreeHost(w.hstatus);

@@ -79,6 +79,7 @@ struct Work {
     float *pc, *px, *pq;   // [F][np] right-hand side c, solution, M_p p
     float *prp;            // [2][F][np] residual and search direction (r, then p)
     ll *cfix;              // = (ll *)prp: fixed-point c before conversion
+    float *pcoef;          // [PM_MAXDEG][np] particle mass matrix rows (2D)
 };
 
 // ---------------------------------------------------------------------------

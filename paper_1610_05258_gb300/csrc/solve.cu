@@ -720,6 +720,7 @@ struct PCG {
     const uint2 *pos;
     const int *nbr;
     const unsigned char *deg;
+    const float *coef;  // [PM_MAXDEG][np] off-diagonal row coefficients (2D)
     float *x, *r, *p, *q;
     double *red, *scal;
     unsigned *bar;
@@ -729,49 +730,80 @@ struct PCG {
     float unit;  // L / 2^32: torus units -> length
 };
 
-template <int DIM>
-__device__ __forceinline__ float pmass_apply(const PCG &a, const float *__restrict__ xf, ll s) {
+// The same row applied to every active field at once (one pass over the row):
+// out[f] = (M_p x_f)_s for the fields with act[f].
+template <int DIM, int FF>
+__device__ __forceinline__ void pmass_apply_all(const PCG &a, const float *__restrict__ xb, ll s, const bool *act,
+                                                float *out) {
+    const int F = a.F;
+    const ll np = a.np;
+    KSum acc[FF];
     if (DIM == 1) {
-        const ll np = a.np;
         const uint32_t X = a.pos[s].x;
         const ll sl = s == 0 ? np - 1 : s - 1, sr = s + 1 == np ? 0 : s + 1;
         const float u = a.unit * (1.0f / 6.0f);
         const float gl = (float)(uint32_t)(X - a.pos[sl].x) * u, gr = (float)(uint32_t)(a.pos[sr].x - X) * u;
-        const float xs = xf[s];
-        KSum acc;
-        acc.add(gl * xf[sl]);
-        acc.add(2.0f * (gl + gr) * xs);
-        acc.add(gr * xf[sr]);
-        return acc.get();
+#pragma unroll
+        for (int f = 0; f < FF; ++f) {
+            if (f >= F || !act[f]) continue;
+            const float *xf = xb + (ll)f * np;
+            acc[f].add(gl * xf[sl]);
+            acc[f].add(2.0f * (gl + gr) * xf[s]);
+            acc[f].add(gr * xf[sr]);
+            out[f] = acc[f].get();
+        }
+        return;
     }
-    const ll np = a.np;
     const int m = a.deg[s];
-    const uint2 Xp = a.pos[s];
-    const float k12 = a.unit * a.unit * (1.0f / 24.0f);  // |T|/12 = area2 u^2 / 24
-    const float xs = xf[s];
-    KSum acc;
-    int e = a.nbr[(ll)(m - 1) * np + s];
-    int ida = e & 0x0fffffff, ca = (unsigned)e >> 28;
-    ll ax = (ll)a.pos[ida].x + (ll)(ca / 3 - 1) * 4294967296LL - (ll)Xp.x;
-    ll ay = (ll)a.pos[ida].y + (ll)(ca % 3 - 1) * 4294967296LL - (ll)Xp.y;
-    float xa = xf[ida];
+    const float d = 0.5f * a.vol[s];
+#pragma unroll
+    for (int f = 0; f < FF; ++f)
+        if (f < F && act[f]) acc[f].add(d * xb[(ll)f * np + s]);
     for (int k = 0; k < m; ++k) {
-        const int eb = a.nbr[(ll)k * np + s];
-        const int idb = eb & 0x0fffffff, cb = (unsigned)eb >> 28;
-        PM_CHK(idb >= 0 && idb < np, 402, break)
-        const ll bx = (ll)a.pos[idb].x + (ll)(cb / 3 - 1) * 4294967296LL - (ll)Xp.x;
-        const ll by = (ll)a.pos[idb].y + (ll)(cb % 3 - 1) * 4294967296LL - (ll)Xp.y;
-        const float xb = xf[idb];
-        const float w = (float)(ax * by - ay * bx) * k12;
-        acc.add(w * (2.0f * xs + xa + xb));
-        ax = bx;
-        ay = by;
-        xa = xb;
+        const int id = a.nbr[(ll)k * np + s] & 0x0fffffff;
+        PM_CHK(id >= 0 && id < np, 403, break)
+        const float w = a.coef[(ll)k * np + s];
+#pragma unroll
+        for (int f = 0; f < FF; ++f)
+            if (f < F && act[f]) acc[f].add(w * xb[(ll)f * np + id]);
     }
-    return acc.get();
+#pragma unroll
+    for (int f = 0; f < FF; ++f)
+        if (f < F && act[f]) out[f] = acc[f].get();
 }
 
-template <int DIM>
+// Coefficients of the particle mass matrix rows from the stars: slot k of
+// particle p gets (|T_k| + |T_k+1|) / 12, T_k = (p, q_k-1, q_k), areas from
+// exact 64-bit cross products of the torus coordinates.
+__global__ void k_star_coef(ll np, const uint2 *__restrict__ pos, const int *__restrict__ nbr,
+                            const unsigned char *__restrict__ deg, float unit, float *__restrict__ coef) {
+    const ll s = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= np) return;
+    const int m = deg[s];
+    if (m < 3) return;
+    const uint2 Xp = pos[s];
+    const float k12 = unit * unit * (1.0f / 24.0f);  // |T|/12 = area2 unit^2 / 24
+    auto rel = [&](int e, ll &rx, ll &ry) {
+        const int id = e & 0x0fffffff, cd = (unsigned)e >> 28;
+        rx = (ll)pos[id].x + (ll)(cd / 3 - 1) * 4294967296LL - (ll)Xp.x;
+        ry = (ll)pos[id].y + (ll)(cd % 3 - 1) * 4294967296LL - (ll)Xp.y;
+    };
+    ll ax, ay, bx, by;
+    rel(nbr[(ll)(m - 1) * np + s], ax, ay);
+    float wprev = 0.0f, wfirst = 0.0f;
+    for (int k = 0; k < m; ++k) {
+        rel(nbr[(ll)k * np + s], bx, by);
+        const float w = (float)(ax * by - ay * bx) * k12;  // triangle k = (p, q_k-1, q_k)
+        if (k == 0) wfirst = w;
+        else coef[(ll)(k - 1) * np + s] = wprev + w;      // edge (p, q_k-1): triangles k-1 and k
+        wprev = w;
+        ax = bx;
+        ay = by;
+    }
+    coef[(ll)(m - 1) * np + s] = wprev + wfirst;           // edge (p, q_m-1): triangles m-1 and 0
+}
+
+template <int DIM, int FF>
 __global__ void __launch_bounds__(256) k_pcg(PCG a) {
     const int F = a.F;
     const ll np = a.np;
@@ -804,20 +836,31 @@ __global__ void __launch_bounds__(256) k_pcg(PCG a) {
     grid_total(a.red, F, 1, sumc);
     grid_total(a.red, F, 2, sumabs);
     // --- r = c - M x, z = r / d, p = z; (r, r), (r, z)
-    for (int f = 0; f < F; ++f) {
-        Dot2 s2, sz;
-        const float *xf = a.x + (ll)f * np;
+    bool all[PM_MAXF];
+    for (int f = 0; f < PM_MAXF; ++f) all[f] = f < F;
+    {
+        Dot2 s2[FF], sz[FF];
+        float mx[FF];
         for (ll s = tid; s < np; s += nth) {
-            const float rv = a.c[(ll)f * np + s] - pmass_apply<DIM>(a, xf, s);
+            pmass_apply_all<DIM, FF>(a, a.x, s, all, mx);
             const float d = dfac * a.vol[s];
-            const float zv = d > 0.0f ? rv / d : 0.0f;
-            a.r[(ll)f * np + s] = rv;
-            a.p[(ll)f * np + s] = zv;
-            s2.fma_acc(rv, rv);
-            sz.fma_acc(rv, zv);
+#pragma unroll
+            for (int f = 0; f < FF; ++f) {
+                if (f >= F) break;
+                const float rv = a.c[(ll)f * np + s] - mx[f];
+                const float zv = d > 0.0f ? rv / d : 0.0f;
+                a.r[(ll)f * np + s] = rv;
+                a.p[(ll)f * np + s] = zv;
+                s2[f].fma_acc(rv, rv);
+                sz[f].fma_acc(rv, zv);
+            }
         }
-        v[f] = (double)s2.hi + (double)s2.lo;
-        w[f] = (double)sz.hi + (double)sz.lo;
+#pragma unroll
+        for (int f = 0; f < FF; ++f) {
+            if (f >= F) break;
+            v[f] = (double)s2[f].hi + (double)s2[f].lo;
+            w[f] = (double)sz[f].hi + (double)sz[f].lo;
+        }
     }
     block_partial(v, F, a.red, 0);
     block_partial(w, F, a.red, 1);
@@ -836,18 +879,22 @@ __global__ void __launch_bounds__(256) k_pcg(PCG a) {
         bool any = false;
         for (int f = 0; f < F; ++f) any |= act[f];
         if (!any) break;
-        // q = M p, (p, q)
-        for (int f = 0; f < F; ++f) {
-            v[f] = 0.0;
-            if (!act[f]) continue;
-            Dot2 s;
-            const float *pf = a.p + (ll)f * np;
+        // q = M p, (p, q) for the active fields in one pass over the rows
+        {
+            Dot2 sq[FF];
+            float mq[FF];
             for (ll i = tid; i < np; i += nth) {
-                const float qv = pmass_apply<DIM>(a, pf, i);
-                a.q[(ll)f * np + i] = qv;
-                s.fma_acc(pf[i], qv);
+                pmass_apply_all<DIM, FF>(a, a.p, i, act, mq);
+#pragma unroll
+                for (int f = 0; f < FF; ++f) {
+                    if (f >= F || !act[f]) continue;
+                    a.q[(ll)f * np + i] = mq[f];
+                    sq[f].fma_acc(a.p[(ll)f * np + i], mq[f]);
+                }
             }
-            v[f] = (double)s.hi + (double)s.lo;
+#pragma unroll
+            for (int f = 0; f < FF; ++f)
+                if (f < F) v[f] = act[f] ? (double)sq[f].hi + (double)sq[f].lo : 0.0;
         }
         block_partial(v, F, a.red, 0);
         if (!grid_sync(a.bar, a.status)) return;
@@ -901,16 +948,25 @@ __global__ void __launch_bounds__(256) k_pcg(PCG a) {
         if (!grid_sync(a.bar, a.status)) return;
     }
     // --- report: true residual, sum v x (= sum c for the exact solution)
-    for (int f = 0; f < F; ++f) {
-        Dot2 s2, sv;
-        const float *xf = a.x + (ll)f * np;
+    {
+        Dot2 s2[FF], sv[FF];
+        float mx[FF];
         for (ll s = tid; s < np; s += nth) {
-            const float rv = a.c[(ll)f * np + s] - pmass_apply<DIM>(a, xf, s);
-            s2.fma_acc(rv, rv);
-            sv.fma_acc(a.vol[s], xf[s]);
+            pmass_apply_all<DIM, FF>(a, a.x, s, all, mx);
+#pragma unroll
+            for (int f = 0; f < FF; ++f) {
+                if (f >= F) break;
+                const float rv = a.c[(ll)f * np + s] - mx[f];
+                s2[f].fma_acc(rv, rv);
+                sv[f].fma_acc(a.vol[s], a.x[(ll)f * np + s]);
+            }
         }
-        v[f] = (double)s2.hi + (double)s2.lo;
-        w[f] = (double)sv.hi + (double)sv.lo;
+#pragma unroll
+        for (int f = 0; f < FF; ++f) {
+            if (f >= F) break;
+            v[f] = (double)s2[f].hi + (double)s2[f].lo;
+            w[f] = (double)sv[f].hi + (double)sv[f].lo;
+        }
     }
     block_partial(v, F, a.red, 0);
     block_partial(w, F, a.red, 1);
@@ -934,7 +990,7 @@ __global__ void __launch_bounds__(256) k_pcg(PCG a) {
 }
 
 int g_cg_grid[3] = {0, 0, 0};
-int g_pcg_grid[2] = {0, 0};
+int g_pcg_grid[6] = {0, 0, 0, 0, 0, 0};
 
 }  // namespace
 
@@ -1003,6 +1059,7 @@ int launch_pcg(const Geo &g, Work &w, ll np, int F, const float *c, float *x, do
     a.pos = w.pos;
     a.nbr = w.nbr;
     a.deg = w.deg;
+    a.coef = w.pcoef;
     a.x = x;
     a.r = w.prp;
     a.p = w.prp + (ll)w.F_max * w.np_max;
@@ -1014,8 +1071,12 @@ int launch_pcg(const Geo &g, Work &w, ll np, int F, const float *c, float *x, do
     a.rtol = rtol;
     a.max_iter = max_iter;
     a.unit = (float)(g.L / 4294967296.0);
-    const int di = g.dim - 1;
-    void (*kern)(PCG) = g.dim == 1 ? k_pcg<1> : k_pcg<2>;
+    // instantiations for up to 2, 4 and PM_MAXF fields (accumulators in registers)
+    const int fi = F <= 2 ? 0 : (F <= 4 ? 1 : 2);
+    const int di = (g.dim - 1) * 3 + fi;
+    void (*const kerns[6])(PCG) = {k_pcg<1, 2>, k_pcg<1, 4>, k_pcg<1, PM_MAXF>,
+                                   k_pcg<2, 2>, k_pcg<2, 4>, k_pcg<2, PM_MAXF>};
+    void (*kern)(PCG) = kerns[di];
     if (!g_pcg_grid[di]) {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
@@ -1028,6 +1089,10 @@ int launch_pcg(const Geo &g, Work &w, ll np, int F, const float *c, float *x, do
     int grid = g_pcg_grid[di];
     const ll need = (np + 255) / 256;
     if (need < grid) grid = (int)(need < 1 ? 1 : need);
+    if (g.dim == 2 && np > 0) {
+        k_star_coef<<<div_up(np, 256), 256, 0, st>>>(np, w.pos, w.nbr, w.deg, a.unit, w.pcoef);
+        count_launches(1);
+    }
     cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st);
     void *args[] = {&a};
     cudaError_t e = cudaLaunchCooperativeKernel((void *)kern, dim3(grid), dim3(256), args, 0, st);
