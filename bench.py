@@ -220,7 +220,7 @@ def run_mixture(args, pm, torch, dist, local):
     out = torch.empty(F, n * n, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    arms = {"plain": {"warm_start": "delta"}, "learned": {"net": net}}
+    arms = {"plain": {"warm_start": "delta"}, "learned": {"net": net}, "direct": {"warm_start": "direct"}}
     res = {}
     clocks = Clocks(local)
     for name, kw in arms.items():
@@ -271,7 +271,7 @@ def run_mixture(args, pm, torch, dist, local):
         e2e = {"value": args.world * N * F / (te * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo, "ms_per_step": te}
 
-    plain, learned = res["plain"], res["learned"]
+    plain, learned, direct = res["plain"], res["learned"], res["direct"]
     # mesh -> particle projections of the assigned fields back onto the same
     # particles: full mass (Eq. proj2, CG to 1e-6) and lumped (Eq. lumped)
     mesh_fields = out.clone()
@@ -330,6 +330,12 @@ def run_mixture(args, pm, torch, dist, local):
                     "phase_ms_per_step": {k: round(v, 4) for k, v in learned["phase_ms"].items()},
                     "solve": solve_report(learned["info"]), "gpu_launches": learned["launches"],
                     "network": "4-layer 3x3 conv 2-32-32-32-1, BF16 tcgen05, shipped weights"},
+        "direct_start": {"value": args.world * N * F / (direct["ms"] * 1e-3), "ms_per_step": direct["ms"],
+                         "speedup_vs_plain": plain["ms"] / direct["ms"],
+                         "phase_ms_per_step": {k: round(v, 4) for k, v in direct["phase_ms"].items()},
+                         "solve": solve_report(direct["info"]),
+                         "what": "start = exact inverse of the periodic mass matrix (separable circulant convolutions), "
+                                 "then CG confirms the residual"},
         "mesh_to_particle": {"what": "the step's mesh fields projected back onto the same particles; each entry is "
                                      "one call per step (full mass includes the sort and triangulation)",
                              **proj},

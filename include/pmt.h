@@ -60,7 +60,12 @@ typedef enum pm_status {
 
 typedef struct pm_ctx pm_ctx;
 
-enum { PM_WS_DELTA = 0, PM_WS_ZERO = 1, PM_WS_USER = 2, PM_WS_NET = 3 };
+/* Start of the mass solve. PM_WS_DIRECT: the exact inverse of the uniform
+ * periodic mass matrix applied to b (M = M1 (x) M1, M1 = (h/6) circ(1,4,1),
+ * whose inverse circulant has entries decaying as (sqrt 3 - 2)^|j|; applied as
+ * separable convolutions truncated below 2e-10), after which conjugate
+ * gradients only confirm the residual and set the mean mode exactly. */
+enum { PM_WS_DELTA = 0, PM_WS_ZERO = 1, PM_WS_USER = 2, PM_WS_NET = 3, PM_WS_DIRECT = 4 };
 
 typedef struct pm_net pm_net;
 

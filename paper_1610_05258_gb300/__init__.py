@@ -19,7 +19,7 @@ _LIBPATH = os.environ.get("PM_LIBRARY") or os.path.join(
     _HERE, "_build_checked" if os.environ.get("PM_CHECKED") == "1" else "_build", "libpmt.so")
 _lib = None
 
-PM_WS_DELTA, PM_WS_ZERO, PM_WS_USER, PM_WS_NET = 0, 1, 2, 3
+PM_WS_DELTA, PM_WS_ZERO, PM_WS_USER, PM_WS_NET, PM_WS_DIRECT = 0, 1, 2, 3, 4
 _STATUS = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ENOTCONV", 4: "PM_ETIMEOUT", 5: "PM_EDEGENERATE",
            6: "PM_ECUDA"}
 
@@ -263,7 +263,8 @@ class Context:
         return (out, e.value) if count_empty else out
 
     def _opts(self, warm_start, rtol, max_iter, x0, net=None):
-        ws = {"delta": PM_WS_DELTA, "zero": PM_WS_ZERO, "user": PM_WS_USER, "net": PM_WS_NET}[warm_start]
+        ws = {"delta": PM_WS_DELTA, "zero": PM_WS_ZERO, "user": PM_WS_USER, "net": PM_WS_NET,
+              "direct": PM_WS_DIRECT}[warm_start]
         return _Opts(ws, rtol, max_iter, x0.data_ptr() if x0 is not None else None, net.h.value if net else None)
 
     def assign_mass(self, px, py, vals, out=None, warm_start="delta", rtol=1e-6, max_iter=200, x0=None,
@@ -312,11 +313,12 @@ class Context:
         self._check(self.lib.pm_mass_apply(self.h, _ptr(x), F, _ptr(out)))
         return out
 
-    def mass_solve(self, b, out=None, rtol=1e-6, max_iter=200, x0=None, info=True):
+    def mass_solve(self, b, out=None, rtol=1e-6, max_iter=200, x0=None, info=True, warm_start=None):
         b, x0 = self._f32(b), self._f32(x0)
         F = b.numel() // self.nodes
         out = out if out is not None else self._empty(F, self.nodes)
-        o = self._opts("user" if x0 is not None else "zero", rtol, max_iter, x0)
+        ws = warm_start or ("user" if x0 is not None else "zero")
+        o = self._opts(ws, rtol, max_iter, x0)
         inf = (_Info * F)() if info else None
         self._stream()
         self._check(self.lib.pm_mass_solve(self.h, _ptr(b), F, _ptr(out), ctypes.byref(o), inf))

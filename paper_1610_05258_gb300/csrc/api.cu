@@ -368,6 +368,11 @@ static pm_status mass_front(pm_ctx *c, const float *px, const float *py, ll np, 
             if (s2) return fail(c, s2, "network forward failed (n must be a multiple of 128 within the net's size)");
             launch_apply_correction(c->g, c->w, F, mesh_out, c->st);
         }
+    } else if (o.warm_start == PM_WS_DIRECT) {
+        // exact inverse of the uniform periodic mass matrix applied to b
+        Phase ph(c, PM_PH_SOLVE);
+        launch_rhs_to_float(c->g, c->w, F, c->w.b, c->st);
+        launch_mass_direct(c->g, c->w.b, F, mesh_out, c->w.r, c->st);
     } else if (o.warm_start == PM_WS_USER) {
         cudaMemcpyAsync(mesh_out, o.x0, sizeof(float) * F * c->g.ncell, cudaMemcpyDeviceToDevice, c->st);
     } else {
@@ -393,6 +398,7 @@ pm_status pm_assign_mass(pm_ctx *c, const float *px, const float *py, long long 
     if (F < 1 || !mesh_out) return fail(c, PM_EINVAL, "null output or no field");
     pm_solve_opts o;
     default_opts(opts, o);
+    if (o.warm_start < PM_WS_DELTA || o.warm_start > PM_WS_DIRECT) return fail(c, PM_EINVAL, "unknown warm start");
     if (o.warm_start == PM_WS_USER && !o.x0) return fail(c, PM_EINVAL, "PM_WS_USER without x0");
     if (o.warm_start == PM_WS_NET && (!o.net || !c->w.feat)) return fail(c, PM_EINVAL, "PM_WS_NET needs a network and a 2D mesh with n % 128 == 0");
     bool start = true;
@@ -504,6 +510,10 @@ pm_status pm_mass_solve(pm_ctx *c, const float *b, int F, float *x, const pm_sol
     if (o.warm_start == PM_WS_USER) {
         if (!o.x0) return fail(c, PM_EINVAL, "PM_WS_USER without x0");
         if (o.x0 != x) cudaMemcpyAsync(x, o.x0, sizeof(float) * F * c->g.ncell, cudaMemcpyDeviceToDevice, c->st);
+        start = true;
+    } else if (o.warm_start == PM_WS_DIRECT) {
+        if (b == x) return fail(c, PM_EINVAL, "PM_WS_DIRECT needs distinct b and x");
+        launch_mass_direct(c->g, b, F, x, c->w.r, c->st);
         start = true;
     }
     int e;

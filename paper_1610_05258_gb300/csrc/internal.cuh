@@ -175,6 +175,8 @@ void launch_volumes_1d(const Geo &g, Work &w, ll np, cudaStream_t st);
 void launch_delta(const Geo &g, Work &w, ll np, int F, float *mesh_out, cudaStream_t st);
 void launch_flip(const Geo &g, Work &w, ll np, int F, float *mesh_out, float *node_vol, cudaStream_t st);
 void rhs_prepare_device();
+// x = M^-1 b exactly (to ~1e-9) by separable circulant convolutions; tmp is scratch.
+void launch_mass_direct(const Geo &g, const float *b, int F, float *x, float *tmp, cudaStream_t st);
 void launch_g2p_integral(const Geo &g, Work &w, ll np, int F, const float *mesh, float *c, cudaStream_t st);
 void launch_div_vol(ll np, int F, const float *vol, float *c, cudaStream_t st);
 void launch_scale(ll m, float s, float *x, cudaStream_t st);

@@ -185,10 +185,15 @@ def test_mass_apply_and_solve(built, dim, n, F):
         kappa = 3.0 if dim == 1 else 9.0
         rate = (math.sqrt(kappa) - 1) / (math.sqrt(kappa) + 1)
         assert info[f].iters <= math.ceil(math.log(2 * math.sqrt(kappa) / 1e-6) / math.log(1 / rate)) + 3
+    # the exact inverse as start: the solution to rounding, no iteration needed
+    xd, dinfo = c.mass_solve(db, rtol=1e-6, warm_start="direct")
+    for f in range(F):
+        assert rel_l2(xd.cpu().numpy()[f], want[f]) <= TOL
+        assert dinfo[f].init_rel_resid <= 1e-6 and dinfo[f].iters == 0
 
 
 @pytest.mark.parametrize("name,mk", CASES_2D + CASES_1D)
-@pytest.mark.parametrize("warm", ["delta", "zero"])
+@pytest.mark.parametrize("warm", ["delta", "zero", "direct"])
 def test_assign_mass(built, name, mk, warm):
     inst = mk()
     c = ctx_for(inst)
