@@ -151,27 +151,33 @@ __device__ __forceinline__ int clip_by(PolyS<NB> P, int &m, float &R2, int sx, i
     }
     // |s| <= sqrt2 max(|sx|, |sy|) stands in for the norm in the margin
     const float hs = 0.5f * d2, ns = 1.41422f * fmaxf(fabsf(fsx), fabsf(fsy)), mr = 2.4e-7f * d2;
-    unsigned mask = 0;
-    float rkeep = 0.0f;
-    int ps = -2;
+    // float pass: certain inside -> mask, certain outside -> nothing, else
+    // undecided (exact pass below, rare)
+    unsigned mask = 0, undecided = 0;
     const int t = P.t;
+#pragma unroll 4
     for (int k = 0; k < m; ++k) {
         const float4 c = P.v[k][t];
         const float hk = c.x * fsx + c.y * fsy - hs;
         const float mg = c.z * ns + mr;
-        int v;
-        if (hk > mg) v = 1;
-        else if (hk < -mg) v = -1;
-        else {
+        const bool in = hk > mg, out = hk < -mg;  // both false also when hk or mg is NaN
+        mask |= (in ? 1u : 0u) << k;
+        undecided |= (!in && !out ? 1u : 0u) << k;
+    }
+    if (undecided) {
+        const int ps = perm[sidx];
+        if (pp == -2) pp = perm[p];
+        for (unsigned u = undecided; u; u &= u - 1) {
+            const int k = __ffs(u) - 1;
             const int4 A = P.q[k][t], Bq = P.q[k + 1 == m ? 0 : k + 1][t];
-            if (pp == -2) pp = perm[p];
-            if (ps == -2) ps = perm[sidx];
-            v = incircle_exact(A.x, A.y, Bq.x, Bq.y, sx, sy, pp, prio(A.z, perm), prio(Bq.z, perm), ps) ? 1 : -1;
+            if (incircle_exact(A.x, A.y, Bq.x, Bq.y, sx, sy, pp, prio(A.z, perm), prio(Bq.z, perm), ps))
+                mask |= 1u << k;
         }
-        if (v > 0) mask |= 1u << k;
-        else rkeep = fmaxf(rkeep, c.w);
     }
     if (mask == 0) return 0;
+    // largest radius bound among the vertices s keeps
+    float rkeep = 0.0f;
+    for (unsigned u = ~mask & ((1u << m) - 1u); u; u &= u - 1) rkeep = fmaxf(rkeep, P.v[__ffs(u) - 1][t].w);
     const unsigned full = (1u << m) - 1u;
     const int cnt = __popc(mask);
     const unsigned prevm = ((mask << 1) | (mask >> (m - 1))) & full;
