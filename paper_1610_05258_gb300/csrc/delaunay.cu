@@ -68,7 +68,7 @@ __device__ __forceinline__ int prio(int enc, const int *__restrict__ perm) {
 }
 
 #define DBLK 64     // threads per block of the main triangulation pass
-#define DCAP 10     // polygon capacity of the main pass (20 warps per SM)
+#define DCAP 9      // polygon capacity of the main pass (22 warps per SM)
 #define RBLK 32     // threads per block of the retry pass
 #define RCAP 24     // polygon capacity of the retry pass (= PM_MAXDEG)
 #define ST_OVERFLOW 0x40000000  // internal: the cell outgrew the main pass's capacity
@@ -399,7 +399,7 @@ __device__ __forceinline__ void add_counts(const WorkCount &wc, ull *__restrict_
 // Main pass: one thread per particle, polygon capacity DCAP. A particle whose
 // cell outgrows it is appended to the retry list (no output written).
 template <bool COUNT>
-__global__ void __launch_bounds__(DBLK) k_delaunay(Geo g, ll np, const uint2 *__restrict__ pos,
+__global__ void __launch_bounds__(DBLK, 11) k_delaunay(Geo g, ll np, const uint2 *__restrict__ pos,
                                                    const int *__restrict__ cell_start, const int *__restrict__ perm,
                                                    int *__restrict__ nbr, unsigned char *__restrict__ deg,
                                                    float *__restrict__ vol, float vol_scale, int *__restrict__ status,
