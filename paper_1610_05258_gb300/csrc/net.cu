@@ -83,51 +83,79 @@ __global__ void k_pack(const float *__restrict__ th, Packed P) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_first(const float *__restrict__ x, int B, int n, const float *__restrict__ w0,
                                                const float *__restrict__ b0, bf16 *__restrict__ out) {
-    __shared__ float sw[576 + 32];
-    for (int i = threadIdx.x; i < 608; i += blockDim.x) sw[i] = i < 576 ? w0[i] : b0[i - 576];
+    // weights transposed to [c][tap][co] so that 4 output channels' weights
+    // are one 16-byte shared-memory read
+    __shared__ __align__(16) float sw[18 * 32];
+    __shared__ float sb[32];
+    for (int i = threadIdx.x; i < 576; i += blockDim.x) {
+        const int co = i % 32, ct = i / 32;  // ct = c * 9 + tap
+        sw[i] = w0[co * 18 + ct];
+    }
+    if (threadIdx.x < 32) sb[threadIdx.x] = b0[threadIdx.x];
     __syncthreads();
     ll p = (ll)blockIdx.x * blockDim.x + threadIdx.x;
     const ll npx = (ll)n * n;
     if (p >= npx * B) return;
     const int img = (int)(p / npx), yx = (int)(p % npx), y = yx / n, xx = yx % n;
-    float in[2][9];
+    float s[32];
+#pragma unroll
+    for (int co = 0; co < 32; ++co) s[co] = sb[co];
+#pragma unroll
     for (int c = 0; c < 2; ++c)
+#pragma unroll
         for (int t = 0; t < 9; ++t) {
-            int yy = wrapn(y + t / 3 - 1, n), xs = wrapn(xx + t % 3 - 1, n);
-            in[c][t] = __bfloat162float(__float2bfloat16(x[((ll)img * 2 + c) * npx + (ll)yy * n + xs]));
+            const int yy = wrapn(y + t / 3 - 1, n), xs = wrapn(xx + t % 3 - 1, n);
+            const float in = __bfloat162float(__float2bfloat16(x[((ll)img * 2 + c) * npx + (ll)yy * n + xs]));
+            const float4 *w4 = (const float4 *)(sw + (c * 9 + t) * 32);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float4 w = w4[q];
+                s[4 * q] = fmaf(w.x, in, s[4 * q]);
+                s[4 * q + 1] = fmaf(w.y, in, s[4 * q + 1]);
+                s[4 * q + 2] = fmaf(w.z, in, s[4 * q + 2]);
+                s[4 * q + 3] = fmaf(w.w, in, s[4 * q + 3]);
+            }
         }
     alignas(16) bf16 o[32];
-    for (int co = 0; co < 32; ++co) {
-        float s = sw[576 + co];
-        for (int c = 0; c < 2; ++c)
-            for (int t = 0; t < 9; ++t) s = fmaf(sw[(co * 2 + c) * 9 + t], in[c][t], s);
-        o[co] = __float2bfloat16(fmaxf(s, 0.0f));
-    }
+#pragma unroll
+    for (int co = 0; co < 32; ++co) o[co] = __float2bfloat16(fmaxf(s[co], 0.0f));
     uint4 *dst = (uint4 *)(out + p * 32);
     const uint4 *src = (const uint4 *)o;
+#pragma unroll
     for (int q = 0; q < 4; ++q) dst[q] = src[q];
 }
 
+// 32 -> 1: one block per tile of LTX x LTY output pixels; the tile's input
+// with its one-pixel periodic halo is staged in shared memory (80-byte pixel
+// stride against bank conflicts), then every thread sums its 9 x 32 products
+// in the same order as before (tap, then channel).
+#define LTX 32
+#define LTY 8
 __global__ void __launch_bounds__(256) k_last(const bf16 *__restrict__ a, int B, int n, const float *__restrict__ w3,
                                               const float *__restrict__ b3, float *__restrict__ out) {
-    // weights transposed to [tap][channel] so that one tap's 32 weights are
-    // contiguous (broadcast reads)
     __shared__ float sw[9 * 32 + 1];
+    __shared__ uint4 tile[(LTX + 2) * (LTY + 2)][5];
     for (int i = threadIdx.x; i < 289; i += blockDim.x) sw[i] = i < 288 ? w3[(i % 32) * 9 + i / 32] : b3[0];
-    __syncthreads();
-    ll p = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    const int tiles_x = n / LTX, tiles_y = n / LTY;
+    const int img = blockIdx.x / (tiles_x * tiles_y), rem = blockIdx.x % (tiles_x * tiles_y);
+    const int x0 = (rem % tiles_x) * LTX, y0 = (rem / tiles_x) * LTY;
     const ll npx = (ll)n * n;
-    if (p >= npx * B) return;
-    const int img = (int)(p / npx), yx = (int)(p % npx), y = yx / n, xx = yx % n;
+    for (int i = threadIdx.x; i < (LTX + 2) * (LTY + 2) * 4; i += blockDim.x) {
+        const int px = i >> 2, q = i & 3;
+        const int ty = px / (LTX + 2), tx = px % (LTX + 2);
+        const int gy = wrapn(y0 + ty - 1, n), gx = wrapn(x0 + tx - 1, n);
+        tile[px][q] = __ldg((const uint4 *)(a + ((ll)img * npx + (ll)gy * n + gx) * 32) + q);
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % LTX, ty = threadIdx.x / LTX;
     float s = sw[288];
 #pragma unroll 1
     for (int t = 0; t < 9; ++t) {
-        int yy = wrapn(y + t / 3 - 1, n), xs = wrapn(xx + t % 3 - 1, n);
-        const uint4 *v = (const uint4 *)(a + ((ll)img * npx + (ll)yy * n + xs) * 32);
+        const int px = (ty + t / 3) * (LTX + 2) + tx + t % 3;
         const float *wt = sw + t * 32;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const uint4 u = __ldg(v + q);
+            const uint4 u = tile[px][q];
             const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -137,7 +165,7 @@ __global__ void __launch_bounds__(256) k_last(const bf16 *__restrict__ a, int B,
             }
         }
     }
-    out[p] = s;
+    out[(ll)img * npx + (ll)(y0 + ty) * n + x0 + tx] = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -470,7 +498,7 @@ void net_forward(pm_net *t, const float *x, int B, int n, float *out) {
     k_conv_mma<<<conv_grid(t, ntiles), 128, CONV_SMEM, t->st>>>(a1);
     ConvArgs a2{t->a2, t->a3, t->P.f2, t->P.b2, nullptr, 1, B, n, t->status};
     k_conv_mma<<<conv_grid(t, ntiles), 128, CONV_SMEM, t->st>>>(a2);
-    k_last<<<div_up(m, 256), 256, 0, t->st>>>(t->a3, B, n, t->P.w3, t->P.b3, out);
+    k_last<<<B * (n / LTX) * (n / LTY), LTX * LTY, 0, t->st>>>(t->a3, B, n, t->P.w3, t->P.b3, out);
     count_launches(4);
 }
 
