@@ -186,22 +186,43 @@ struct ConvArgs {
     int *status;
 };
 
-// Dynamic shared memory: A planes (24,960 B, padded to 25,600), B (18,432 B)
-// and 12 KB of slack, so that every address an operand descriptor can reach
-// stays inside this CTA's allocation.
-#define CONV_SMEM (25600 + 18432 + 12288)
+// One work item is a strip of CR output rows of CT pixels. Input rows live in
+// a ring of 4 slots in shared memory, each slot 4 planes of 8 channels x CPW
+// pixels (16 bytes per pixel); a row is staged once and serves the three
+// output rows that need it. Two accumulators of 32 TMEM columns alternate
+// between rows: while the tensor cores run the 18 MMAs of row y (issued by
+// one thread), the block stores row y-1 from the other accumulator and stages
+// row y+2 into the slot that row y-2 used (free once the MMAs of row y-1, the
+// last to read it, have signalled their mbarrier).
+#define CR 16                      // output rows per work item
+#define RING (4 * 4 * PLANE)       // 4 row slots of 4 planes (33,280 B)
+#define RING_PAD 33792             // ring rounded up to 1 KB
+// Dynamic shared memory: ring, B (18,432 B), and 4 KB of slack so that every
+// address an operand descriptor can reach stays inside this CTA's allocation.
+#define CONV_SMEM (RING_PAD + 18432 + 4096)
+
+__device__ __forceinline__ void stage_row(uint8_t *sA, const bf16 *in, ll img_off, int n, int gy, int x0, int slot,
+                                          int tid) {
+    for (int i = tid; i < CPW * 4; i += 128) {
+        const int px = i >> 2, c = i & 3;
+        const int gx = wrapn(x0 + px - 1, n);
+        const uint4 v = *(const uint4 *)(in + (img_off + (ll)gy * n + gx) * 32 + c * 8);
+        *(uint4 *)(sA + (slot * 4 + c) * PLANE + px * 16) = v;
+    }
+}
 
 __global__ void __launch_bounds__(128) k_conv_mma(ConvArgs a) {
     extern __shared__ __align__(1024) uint8_t conv_smem[];
     uint8_t *sA = conv_smem;
-    uint8_t *sB = conv_smem + 25600;
-    __shared__ __align__(8) uint64_t mbar;
+    uint8_t *sB = conv_smem + RING_PAD;
+    __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (warp == 0) tc::alloc(&tmem_base, 32);
+    if (warp == 0) tc::alloc(&tmem_base, 64);
     if (tid == 0) {
-        tc::mbar_init(&mbar, 1);
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
         abort_flag = 0;
     }
     // weights: B operand, 36 chunks of [32 rows][8 k] (16 bytes per row)
@@ -214,48 +235,28 @@ __global__ void __launch_bounds__(128) k_conv_mma(ConvArgs a) {
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = tmem_base;
-    const int n = a.n, tiles_row = n / CT;
-    const ll ntiles = (ll)a.B * n * tiles_row;
+    const int n = a.n, strips = n / CT, groups = n / CR;
+    const ll nitems = (ll)a.B * strips * groups;
     const uint32_t idesc = tc::idesc_bf16(128, 32);
     const uint32_t sa = tc::smem_u32(sA), sb = tc::smem_u32(sB);
-    uint32_t phase = 0;
-    for (ll tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int img = (int)(tile / ((ll)n * tiles_row));
-        const int rem = (int)(tile % ((ll)n * tiles_row));
-        const int y = rem / tiles_row, x0 = (rem % tiles_row) * CT;
-        const ll img_off = (ll)img * n * n;
-        // stage rows y-1, y, y+1 as planes [row][chunk][pixel] of 16 bytes
-        for (int i = tid; i < 3 * CPW * 4; i += blockDim.x) {
-            int r = i / (CPW * 4), rm = i % (CPW * 4), px = rm >> 2, c = rm & 3;
-            int gy = wrapn(y + r - 1, n), gx = wrapn(x0 + px - 1, n);
-            uint4 v = *(const uint4 *)(a.in + (img_off + (ll)gy * n + gx) * 32 + c * 8);
-            *(uint4 *)(sA + (r * 4 + c) * PLANE + px * 16) = v;
-        }
-        tc::fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            tc::fence_after();
-            for (int kb = 0; kb < 18; ++kb) {
-                const int t = kb >> 1, h = kb & 1, dy = t / 3, dx = t % 3;  // dy, dx in 0..2
-                const uint64_t ad = tc::desc(sa + (dy * 4 + 2 * h) * PLANE + dx * 16, PLANE, 128);
-                const uint64_t bd = tc::desc(sb + (2 * kb) * 512, 512, 128);
-                tc::mma_bf16(tmem, ad, bd, idesc, kb > 0 ? 1u : 0u);
-            }
-            tc::commit(&mbar);
-        }
-        __syncwarp();
-        if (!tc::mbar_wait(&mbar, phase, 1LL << 24)) {
+    uint32_t phase[2] = {0u, 0u};
+    bool pend[2] = {false, false};  // a commit on this mbarrier not yet waited for
+    float bias[32];
+    for (int c = 0; c < 32; ++c) bias[c] = a.bias ? a.bias[c] : 0.0f;
+
+    // epilogue of output row yo from accumulator buf: warp w owns TMEM lanes
+    // (pixels) 32w .. 32w+31
+    auto epilogue = [&](int buf, ll img_off, int yo, int x0) {
+        if (!tc::mbar_wait(&mbar[buf], phase[buf], 1LL << 24)) {
             atomicOr(a.status, ST_TIMEOUT);
             abort_flag = 1;
         }
-        phase ^= 1u;
+        phase[buf] ^= 1u;
+        pend[buf] = false;
         tc::fence_after();
-        __syncthreads();
-        if (abort_flag) break;
-        // epilogue: warp w owns TMEM lanes (pixels) 32w .. 32w+31
         float acc[32];
-        tc::ld32(tmem + ((uint32_t)(warp * 32) << 16), acc);
-        const ll p = img_off + (ll)y * n + x0 + warp * 32 + lane;
+        tc::ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * 32), acc);
+        const ll p = img_off + (ll)yo * n + x0 + warp * 32 + lane;
         alignas(16) bf16 o[32];
         if (a.mask) {
             alignas(16) bf16 mk[32];
@@ -264,18 +265,60 @@ __global__ void __launch_bounds__(128) k_conv_mma(ConvArgs a) {
             for (int c = 0; c < 32; ++c) o[c] = __float2bfloat16(__bfloat162float(mk[c]) > 0.0f ? acc[c] : 0.0f);
         } else {
             for (int c = 0; c < 32; ++c) {
-                float v = acc[c] + (a.bias ? a.bias[c] : 0.0f);
+                const float v = acc[c] + bias[c];
                 o[c] = __float2bfloat16(a.relu ? fmaxf(v, 0.0f) : v);
             }
         }
         uint4 *dst = (uint4 *)(a.out + p * 32);
         for (int q = 0; q < 4; ++q) dst[q] = ((const uint4 *)o)[q];
+    };
+
+    for (ll item = blockIdx.x; item < nitems && !abort_flag; item += gridDim.x) {
+        const int img = (int)(item / ((ll)strips * groups));
+        const int rem = (int)(item % ((ll)strips * groups));
+        const int y0 = (rem / strips) * CR, x0 = (rem % strips) * CT;
+        const ll img_off = (ll)img * n * n;
+        // prologue: rows y0-1, y0, y0+1
+        for (int r = -1; r <= 1; ++r) stage_row(sA, a.in, img_off, n, wrapn(y0 + r, n), x0, (y0 + r) & 3, tid);
+        tc::fence_proxy_async();
+        tc::fence_before();
+        __syncthreads();
+        for (int i = 0; i < CR; ++i) {
+            const int y = y0 + i, buf = i & 1;
+            if (tid == 0) {
+                tc::fence_after();
+                for (int kb = 0; kb < 18; ++kb) {
+                    const int t = kb >> 1, h = kb & 1, dy = t / 3, dx = t % 3;  // dy, dx in 0..2
+                    const int slot = (y + dy - 1) & 3;
+                    const uint64_t ad = tc::desc(sa + (slot * 4 + 2 * h) * PLANE + dx * 16, PLANE, 128);
+                    const uint64_t bd = tc::desc(sb + (2 * kb) * 512, 512, 128);
+                    tc::mma_bf16(tmem + (uint32_t)(buf * 32), ad, bd, idesc, kb > 0 ? 1u : 0u);
+                }
+                tc::commit(&mbar[buf]);
+            }
+            pend[buf] = true;
+            __syncwarp();
+            // row y-1 out of the other accumulator (its MMAs have finished,
+            // so the ring slot of row y-2 is free as well)
+            if (i > 0) epilogue(buf ^ 1, img_off, y - 1, x0);
+            if (i + 1 < CR) stage_row(sA, a.in, img_off, n, wrapn(y + 2, n), x0, (y + 2) & 3, tid);
+            tc::fence_proxy_async();
+            tc::fence_before();
+            __syncthreads();
+            if (abort_flag) break;
+        }
+        if (abort_flag) break;
+        epilogue((CR - 1) & 1, img_off, y0 + CR - 1, x0);
         tc::fence_before();
         __syncthreads();
     }
+    // after an abort, give MMAs still in flight a bounded time to finish
+    // before the accumulators are freed
+    for (int b = 0; b < 2; ++b)
+        if (pend[b]) tc::mbar_wait(&mbar[b], phase[b], 1LL << 20);
     tc::fence_after();
     __syncthreads();
-    if (warp == 0) tc::dealloc(tmem, 32);
+    if (warp == 0) tc::dealloc(tmem, 64);
 }
 
 // ---------------------------------------------------------------------------
@@ -493,7 +536,7 @@ void net_forward(pm_net *t, const float *x, int B, int n, float *out) {
     const ll m = (ll)B * n * n;
     net_pack(t);
     k_first<<<div_up(m, 256), 256, 0, t->st>>>(x, B, n, t->P.w0, t->P.b0, t->a1);
-    const ll ntiles = (ll)B * n * (n / CT);
+    const ll ntiles = (ll)B * (n / CR) * (n / CT);
     ConvArgs a1{t->a1, t->a2, t->P.f1, t->P.b1, nullptr, 1, B, n, t->status};
     k_conv_mma<<<conv_grid(t, ntiles), 128, CONV_SMEM, t->st>>>(a1);
     ConvArgs a2{t->a2, t->a3, t->P.f2, t->P.b2, nullptr, 1, B, n, t->status};
@@ -602,7 +645,7 @@ pm_status pm_net_train_step(pm_net *t, const float *x, const float *target, int 
     net_forward(t, x, B, n, t->out);
     k_loss<<<LOSS_BLOCKS, 256, 0, t->st>>>(t->out, target, m, t->gout, t->loss_part);
     k_last_back<<<div_up(m, 256), 256, 0, t->st>>>(t->gout, t->a3, B, n, t->P.w3, t->g2);  // g2 = dL/dz3 (pre-ReLU)
-    const ll ntiles = (ll)B * n * (n / CT);
+    const ll ntiles = (ll)B * (n / CR) * (n / CT);
     const size_t wsm = (128 * 32 + 3 * CPW * 32) * 4;
     // layer 2 (input a2, output gradient g2)
     k_wgrad_mid<<<WG_BLOCKS, 256, wsm, t->st>>>(t->g2, t->a2, B, n, t->part_mid);
