@@ -201,15 +201,22 @@ struct ConvArgs {
 // address an operand descriptor can reach stays inside this CTA's allocation.
 #define CONV_SMEM (RING_PAD + 18432 + 4096)
 
+// Stage one input row into a ring slot with 16-byte asynchronous copies
+// (cp.async): the copies proceed while the block stores the previous output
+// row; cp.async.wait_all before the next barrier makes them complete.
 __device__ __forceinline__ void stage_row(uint8_t *sA, const bf16 *in, ll img_off, int n, int gy, int x0, int slot,
                                           int tid) {
     for (int i = tid; i < CPW * 4; i += 128) {
         const int px = i >> 2, c = i & 3;
         const int gx = wrapn(x0 + px - 1, n);
-        const uint4 v = *(const uint4 *)(in + (img_off + (ll)gy * n + gx) * 32 + c * 8);
-        *(uint4 *)(sA + (slot * 4 + c) * PLANE + px * 16) = v;
+        const bf16 *src = in + (img_off + (ll)gy * n + gx) * 32 + c * 8;
+        const uint32_t dst = tc::smem_u32(sA + (slot * 4 + c) * PLANE + px * 16);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
 }
+
+__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __global__ void __launch_bounds__(128) k_conv_mma(ConvArgs a) {
     extern __shared__ __align__(1024) uint8_t conv_smem[];
@@ -246,7 +253,8 @@ __global__ void __launch_bounds__(128) k_conv_mma(ConvArgs a) {
 
     // epilogue of output row yo from accumulator buf: warp w owns TMEM lanes
     // (pixels) 32w .. 32w+31
-    auto epilogue = [&](int buf, ll img_off, int yo, int x0) {
+    // completion of the MMAs of accumulator buf (bounded wait)
+    auto mma_wait = [&](int buf) {
         if (!tc::mbar_wait(&mbar[buf], phase[buf], 1LL << 24)) {
             atomicOr(a.status, ST_TIMEOUT);
             abort_flag = 1;
@@ -254,6 +262,10 @@ __global__ void __launch_bounds__(128) k_conv_mma(ConvArgs a) {
         phase[buf] ^= 1u;
         pend[buf] = false;
         tc::fence_after();
+    };
+    // epilogue of output row yo from accumulator buf: warp w owns TMEM lanes
+    // (pixels) 32w .. 32w+31
+    auto epilogue = [&](int buf, ll img_off, int yo, int x0) {
         float acc[32];
         tc::ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * 32), acc);
         const ll p = img_off + (ll)yo * n + x0 + warp * 32 + lane;
@@ -280,6 +292,7 @@ __global__ void __launch_bounds__(128) k_conv_mma(ConvArgs a) {
         const ll img_off = (ll)img * n * n;
         // prologue: rows y0-1, y0, y0+1
         for (int r = -1; r <= 1; ++r) stage_row(sA, a.in, img_off, n, wrapn(y0 + r, n), x0, (y0 + r) & 3, tid);
+        stage_wait();
         tc::fence_proxy_async();
         tc::fence_before();
         __syncthreads();
@@ -298,16 +311,20 @@ __global__ void __launch_bounds__(128) k_conv_mma(ConvArgs a) {
             }
             pend[buf] = true;
             __syncwarp();
-            // row y-1 out of the other accumulator (its MMAs have finished,
-            // so the ring slot of row y-2 is free as well)
-            if (i > 0) epilogue(buf ^ 1, img_off, y - 1, x0);
+            // once the MMAs of row y-1 are done, the ring slot of row y-2 is
+            // free: start staging row y+2 there, then store row y-1 out of
+            // the other accumulator while the copies are in flight
+            if (i > 0) mma_wait(buf ^ 1);
             if (i + 1 < CR) stage_row(sA, a.in, img_off, n, wrapn(y + 2, n), x0, (y + 2) & 3, tid);
+            if (i > 0) epilogue(buf ^ 1, img_off, y - 1, x0);
+            stage_wait();
             tc::fence_proxy_async();
             tc::fence_before();
             __syncthreads();
             if (abort_flag) break;
         }
         if (abort_flag) break;
+        mma_wait((CR - 1) & 1);
         epilogue((CR - 1) & 1, img_off, y0 + CR - 1, x0);
         tc::fence_before();
         __syncthreads();
