@@ -258,10 +258,12 @@ struct Mom {
     }
 };
 
-// Liang-Barsky step for the constraint p t <= q on t in [t0, t1].
-__device__ __forceinline__ bool lb(float p, float q, float &t0, float &t1) {
+// Liang-Barsky step for the constraint p t <= q on t in [t0, t1], with
+// rinv = 1/p given (every p here is a component of a triangle edge, so each
+// piece needs only six reciprocals).
+__device__ __forceinline__ bool lb(float p, float q, float rinv, float &t0, float &t1) {
     if (p == 0.0f) return q >= 0.0f;
-    float r = q / p;
+    const float r = q * rinv;
     if (p < 0.0f) t0 = fmaxf(t0, r);
     else t1 = fminf(t1, r);
     return true;
@@ -273,13 +275,22 @@ __device__ __forceinline__ bool lb(float p, float q, float &t0, float &t1) {
 // edges inside the cell plus the part of the cell's edges inside T.
 __device__ __forceinline__ Mom tri_cell_moments(const float tx[3], const float ty[3], float ox, float oy) {
     Mom M;
+    float ex[3], ey[3], rx[3], ry[3];
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
         const int k1 = k == 2 ? 0 : k + 1;
-        const float px = tx[k], py = ty[k], dx = tx[k1] - px, dy = ty[k1] - py;
+        ex[k] = tx[k1] - tx[k];
+        ey[k] = ty[k1] - ty[k];
+        rx[k] = __frcp_rn(ex[k]);
+        ry[k] = __frcp_rn(ey[k]);
+    }
+    for (int k = 0; k < 3; ++k) {
+        const float px = tx[k], py = ty[k], dx = ex[k], dy = ey[k];
         // an edge lying exactly on a cell line is accounted for by the cell edge
         if ((dx == 0.0f && (px == 0.0f || px == 1.0f)) || (dy == 0.0f && (py == 0.0f || py == 1.0f))) continue;
         float t0 = 0.0f, t1 = 1.0f;
-        if (!lb(-dx, px, t0, t1) || !lb(dx, 1.0f - px, t0, t1) || !lb(-dy, py, t0, t1) || !lb(dy, 1.0f - py, t0, t1))
+        if (!lb(-dx, px, -rx[k], t0, t1) || !lb(dx, 1.0f - px, rx[k], t0, t1) || !lb(-dy, py, -ry[k], t0, t1) ||
+            !lb(dy, 1.0f - py, ry[k], t0, t1))
             continue;
         if (!(t0 < t1)) continue;
         M.seg(px + t0 * dx - ox, py + t0 * dy - oy, px + t1 * dx - ox, py + t1 * dy - oy);
@@ -290,11 +301,11 @@ __device__ __forceinline__ Mom tri_cell_moments(const float tx[3], const float t
         float t0 = 0.0f, t1 = 1.0f;
         bool ok = true;
         for (int k = 0; k < 3 && ok; ++k) {
-            const int k1 = k == 2 ? 0 : k + 1;
-            const float ex = tx[k1] - tx[k], ey = ty[k1] - ty[k];
-            const float q0 = ex * (uy - ty[k]) - ey * (ux - tx[k]);
-            const float dq = ex * (vy - uy) - ey * (vx - ux);
-            ok = lb(-dq, q0, t0, t1);
+            const float q0 = ex[k] * (uy - ty[k]) - ey[k] * (ux - tx[k]);
+            // cell edge directions (1,0), (0,1), (-1,0), (0,-1): dq = -ey, ex, ey, -ex
+            const float dq = e == 0 ? -ey[k] : (e == 1 ? ex[k] : (e == 2 ? ey[k] : -ex[k]));
+            const float rdq = e == 0 ? -ry[k] : (e == 1 ? rx[k] : (e == 2 ? ry[k] : -rx[k]));
+            ok = lb(-dq, q0, -rdq, t0, t1);
         }
         if (!ok || !(t0 < t1)) continue;
         M.seg(ux + t0 * (vx - ux) - ox, uy + t0 * (vy - uy) - oy, ux + t1 * (vx - ux) - ox, uy + t1 * (vy - uy) - oy);
@@ -368,6 +379,7 @@ __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__rest
     unsigned(*tab)[256] = (unsigned(*)[256])(rhs_smem + 2 * FF * RWIN * RWIN);  // (star slot << 16) | pieces so far
     __shared__ int rowpre[RTS + 1];
     __shared__ int rowbeg[RTS];
+    __shared__ int next_chunk;  // next 32-particle chunk of the tile (warps take chunks as they finish)
     const int n = g.n;
     const int tx0 = (blockIdx.x % tiles_x) * RTS, ty0 = (blockIdx.x / tiles_x) * RTS;
     const int wx0 = tx0 - RHALO, wy0 = ty0 - RHALO;
@@ -389,6 +401,7 @@ __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__rest
             }
         }
         rowpre[RTS] = tot;
+        next_chunk = 0;
     }
     __syncthreads();
     const float hd = g.h * g.h;
@@ -398,7 +411,13 @@ __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__rest
     const int total = rowpre[RTS];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int tcol = threadIdx.x;
-    for (int base = wid * 32; base < total; base += nw * 32) {
+    (void)wid;
+    (void)nw;
+    for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&next_chunk, 32);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= total) break;
         // this lane's particle, its owned triangles and its number of pieces
         const int k = base + lane;
         int p = -1, cnt = 0;
