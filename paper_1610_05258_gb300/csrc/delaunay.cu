@@ -153,7 +153,11 @@ __device__ __forceinline__ int clip_by(PolyS<NB> P, int &m, float &R2, int sx, i
     const float hs = 0.5f * d2, ns = 1.41422f * fmaxf(fabsf(fsx), fabsf(fsy)), mr = 2.4e-7f * d2;
     // float pass: certain inside -> mask, certain outside -> nothing, else
     // undecided (exact pass below, rare)
+    // rkeep: the largest radius bound among the vertices not certainly
+    // removed (an upper bound of the kept ones: undecided vertices that the
+    // exact pass removes only make it larger, which is safe)
     unsigned mask = 0, undecided = 0;
+    float rkeep = 0.0f;
     const int t = P.t;
 #pragma unroll 4
     for (int k = 0; k < m; ++k) {
@@ -163,6 +167,7 @@ __device__ __forceinline__ int clip_by(PolyS<NB> P, int &m, float &R2, int sx, i
         const bool in = hk > mg, out = hk < -mg;  // both false also when hk or mg is NaN
         mask |= (in ? 1u : 0u) << k;
         undecided |= (!in && !out ? 1u : 0u) << k;
+        rkeep = in ? rkeep : fmaxf(rkeep, c.w);
     }
     if (undecided) {
         const int ps = perm[sidx];
@@ -175,9 +180,6 @@ __device__ __forceinline__ int clip_by(PolyS<NB> P, int &m, float &R2, int sx, i
         }
     }
     if (mask == 0) return 0;
-    // largest radius bound among the vertices s keeps
-    float rkeep = 0.0f;
-    for (unsigned u = ~mask & ((1u << m) - 1u); u; u &= u - 1) rkeep = fmaxf(rkeep, P.v[__ffs(u) - 1][t].w);
     const unsigned full = (1u << m) - 1u;
     const int cnt = __popc(mask);
     const unsigned prevm = ((mask << 1) | (mask >> (m - 1))) & full;
