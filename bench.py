@@ -398,7 +398,7 @@ def run_batched(args, pm, torch, dist, local):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"batched: {len(insts)} instances, sides 64..512, 1..8 particles/cell, F={F}, "
                                f"{N} particles, {sum(i.n * i.n for i in insts)} nodes; one mass assignment of every "
-                               f"instance per step (CUDA graph replay)",
+                               f"instance per step to 1e-6 (direct start, CUDA graph replay)",
                    "l2": "flushed before every timed step (512 MB write)", "parallelism": f"replicas x{args.world}",
                    "autotuned_streams": S},
         "solve": {"max_iters": max(x.iters for x in flat), "max_rel_resid": max(x.rel_resid for x in flat),

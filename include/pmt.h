@@ -283,7 +283,9 @@ void pm_batch_destroy(pm_batch *b);
 const char *pm_batch_last_error(const pm_batch *b);
 /* The chosen stream count and the step time measured when choosing it. */
 pm_status pm_batch_tuning(const pm_batch *b, int *streams, double *step_ms);
-/* Mass assignment (as pm_assign_mass, delta warm start) of every instance.
+/* Mass assignment (as pm_assign_mass with the PM_WS_DIRECT start: the exact
+ * inverse of each instance's mass matrix, then conjugate gradients confirm
+ * the residual) of every instance.
  * px, py, vals, mesh_out are HOST arrays of ninst DEVICE pointers (instance
  * k: px[k][np[k]], vals[k] [F][np[k]], mesh_out[k] [F][n[k]^2]); np is a host
  * array. One step is captured into a CUDA graph (particle phases of all

@@ -806,8 +806,10 @@ pm_status pm_batch_assign_mass(pm_batch *b, const float *const *px, const float 
         if (s) return bfail(b, s, "instance " + std::to_string(k) + ": " + b->ctx[k]->err);
         if (!mesh_out[k]) return bfail(b, PM_EINVAL, "null output");
     }
+    // start from the exact inverse of each instance's mass matrix: the
+    // solves, which run one after another, then only confirm the residual
     pm_solve_opts o;
-    o.warm_start = PM_WS_DELTA;
+    o.warm_start = PM_WS_DIRECT;
     o.rtol = rtol > 0.0 ? rtol : 1e-6;
     o.max_iter = max_iter > 0 ? max_iter : 200;
     o.x0 = nullptr;

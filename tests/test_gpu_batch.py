@@ -24,7 +24,7 @@ def test_batch_matches_single_and_oracle():
     first = [o.clone() for o in outs]
     for k, inst in enumerate(insts):
         c = Context(2, inst.n, inst.L, inst.np, 2)
-        single, sinfo = c.assign_mass(*dev[k])
+        single, sinfo = c.assign_mass(*dev[k], warm_start="direct")
         assert torch.equal(single, outs[k]), k
         want = oracle.assign_mass(2, inst.n, inst.L, inst.px, inst.py, inst.vals)
         for f in range(2):
