@@ -203,8 +203,8 @@ pm_status pm_ctx_create(pm_ctx **out, int dim, int n, double L, long long max_pa
               alloc(c, &w.red, 6LL * PM_MAXF * 4096) && alloc(c, &w.scal, 16LL * PM_MAXF) &&
               alloc(c, &w.bar, 2) && alloc(c, &w.status, 1) && alloc(c, &w.empty, 1) && alloc(c, &w.ntri, 1) &&
               alloc(c, &w.wsum, 8) && alloc(c, &w.nretry, 1) && alloc(c, &w.meshmax, PM_MAXF) &&
-              alloc(c, &w.pc, F * np) && alloc(c, &w.px, F * np) && alloc(c, &w.pq, F * np) &&
-              alloc(c, &w.prp, 2 * F * np);
+              alloc(c, &w.pc, F * np) && alloc(c, &w.px, pcg_width((int)F) * np) &&
+              alloc(c, &w.pq, pcg_width((int)F) * np) && alloc(c, &w.prp, 2LL * pcg_width((int)F) * np);
     w.cfix = (ll *)w.prp;
     if (ok && dim == 2) ok = alloc(c, &w.nbr, (ll)PM_MAXDEG * np) && alloc(c, &w.pcoef, (ll)PM_MAXDEG * np);
     if (ok && dim == 2 && n % 128 == 0)
@@ -451,13 +451,9 @@ pm_status pm_interpolate_mass(pm_ctx *c, const float *mesh, int F, const float *
     int e;
     {
         Phase ph(c, PM_PH_SOLVE);
-        e = launch_pcg(c->g, c->w, np, F, c->w.pc, c->w.px, o.rtol, o.max_iter, c->st);
+        e = launch_pcg(c->g, c->w, np, F, c->w.pc, out, o.rtol, o.max_iter, c->st);
     }
     if (e) return cuda_fail(c, (cudaError_t)e, "pm_interpolate_mass solve launch");
-    {
-        Phase ph(c, PM_PH_G2P);
-        unsort_fields(c, np, F, c->w.px, out);
-    }
     if ((s = check_launch(c, "pm_interpolate_mass"))) return s;
     if (info) return fill_info(c, F, info);
     return PM_OK;

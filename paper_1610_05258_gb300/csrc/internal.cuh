@@ -76,8 +76,9 @@ struct Work {
     int *nretry;           // particles handed to the triangulation's retry pass
     // mesh -> particle projections (particle-sized, sorted order)
     unsigned *meshmax;     // [PM_MAXF] max |Ab| bit patterns
-    float *pc, *px, *pq;   // [F][np] right-hand side c, solution, M_p p
-    float *prp;            // [2][F][np] residual and search direction (r, then p)
+    float *pc;             // [F][np] right-hand side c
+    float *px, *pq;        // [np][W] solution, M_p p (W = pcg_width(F_max), fields interleaved)
+    float *prp;            // [2][np][W] residual and search direction (r, then p)
     ll *cfix;              // = (ll *)prp: fixed-point c before conversion
     float *pcoef;          // [PM_MAXDEG][np] particle mass matrix rows (2D)
 };
@@ -180,9 +181,12 @@ void launch_mass_direct(const Geo &g, const float *b, int F, float *x, float *tm
 void launch_g2p_integral(const Geo &g, Work &w, ll np, int F, const float *mesh, float *c, cudaStream_t st);
 void launch_div_vol(ll np, int F, const float *vol, float *c, cudaStream_t st);
 void launch_scale(ll m, float s, float *x, cudaStream_t st);
-// Full-mass mesh -> particle solve M_p x = c (sorted order); 0 or a CUDA error.
-int launch_pcg(const Geo &g, Work &w, ll np, int F, const float *c, float *x, double rtol, int max_iter,
+// Full-mass mesh -> particle solve M_p x = c (c sorted, [F][np]); writes the
+// solution to out in caller order [F][np]. 0 or a CUDA error.
+int launch_pcg(const Geo &g, Work &w, ll np, int F, const float *c, float *out, double rtol, int max_iter,
                cudaStream_t st);
+// Interleaved width of the particle solve's vectors for F fields (2, 4 or PM_MAXF).
+int pcg_width(int F);
 void launch_rhs(const Geo &g, Work &w, ll np, int F, cudaStream_t st);
 void launch_rhs_to_float(const Geo &g, Work &w, int F, float *b_out, cudaStream_t st);
 void launch_mass_apply(const Geo &g, const float *x, int F, float *y, cudaStream_t st);

@@ -705,23 +705,26 @@ __global__ void k_mass_apply(Geo g, const float *__restrict__ x, int F, float *_
 // ---------------------------------------------------------------------------
 // Full-mass mesh -> particle projection (Eq. proj2): solve M_p x = c with
 // (M_p)_{mu nu} = int psi_mu psi_nu, applied matrix-free from the Delaunay
-// stars (2D: each triangle T of p's star contributes |T|/12 (2 x_p + x_a +
-// x_b)) or from the sorted order (1D: gaps g give g/6 (x_left + 2 x_p) and
-// g/6 (2 x_p + x_right)). Conjugate gradients with the Jacobi preconditioner
-// (diagonal v/2 in 2D, 2v/3 in 1D), from the lumped start c/v, in one
-// persistent cooperative kernel with the same fixed-order FP64 reductions as
-// the mesh solve.
+// stars (2D: diagonal v/2 and, for neighbour q_k, the coefficient
+// (|T_k| + |T_k+1|)/12 of the two star triangles sharing the edge; 1D: gaps g
+// give g/6 (x_left + 2 x_p) and g/6 (2 x_p + x_right)). Conjugate gradients
+// with the Jacobi preconditioner (diagonal v/2 in 2D, 2v/3 in 1D), from the
+// lumped start c/v, in one persistent cooperative kernel with the same
+// fixed-order FP64 reductions as the mesh solve. The vectors are interleaved
+// per particle, [np][FF] with FF = 2, 4 or 8 >= F, so that one row of M_p
+// gathers each neighbour's fields with one wide load; fields past F stay 0,
+// and a converged field is frozen by zero step lengths.
 // ---------------------------------------------------------------------------
 struct PCG {
     Geo g;
     int F;
     ll np;
-    const float *c, *vol;
+    const float *c, *vol;  // c: [F][np] (fields apart), vol: [np]
     const uint2 *pos;
     const int *nbr;
     const unsigned char *deg;
     const float *coef;  // [PM_MAXDEG][np] off-diagonal row coefficients (2D)
-    float *x, *r, *p, *q;
+    float *x, *r, *p, *q;  // [np][FF]
     double *red, *scal;
     unsigned *bar;
     int *status;
@@ -730,12 +733,45 @@ struct PCG {
     float unit;  // L / 2^32: torus units -> length
 };
 
-// The same row applied to every active field at once (one pass over the row):
-// out[f] = (M_p x_f)_s for the fields with act[f].
+template <int FF>
+struct VF {
+    float v[FF];
+};
+
+template <int FF>
+__device__ __forceinline__ VF<FF> ldv(const float *p) {
+    VF<FF> o;
+    if (FF == 2) {
+        const float2 t = *(const float2 *)p;
+        o.v[0] = t.x;
+        o.v[1] = t.y;
+    } else {
+#pragma unroll
+        for (int i = 0; i < FF / 4; ++i) {
+            const float4 t = ((const float4 *)p)[i];
+            o.v[4 * i] = t.x;
+            o.v[4 * i + 1] = t.y;
+            o.v[4 * i + 2] = t.z;
+            o.v[4 * i + 3] = t.w;
+        }
+    }
+    return o;
+}
+
+template <int FF>
+__device__ __forceinline__ void stv(float *p, const VF<FF> &o) {
+    if (FF == 2) {
+        *(float2 *)p = make_float2(o.v[0], o.v[1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < FF / 4; ++i)
+            ((float4 *)p)[i] = make_float4(o.v[4 * i], o.v[4 * i + 1], o.v[4 * i + 2], o.v[4 * i + 3]);
+    }
+}
+
+// Row s of M_p applied to the interleaved vector xb (all FF fields).
 template <int DIM, int FF>
-__device__ __forceinline__ void pmass_apply_all(const PCG &a, const float *__restrict__ xb, ll s, const bool *act,
-                                                float *out) {
-    const int F = a.F;
+__device__ __forceinline__ VF<FF> pmass_row(const PCG &a, const float *__restrict__ xb, ll s) {
     const ll np = a.np;
     KSum acc[FF];
     if (DIM == 1) {
@@ -743,33 +779,32 @@ __device__ __forceinline__ void pmass_apply_all(const PCG &a, const float *__res
         const ll sl = s == 0 ? np - 1 : s - 1, sr = s + 1 == np ? 0 : s + 1;
         const float u = a.unit * (1.0f / 6.0f);
         const float gl = (float)(uint32_t)(X - a.pos[sl].x) * u, gr = (float)(uint32_t)(a.pos[sr].x - X) * u;
+        const VF<FF> xl = ldv<FF>(xb + sl * FF), xs = ldv<FF>(xb + s * FF), xr = ldv<FF>(xb + sr * FF);
 #pragma unroll
         for (int f = 0; f < FF; ++f) {
-            if (f >= F || !act[f]) continue;
-            const float *xf = xb + (ll)f * np;
-            acc[f].add(gl * xf[sl]);
-            acc[f].add(2.0f * (gl + gr) * xf[s]);
-            acc[f].add(gr * xf[sr]);
-            out[f] = acc[f].get();
+            acc[f].add(gl * xl.v[f]);
+            acc[f].add(2.0f * (gl + gr) * xs.v[f]);
+            acc[f].add(gr * xr.v[f]);
         }
-        return;
+    } else {
+        const int m = a.deg[s];
+        const float d = 0.5f * a.vol[s];
+        const VF<FF> xs = ldv<FF>(xb + s * FF);
+#pragma unroll
+        for (int f = 0; f < FF; ++f) acc[f].add(d * xs.v[f]);
+        for (int k = 0; k < m; ++k) {
+            const int id = a.nbr[(ll)k * np + s] & 0x0fffffff;
+            PM_CHK(id >= 0 && id < np, 402, break)
+            const float w = a.coef[(ll)k * np + s];
+            const VF<FF> xn = ldv<FF>(xb + (ll)id * FF);
+#pragma unroll
+            for (int f = 0; f < FF; ++f) acc[f].add(w * xn.v[f]);
+        }
     }
-    const int m = a.deg[s];
-    const float d = 0.5f * a.vol[s];
+    VF<FF> o;
 #pragma unroll
-    for (int f = 0; f < FF; ++f)
-        if (f < F && act[f]) acc[f].add(d * xb[(ll)f * np + s]);
-    for (int k = 0; k < m; ++k) {
-        const int id = a.nbr[(ll)k * np + s] & 0x0fffffff;
-        PM_CHK(id >= 0 && id < np, 403, break)
-        const float w = a.coef[(ll)k * np + s];
-#pragma unroll
-        for (int f = 0; f < FF; ++f)
-            if (f < F && act[f]) acc[f].add(w * xb[(ll)f * np + id]);
-    }
-#pragma unroll
-    for (int f = 0; f < FF; ++f)
-        if (f < F && act[f]) out[f] = acc[f].get();
+    for (int f = 0; f < FF; ++f) o.v[f] = acc[f].get();
+    return o;
 }
 
 // Coefficients of the particle mass matrix rows from the stars: slot k of
@@ -809,23 +844,33 @@ __global__ void __launch_bounds__(256) k_pcg(PCG a) {
     const ll np = a.np;
     const ll tid = (ll)blockIdx.x * blockDim.x + threadIdx.x, nth = (ll)gridDim.x * blockDim.x;
     const float dfac = DIM == 2 ? 0.5f : 2.0f / 3.0f;  // Jacobi diagonal = dfac v
-    double v[PM_MAXF], w[PM_MAXF], cc[PM_MAXF], rz[PM_MAXF];
+    double v[PM_MAXF], w[PM_MAXF], cc[PM_MAXF], rz[PM_MAXF], ab[PM_MAXF];
     bool act[PM_MAXF];
     int it_f[PM_MAXF];
+    for (int f = 0; f < PM_MAXF; ++f) v[f] = w[f] = ab[f] = 0.0;
     // --- lumped start x = c / v; norms and sums of c
-    double ab[PM_MAXF];
-    for (int f = 0; f < F; ++f) {
-        Dot2 s2, s1, sa;
+    {
+        Dot2 s2[FF], s1[FF], sa[FF];
         for (ll s = tid; s < np; s += nth) {
-            const float cv = a.c[(ll)f * np + s], vv = a.vol[s];
-            a.x[(ll)f * np + s] = vv > 0.0f ? cv / vv : 0.0f;
-            s2.fma_acc(cv, cv);
-            s1.add(cv);
-            sa.add(fabsf(cv));
+            const float vv = a.vol[s];
+            VF<FF> cv, xv;
+#pragma unroll
+            for (int f = 0; f < FF; ++f) {
+                cv.v[f] = f < F ? a.c[(ll)f * np + s] : 0.0f;
+                xv.v[f] = vv > 0.0f ? cv.v[f] / vv : 0.0f;
+                s2[f].fma_acc(cv.v[f], cv.v[f]);
+                s1[f].add(cv.v[f]);
+                sa[f].add(fabsf(cv.v[f]));
+            }
+            stv<FF>(a.x + s * FF, xv);
         }
-        v[f] = (double)s2.hi + (double)s2.lo;
-        w[f] = (double)s1.hi + (double)s1.lo;
-        ab[f] = (double)sa.hi + (double)sa.lo;
+#pragma unroll
+        for (int f = 0; f < FF; ++f)
+            if (f < F) {
+                v[f] = (double)s2[f].hi + (double)s2[f].lo;
+                w[f] = (double)s1[f].hi + (double)s1[f].lo;
+                ab[f] = (double)sa[f].hi + (double)sa[f].lo;
+            }
     }
     block_partial(v, F, a.red, 0);
     block_partial(w, F, a.red, 1);
@@ -836,31 +881,28 @@ __global__ void __launch_bounds__(256) k_pcg(PCG a) {
     grid_total(a.red, F, 1, sumc);
     grid_total(a.red, F, 2, sumabs);
     // --- r = c - M x, z = r / d, p = z; (r, r), (r, z)
-    bool all[PM_MAXF];
-    for (int f = 0; f < PM_MAXF; ++f) all[f] = f < F;
     {
         Dot2 s2[FF], sz[FF];
-        float mx[FF];
         for (ll s = tid; s < np; s += nth) {
-            pmass_apply_all<DIM, FF>(a, a.x, s, all, mx);
+            const VF<FF> mx = pmass_row<DIM, FF>(a, a.x, s);
             const float d = dfac * a.vol[s];
+            VF<FF> rv, zv;
 #pragma unroll
             for (int f = 0; f < FF; ++f) {
-                if (f >= F) break;
-                const float rv = a.c[(ll)f * np + s] - mx[f];
-                const float zv = d > 0.0f ? rv / d : 0.0f;
-                a.r[(ll)f * np + s] = rv;
-                a.p[(ll)f * np + s] = zv;
-                s2[f].fma_acc(rv, rv);
-                sz[f].fma_acc(rv, zv);
+                rv.v[f] = (f < F ? a.c[(ll)f * np + s] : 0.0f) - mx.v[f];
+                zv.v[f] = d > 0.0f ? rv.v[f] / d : 0.0f;
+                s2[f].fma_acc(rv.v[f], rv.v[f]);
+                sz[f].fma_acc(rv.v[f], zv.v[f]);
             }
+            stv<FF>(a.r + s * FF, rv);
+            stv<FF>(a.p + s * FF, zv);
         }
 #pragma unroll
-        for (int f = 0; f < FF; ++f) {
-            if (f >= F) break;
-            v[f] = (double)s2[f].hi + (double)s2[f].lo;
-            w[f] = (double)sz[f].hi + (double)sz[f].lo;
-        }
+        for (int f = 0; f < FF; ++f)
+            if (f < F) {
+                v[f] = (double)s2[f].hi + (double)s2[f].lo;
+                w[f] = (double)sz[f].hi + (double)sz[f].lo;
+            }
     }
     block_partial(v, F, a.red, 0);
     block_partial(w, F, a.red, 1);
@@ -879,94 +921,99 @@ __global__ void __launch_bounds__(256) k_pcg(PCG a) {
         bool any = false;
         for (int f = 0; f < F; ++f) any |= act[f];
         if (!any) break;
-        // q = M p, (p, q) for the active fields in one pass over the rows
+        // q = M p, (p, q)
         {
             Dot2 sq[FF];
-            float mq[FF];
             for (ll i = tid; i < np; i += nth) {
-                pmass_apply_all<DIM, FF>(a, a.p, i, act, mq);
+                const VF<FF> qv = pmass_row<DIM, FF>(a, a.p, i);
+                const VF<FF> pv = ldv<FF>(a.p + i * FF);
+                stv<FF>(a.q + i * FF, qv);
 #pragma unroll
-                for (int f = 0; f < FF; ++f) {
-                    if (f >= F || !act[f]) continue;
-                    a.q[(ll)f * np + i] = mq[f];
-                    sq[f].fma_acc(a.p[(ll)f * np + i], mq[f]);
-                }
+                for (int f = 0; f < FF; ++f) sq[f].fma_acc(pv.v[f], qv.v[f]);
             }
 #pragma unroll
             for (int f = 0; f < FF; ++f)
-                if (f < F) v[f] = act[f] ? (double)sq[f].hi + (double)sq[f].lo : 0.0;
+                if (f < F) v[f] = (double)sq[f].hi + (double)sq[f].lo;
         }
         block_partial(v, F, a.red, 0);
         if (!grid_sync(a.bar, a.status)) return;
         grid_total(a.red, F, 0, w);
-        // x += alpha p, r -= alpha q; (r, r), (r, z) with z = r / d
-        double rz_new[PM_MAXF];
-        for (int f = 0; f < F; ++f) {
-            v[f] = 0.0;
-            rz_new[f] = 0.0;
-            if (!act[f]) continue;
-            const float al = (float)(rz[f] / w[f]);
-            Dot2 s2, sz;
+        // x += alpha p, r -= alpha q; (r, r), (r, z) with z = r / d. A
+        // converged field gets alpha = 0 (frozen).
+        float al[FF];
+#pragma unroll
+        for (int f = 0; f < FF; ++f) al[f] = (f < F && act[f]) ? (float)(rz[f] / w[f]) : 0.0f;
+        {
+            Dot2 s2[FF], sz[FF];
             for (ll i = tid; i < np; i += nth) {
-                const ll o = (ll)f * np + i;
-                a.x[o] = fmaf(al, a.p[o], a.x[o]);
-                const float rv = fmaf(-al, a.q[o], a.r[o]);
-                a.r[o] = rv;
+                VF<FF> xv = ldv<FF>(a.x + i * FF), pv = ldv<FF>(a.p + i * FF);
+                VF<FF> qv = ldv<FF>(a.q + i * FF), rv = ldv<FF>(a.r + i * FF);
                 const float d = dfac * a.vol[i];
-                const float zv = d > 0.0f ? rv / d : 0.0f;
-                s2.fma_acc(rv, rv);
-                sz.fma_acc(rv, zv);
+#pragma unroll
+                for (int f = 0; f < FF; ++f) {
+                    xv.v[f] = fmaf(al[f], pv.v[f], xv.v[f]);
+                    rv.v[f] = fmaf(-al[f], qv.v[f], rv.v[f]);
+                    const float zv = d > 0.0f ? rv.v[f] / d : 0.0f;
+                    s2[f].fma_acc(rv.v[f], rv.v[f]);
+                    sz[f].fma_acc(rv.v[f], zv);
+                }
+                stv<FF>(a.x + i * FF, xv);
+                stv<FF>(a.r + i * FF, rv);
             }
-            v[f] = (double)s2.hi + (double)s2.lo;
-            rz_new[f] = (double)sz.hi + (double)sz.lo;
+#pragma unroll
+            for (int f = 0; f < FF; ++f)
+                if (f < F) {
+                    v[f] = (double)s2[f].hi + (double)s2[f].lo;
+                    w[f] = (double)sz[f].hi + (double)sz[f].lo;
+                }
         }
         block_partial(v, F, a.red, 0);
-        block_partial(rz_new, F, a.red, 1);
+        block_partial(w, F, a.red, 1);
         if (!grid_sync(a.bar, a.status)) return;
         grid_total(a.red, F, 0, rr);
+        double rz_new[PM_MAXF];
         grid_total(a.red, F, 1, rz_new);
-        double beta[PM_MAXF];
+        float be[FF];
+#pragma unroll
+        for (int f = 0; f < FF; ++f) be[f] = 0.0f;
         for (int f = 0; f < F; ++f) {
-            beta[f] = 0.0;
             if (!act[f]) continue;
-            beta[f] = rz_new[f] / rz[f];
+            be[f] = (float)(rz_new[f] / rz[f]);
             rz[f] = rz_new[f];
             ++it_f[f];
             if (rr[f] <= tol2 * cc[f]) act[f] = false;
         }
         // p = z + beta p
-        for (int f = 0; f < F; ++f) {
-            if (!act[f]) continue;
-            const float be = (float)beta[f];
-            for (ll i = tid; i < np; i += nth) {
-                const ll o = (ll)f * np + i;
-                const float d = dfac * a.vol[i];
-                const float zv = d > 0.0f ? a.r[o] / d : 0.0f;
-                a.p[o] = fmaf(be, a.p[o], zv);
-            }
+        for (ll i = tid; i < np; i += nth) {
+            VF<FF> pv = ldv<FF>(a.p + i * FF);
+            const VF<FF> rv = ldv<FF>(a.r + i * FF);
+            const float d = dfac * a.vol[i];
+#pragma unroll
+            for (int f = 0; f < FF; ++f) pv.v[f] = fmaf(be[f], pv.v[f], d > 0.0f ? rv.v[f] / d : 0.0f);
+            stv<FF>(a.p + i * FF, pv);
         }
         if (!grid_sync(a.bar, a.status)) return;
     }
     // --- report: true residual, sum v x (= sum c for the exact solution)
     {
         Dot2 s2[FF], sv[FF];
-        float mx[FF];
         for (ll s = tid; s < np; s += nth) {
-            pmass_apply_all<DIM, FF>(a, a.x, s, all, mx);
+            const VF<FF> mx = pmass_row<DIM, FF>(a, a.x, s);
+            const VF<FF> xv = ldv<FF>(a.x + s * FF);
+            const float vv = a.vol[s];
 #pragma unroll
             for (int f = 0; f < FF; ++f) {
-                if (f >= F) break;
-                const float rv = a.c[(ll)f * np + s] - mx[f];
+                const float rv = (f < F ? a.c[(ll)f * np + s] : 0.0f) - mx.v[f];
                 s2[f].fma_acc(rv, rv);
-                sv[f].fma_acc(a.vol[s], a.x[(ll)f * np + s]);
+                sv[f].fma_acc(vv, xv.v[f]);
             }
         }
 #pragma unroll
-        for (int f = 0; f < FF; ++f) {
-            if (f >= F) break;
-            v[f] = (double)s2[f].hi + (double)s2[f].lo;
-            w[f] = (double)sv[f].hi + (double)sv[f].lo;
-        }
+        for (int f = 0; f < FF; ++f)
+            if (f < F) {
+                v[f] = (double)s2[f].hi + (double)s2[f].lo;
+                w[f] = (double)sv[f].hi + (double)sv[f].lo;
+            }
     }
     block_partial(v, F, a.red, 0);
     block_partial(w, F, a.red, 1);
@@ -980,13 +1027,22 @@ __global__ void __launch_bounds__(256) k_pcg(PCG a) {
             const double res = cc[f] > 0.0 ? sqrt(tr[f] / cc[f]) : 0.0;
             a.scal[f * 16 + S_ITERS] = it_f[f];
             a.scal[f * 16 + S_RESID] = res;
-            a.scal[f * 16 + S_SUMMESH] = sumc[f];  // int Ab = sum_mu c_mu
-            a.scal[f * 16 + S_SUMPART] = svx[f];   // sum_mu v_mu Abb_mu
-            a.scal[f * 16 + S_SUMABS] = sumabs[f]; // sum_mu |c_mu|: scale of the conservation error
+            a.scal[f * 16 + S_SUMMESH] = sumc[f];   // int Ab = sum_mu c_mu
+            a.scal[f * 16 + S_SUMPART] = svx[f];    // sum_mu v_mu Abb_mu
+            a.scal[f * 16 + S_SUMABS] = sumabs[f];  // sum_mu |c_mu|: scale of the conservation error
             if (res > a.rtol) bad = true;
         }
         if (bad) atomicOr(a.status, ST_NOTCONV);
     }
+}
+
+// Interleaved solution [np][FF] -> caller order [F][np].
+__global__ void k_unsort_aos(ll np, int F, int FF, const int *__restrict__ perm, const float *__restrict__ x,
+                             float *__restrict__ out) {
+    const ll s = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= np) return;
+    const int k = perm[s];
+    for (int f = 0; f < F; ++f) out[(ll)f * np + k] = x[s * FF + f];
 }
 
 int g_cg_grid[3] = {0, 0, 0};
@@ -1048,8 +1104,11 @@ int launch_cg(const Geo &g, Work &w, int F, const float *b_float, bool b_from_fi
     return (int)e;
 }
 
-int launch_pcg(const Geo &g, Work &w, ll np, int F, const float *c, float *x, double rtol, int max_iter,
+int pcg_width(int F) { return F <= 2 ? 2 : (F <= 4 ? 4 : PM_MAXF); }
+
+int launch_pcg(const Geo &g, Work &w, ll np, int F, const float *c, float *out, double rtol, int max_iter,
                cudaStream_t st) {
+    const int FF = pcg_width(F);
     PCG a;
     a.g = g;
     a.F = F;
@@ -1060,9 +1119,9 @@ int launch_pcg(const Geo &g, Work &w, ll np, int F, const float *c, float *x, do
     a.nbr = w.nbr;
     a.deg = w.deg;
     a.coef = w.pcoef;
-    a.x = x;
+    a.x = w.px;
     a.r = w.prp;
-    a.p = w.prp + (ll)w.F_max * w.np_max;
+    a.p = w.prp + (ll)pcg_width(w.F_max) * w.np_max;
     a.q = w.pq;
     a.red = w.red;
     a.scal = w.scal;
@@ -1071,8 +1130,7 @@ int launch_pcg(const Geo &g, Work &w, ll np, int F, const float *c, float *x, do
     a.rtol = rtol;
     a.max_iter = max_iter;
     a.unit = (float)(g.L / 4294967296.0);
-    // instantiations for up to 2, 4 and PM_MAXF fields (accumulators in registers)
-    const int fi = F <= 2 ? 0 : (F <= 4 ? 1 : 2);
+    const int fi = FF == 2 ? 0 : (FF == 4 ? 1 : 2);
     const int di = (g.dim - 1) * 3 + fi;
     void (*const kerns[6])(PCG) = {k_pcg<1, 2>, k_pcg<1, 4>, k_pcg<1, PM_MAXF>,
                                    k_pcg<2, 2>, k_pcg<2, 4>, k_pcg<2, PM_MAXF>};
@@ -1097,5 +1155,10 @@ int launch_pcg(const Geo &g, Work &w, ll np, int F, const float *c, float *x, do
     void *args[] = {&a};
     cudaError_t e = cudaLaunchCooperativeKernel((void *)kern, dim3(grid), dim3(256), args, 0, st);
     count_launches(1);
-    return (int)e;
+    if (e != cudaSuccess) return (int)e;
+    if (np > 0) {
+        k_unsort_aos<<<div_up(np, 256), 256, 0, st>>>(np, F, FF, w.perm, w.px, out);
+        count_launches(1);
+    }
+    return 0;
 }
