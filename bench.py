@@ -171,14 +171,21 @@ def run_reference(args):
 DELAUNAY_OP_WEIGHTS = {"candidates": 10, "tested": 5, "vertex_tests": 5, "clips": 80, "cell_size_sum": 9}
 # ALU peak: 152 SMs x 128 FP32 lanes x one instruction per lane per clock.
 ALU_LANES = 152 * 128
+# DRAM traffic of one k_delaunay launch per particle: dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture on the 1024^2 mixture (4,194,304
+# particles: 99.46 MB read + 103.85 MB written), scaled to a launch by its
+# particle count (the kernel's traffic grows in proportion to it).
+DELAUNAY_DRAM_BYTES_PER_PARTICLE = (99.463680e6 + 103.848704e6) / 4194304
 
 
-def alu_roofline(kernel, counts, ms, sm_mhz):
+def alu_roofline(kernel, counts, ms, sm_mhz, n_particles):
     ops = float(sum(DELAUNAY_OP_WEIGHTS[k] * counts[k] for k in DELAUNAY_OP_WEIGHTS))
     achieved = ops / (ms * 1e-3) / 1e12
     peak = ALU_LANES * sm_mhz * 1e6 / 1e12
     return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-            "frac": achieved / peak, "traffic": None, "ops_per_launch": ops, "work_counts": counts,
+            "frac": achieved / peak, "traffic": DELAUNAY_DRAM_BYTES_PER_PARTICLE * n_particles,
+            "traffic_source": "ncu dram bytes of k_delaunay on the 1024^2 mixture, scaled by particles",
+            "ops_per_launch": ops, "work_counts": counts,
             "peak_source": f"derived: 152 SMs x 128 lanes x {sm_mhz:.0f} MHz (median SM clock sampled during the "
                            f"timed region)"}
 
@@ -302,7 +309,7 @@ def run_mixture(args, pm, torch, dist, local):
     ctx.profile(False)
     sm = ck.get("sm_mhz") or float(measured_peaks().get("sm_max_mhz", 2070.0))
     dom = max(plain["phase_ms"], key=plain["phase_ms"].get)
-    roof = alu_roofline("k_delaunay (phase triangulate)", counts, plain["phase_ms"]["triangulate"], sm)
+    roof = alu_roofline("k_delaunay (phase triangulate)", counts, plain["phase_ms"]["triangulate"], sm, N)
     roof["dominant_phase"] = dom
     hbm = float(measured_peaks().get("hbm_gbs", 6800.0))
     minimal = N * (8 + 4 * F) + n * n * 4 * F  # positions + values in, fields out
@@ -547,7 +554,7 @@ def main():
     counts = ctx.work_read()
     ctx.profile(False)
     sm = ck.get("sm_mhz") or float(measured_peaks().get("sm_max_mhz", 2070.0))
-    roof = alu_roofline("k_delaunay (phase triangulate)", counts, phase_ms["triangulate"], sm)
+    roof = alu_roofline("k_delaunay (phase triangulate)", counts, phase_ms["triangulate"], sm, N)
     roof["dominant_phase"] = dom
 
     cpu = None

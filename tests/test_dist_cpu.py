@@ -87,3 +87,18 @@ def test_reference_arm_rank_handling(monkeypatch):
 def _tiny():
     from paper_1610_05258_gb300 import workloads as W
     return W.mixture(16, 2, F=1, seed=3)
+
+
+def test_alu_roofline_arithmetic():
+    """The triangulation's roofline: weighted work counts over the phase time,
+    the lane peak at the given clock, DRAM traffic in proportion to particles."""
+    import bench
+    counts = {k: 0 for k in bench.DELAUNAY_OP_WEIGHTS}
+    counts["clips"] = 10 ** 9
+    r = bench.alu_roofline("k", counts, 10.0, 2000.0, 4194304)
+    assert r["bound"] == "alu" and r["unit"] == "Tops/s"
+    assert r["achieved"] == pytest.approx(80e9 / 1e-2 / 1e12)
+    assert r["peak"] == pytest.approx(152 * 128 * 2000e6 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["traffic"] == pytest.approx(99.463680e6 + 103.848704e6)
+    assert bench.alu_roofline("k", counts, 10.0, 2000.0, 2 * 4194304)["traffic"] == pytest.approx(2 * r["traffic"])
