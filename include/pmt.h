@@ -350,9 +350,12 @@ pm_status pm_profile_read(pm_ctx *ctx, double *ms, long long *calls, int reset);
  * build of the triangulation kernel (same results, slower; not for timing).
  * counts[0..4] = candidates examined, candidates within the distance bound,
  * in-circle vertex tests, clips of the Voronoi cell, sum of the cell sizes
- * after each clip, summed over all particles and calls since the last reset.
+ * after each clip, summed over all particles and calls since the last reset,
+ * each particle counted once, in the pass that completes its cell.
+ * counts[5] = cells the main pass gave up to the retry passes (capacity 9),
+ * counts[6] = cells the first retry pass gave up to the last (capacity 12).
  * Waits for the context's stream. Host array of `ncounts` entries (entries
- * past 4 are written as 0). PM_EINVAL on a NULL ctx or array. */
+ * past 6 are written as 0). PM_EINVAL on a NULL ctx or array. */
 pm_status pm_work_read(pm_ctx *ctx, long long *counts, int ncounts, int reset);
 const char *pm_phase_name(int phase);
 /* Number of kernels this library has launched in the process so far. */

@@ -69,8 +69,10 @@ __device__ __forceinline__ int prio(int enc, const int *__restrict__ perm) {
 
 #define DBLK 64     // threads per block of the main triangulation pass
 #define DCAP 9      // polygon capacity of the main pass (22 warps per SM)
-#define RBLK 32     // threads per block of the retry pass
-#define RCAP 24     // polygon capacity of the retry pass (= PM_MAXDEG)
+#define R1BLK 32    // threads per block of the first retry pass
+#define R1CAP 12    // polygon capacity of the first retry pass (17 warps per SM)
+#define RBLK 32     // threads per block of the last retry pass
+#define RCAP 24     // polygon capacity of the last retry pass (= PM_MAXDEG)
 #define ST_OVERFLOW 0x40000000  // internal: the cell outgrew the main pass's capacity
 
 // Float circumcentre c of (0, a, b) and a bound e on the error of each of its
@@ -130,8 +132,10 @@ __device__ __forceinline__ float set_vertex(PolyS<NB> P, int k, float ax, float 
 // Work of one thread, counted by the counting instantiation of the kernel:
 // candidates examined, candidates passing the distance test, vertex tests,
 // clips, and the sum of the cell sizes after each clip.
+// Work of the cells a pass completes (a pass that gives a cell up to a larger
+// capacity drops what it counted for it), and the cells given up.
 struct WorkCount {
-    unsigned cand = 0, tested = 0, vtests = 0, clips = 0, msum = 0;
+    unsigned cand = 0, tested = 0, vtests = 0, clips = 0, msum = 0, over = 0;
 };
 
 // Clip the cell of p by the bisector of candidate s (relative position
@@ -385,21 +389,24 @@ __device__ __forceinline__ int star_of(PolyS<NB> P, int p, const Geo &g, ll np, 
     return 0;
 }
 
+// Work counters 0..4 into wsum[0..4], the give-ups into wsum[over_slot].
 template <bool COUNT>
-__device__ __forceinline__ void add_counts(const WorkCount &wc, ull *__restrict__ wsum) {
+__device__ __forceinline__ void add_counts(const WorkCount &wc, ull *__restrict__ wsum, int over_slot) {
     if (!COUNT) return;
     // warp sums, one atomic per warp and counter
-    unsigned v[5] = {wc.cand, wc.tested, wc.vtests, wc.clips, wc.msum};
+    unsigned v[6] = {wc.cand, wc.tested, wc.vtests, wc.clips, wc.msum, wc.over};
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i < 6; ++i) {
         unsigned x = v[i];
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if ((threadIdx.x & 31) == 0 && x) atomicAdd(wsum + i, (ull)x);
+        if ((threadIdx.x & 31) == 0 && x) atomicAdd(wsum + (i < 5 ? i : over_slot), (ull)x);
     }
 }
 
 // Main pass: one thread per particle, polygon capacity DCAP. A particle whose
 // cell outgrows it is appended to the retry list (no output written).
+// Counters: wsum[0..4] the work of completed cells, wsum[5] the cells given
+// up by the main pass, wsum[6] those given up by the first retry pass.
 template <bool COUNT>
 __global__ void __launch_bounds__(DBLK, 11) k_delaunay(Geo g, ll np, const uint2 *__restrict__ pos,
                                                    const int *__restrict__ cell_start, const int *__restrict__ perm,
@@ -416,6 +423,10 @@ __global__ void __launch_bounds__(DBLK, 11) k_delaunay(Geo g, ll np, const uint2
         PolyS<DBLK> P{sq, sv, (int)threadIdx.x};
         const int err = star_of<DCAP, DBLK, COUNT>(P, p, g, np, pos, cell_start, perm, nbr, deg, vol, vol_scale, wc);
         if (err == ST_OVERFLOW) {
+            if (COUNT) {
+                wc = WorkCount{};
+                wc.over = 1;
+            }
             const int k = atomicAdd(nretry, 1);
             PM_CHK(k >= 0 && k < np, 205, k = -1)
             if (k >= 0) retry[k] = p;
@@ -425,34 +436,48 @@ __global__ void __launch_bounds__(DBLK, 11) k_delaunay(Geo g, ll np, const uint2
             vol[p] = 0.0f;
         }
     }
-    add_counts<COUNT>(wc, wsum);
+    add_counts<COUNT>(wc, wsum, 5);
 }
 
-// Retry pass over the listed particles with capacity RCAP (grid-stride).
-template <bool COUNT>
-__global__ void __launch_bounds__(RBLK) k_delaunay_retry(Geo g, ll np, const uint2 *__restrict__ pos,
-                                                         const int *__restrict__ cell_start,
-                                                         const int *__restrict__ perm, int *__restrict__ nbr,
-                                                         unsigned char *__restrict__ deg, float *__restrict__ vol,
-                                                         float vol_scale, int *__restrict__ status,
-                                                         const int *__restrict__ retry, const int *__restrict__ nretry,
-                                                         ull *__restrict__ wsum) {
-    __shared__ int4 sq[RCAP][RBLK];
-    __shared__ float4 sv[RCAP][RBLK];
+// Retry passes over the listed particles (grid-stride). The first (capacity
+// R1CAP, LAST false) marks a particle whose cell outgrows it by storing ~p in
+// its list entry; the last (capacity RCAP, LAST true) takes only the marked
+// entries.
+template <int CAP, int NB, bool LAST, bool COUNT>
+__global__ void __launch_bounds__(NB) k_delaunay_retry(Geo g, ll np, const uint2 *__restrict__ pos,
+                                                       const int *__restrict__ cell_start,
+                                                       const int *__restrict__ perm, int *__restrict__ nbr,
+                                                       unsigned char *__restrict__ deg, float *__restrict__ vol,
+                                                       float vol_scale, int *__restrict__ status,
+                                                       int *__restrict__ retry, const int *__restrict__ nretry,
+                                                       ull *__restrict__ wsum) {
+    __shared__ int4 sq[CAP][NB];
+    __shared__ float4 sv[CAP][NB];
     const int cnt = *nretry;
     WorkCount wc;
-    PolyS<RBLK> P{sq, sv, (int)threadIdx.x};
-    for (ll j = (ll)blockIdx.x * RBLK + threadIdx.x; j < cnt; j += (ll)gridDim.x * RBLK) {
-        const int p = retry[j];
+    PolyS<NB> P{sq, sv, (int)threadIdx.x};
+    for (ll j = (ll)blockIdx.x * NB + threadIdx.x; j < cnt; j += (ll)gridDim.x * NB) {
+        int p = retry[j];
+        if (LAST) {
+            if (p >= 0) continue;
+            p = ~p;
+        }
         PM_CHK(p >= 0 && p < np, 206, continue)
-        const int err = star_of<RCAP, RBLK, COUNT>(P, p, g, np, pos, cell_start, perm, nbr, deg, vol, vol_scale, wc);
-        if (err) {
+        const WorkCount before = wc;
+        const int err = star_of<CAP, NB, COUNT>(P, p, g, np, pos, cell_start, perm, nbr, deg, vol, vol_scale, wc);
+        if (!LAST && err == ST_OVERFLOW) {
+            if (COUNT) {
+                wc = before;
+                wc.over++;
+            }
+            retry[j] = ~p;
+        } else if (err) {
             atomicOr(status, (err & ~ST_OVERFLOW) | (err == ST_OVERFLOW ? ST_DEGREE : 0));
             deg[p] = 0;
             vol[p] = 0.0f;
         }
     }
-    add_counts<COUNT>(wc, wsum);
+    add_counts<COUNT>(wc, wsum, 6);  // the first retry pass's give-ups (none in the last)
 }
 
 // 1D: v_mu = half the distance between the two neighbours on the circle.
@@ -496,19 +521,25 @@ void launch_triangulate(const Geo &g, Work &w, ll np, cudaStream_t st, bool coun
     float scale = (float)(u * u / 6.0);
     cudaMemsetAsync(w.nretry, 0, sizeof(int), st);
     // w.tmp (caller indices before the canonical cell order) is free after the sort
-    const int rgrid = 16 * 152;  // about one listed particle per thread
+    // grid-stride passes over the retry list: the first with 17 resident
+    // blocks per SM, the last (rare entries) with 8
+    const int r1grid = 17 * 152, rgrid = 8 * 152;
     if (count_work) {
         k_delaunay<true><<<div_up(np, DBLK), DBLK, 0, st>>>(g, np, w.pos, w.cell_start, w.perm, w.nbr, w.deg, w.vol,
                                                              scale, w.status, w.tmp, w.nretry, w.wsum);
-        k_delaunay_retry<true><<<rgrid, RBLK, 0, st>>>(g, np, w.pos, w.cell_start, w.perm, w.nbr, w.deg, w.vol,
-                                                        scale, w.status, w.tmp, w.nretry, w.wsum);
+        k_delaunay_retry<R1CAP, R1BLK, false, true><<<r1grid, R1BLK, 0, st>>>(
+            g, np, w.pos, w.cell_start, w.perm, w.nbr, w.deg, w.vol, scale, w.status, w.tmp, w.nretry, w.wsum);
+        k_delaunay_retry<RCAP, RBLK, true, true><<<rgrid, RBLK, 0, st>>>(
+            g, np, w.pos, w.cell_start, w.perm, w.nbr, w.deg, w.vol, scale, w.status, w.tmp, w.nretry, w.wsum);
     } else {
         k_delaunay<false><<<div_up(np, DBLK), DBLK, 0, st>>>(g, np, w.pos, w.cell_start, w.perm, w.nbr, w.deg,
                                                               w.vol, scale, w.status, w.tmp, w.nretry, nullptr);
-        k_delaunay_retry<false><<<rgrid, RBLK, 0, st>>>(g, np, w.pos, w.cell_start, w.perm, w.nbr, w.deg, w.vol,
-                                                         scale, w.status, w.tmp, w.nretry, nullptr);
+        k_delaunay_retry<R1CAP, R1BLK, false, false><<<r1grid, R1BLK, 0, st>>>(
+            g, np, w.pos, w.cell_start, w.perm, w.nbr, w.deg, w.vol, scale, w.status, w.tmp, w.nretry, nullptr);
+        k_delaunay_retry<RCAP, RBLK, true, false><<<rgrid, RBLK, 0, st>>>(
+            g, np, w.pos, w.cell_start, w.perm, w.nbr, w.deg, w.vol, scale, w.status, w.tmp, w.nretry, nullptr);
     }
-    count_launches(2);
+    count_launches(3);
 }
 
 void launch_volumes_1d(const Geo &g, Work &w, ll np, cudaStream_t st) {

@@ -110,45 +110,53 @@ __global__ void k_place(ll np, const int *__restrict__ key, const int *__restric
     tmp[cell_start[key[k]] + slot[k]] = (int)k;
 }
 
-// One thread per cell: canonical order inside the cell, then gather the
-// particle records into sorted order and track max |A| per field.
+// One thread per cell: canonical order of the caller indices inside the cell
+// (ascending index in 2D; by coordinate, then index, in 1D).
 __global__ void k_canon(Geo g, ll np, const int *__restrict__ cell_start, int *__restrict__ tmp,
-                        const uint2 *__restrict__ fx, const float *__restrict__ vals, int F, int *__restrict__ perm,
-                        uint2 *__restrict__ pos, float *__restrict__ vals_s, unsigned *__restrict__ maxabs,
-                        int *__restrict__ status) {
+                        const uint2 *__restrict__ fx) {
     ll c = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.ncell) return;
+    int s0 = cell_start[c], s1 = cell_start[c + 1];
+    PM_CHK(s0 >= 0 && s0 <= s1 && s1 <= np, 104, return)
+    for (int i = s0 + 1; i < s1; ++i) {
+        int v = tmp[i];
+        uint32_t xv = g.dim == 1 ? fx[v].x : 0u;
+        int j = i - 1;
+        while (j >= s0) {
+            int u = tmp[j];
+            bool greater;
+            if (g.dim == 1) {
+                uint32_t xu = fx[u].x;
+                greater = xu > xv || (xu == xv && u > v);
+            } else {
+                greater = u > v;
+            }
+            if (!greater) break;
+            tmp[j + 1] = u;
+            --j;
+        }
+        tmp[j + 1] = v;
+    }
+}
+
+// One thread per sorted slot: gather the particle records into sorted order
+// (coalesced writes) and track max |A| per field.
+#define GATHER_BLK 256
+__global__ void __launch_bounds__(GATHER_BLK) k_gather(ll np, const int *__restrict__ tmp, const uint2 *__restrict__ fx,
+                         const float *__restrict__ vals, int F, int *__restrict__ perm, uint2 *__restrict__ pos,
+                         float *__restrict__ vals_s, unsigned *__restrict__ maxabs, int *__restrict__ status) {
+    ll s = (ll)blockIdx.x * blockDim.x + threadIdx.x;
     float mx[PM_MAXF];
     for (int f = 0; f < PM_MAXF; ++f) mx[f] = 0.0f;
     bool bad = false;
-    if (c < g.ncell) {
-        int s0 = cell_start[c], s1 = cell_start[c + 1];
-        PM_CHK(s0 >= 0 && s0 <= s1 && s1 <= np, 104, s1 = s0)
-        for (int i = s0 + 1; i < s1; ++i) {
-            int v = tmp[i];
-            uint32_t xv = g.dim == 1 ? fx[v].x : 0u;
-            int j = i - 1;
-            while (j >= s0) {
-                int u = tmp[j];
-                bool greater;
-                if (g.dim == 1) {
-                    uint32_t xu = fx[u].x;
-                    greater = xu > xv || (xu == xv && u > v);
-                } else {
-                    greater = u > v;
-                }
-                if (!greater) break;
-                tmp[j + 1] = u;
-                --j;
-            }
-            tmp[j + 1] = v;
-        }
-        for (int s = s0; s < s1; ++s) {
-            int idx = tmp[s];
-            PM_CHK(idx >= 0 && idx < np, 105, continue)
+    if (s < np) {
+        const int idx = tmp[s];
+        PM_CHK(idx >= 0 && idx < np, 105, s = np)
+        if (s < np) {
             perm[s] = idx;
-            pos[s] = fx[idx];
+            pos[s] = __ldg(fx + idx);
             for (int f = 0; f < F; ++f) {
-                float a = vals[(ll)f * np + idx];
+                float a = __ldg(vals + (ll)f * np + idx);
                 if (!isfinite(a)) bad = true;
                 vals_s[(ll)f * np + s] = a;
                 mx[f] = fmaxf(mx[f], fabsf(a));
@@ -156,10 +164,21 @@ __global__ void k_canon(Geo g, ll np, const int *__restrict__ cell_start, int *_
         }
     }
     if (bad) atomicOr(status, ST_NONFINITE);
+    // block maximum per field, then one atomic per block and field, issued
+    // only when it raises the stored value (the words every block updates)
+    __shared__ float wmax[GATHER_BLK / 32][PM_MAXF];
     for (int f = 0; f < F; ++f) {
         float m = mx[f];
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(&maxabs[f], __float_as_uint(m));
+        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5][f] = m;
+    }
+    __syncthreads();
+    if (threadIdx.x < F) {
+        const int f = threadIdx.x;
+        float m = 0.0f;
+        for (int k = 0; k < GATHER_BLK / 32; ++k) m = fmaxf(m, wmax[k][f]);
+        const unsigned mu = __float_as_uint(m);
+        if (m > 0.0f && *(volatile const unsigned *)&maxabs[f] < mu) atomicMax(&maxabs[f], mu);
     }
 }
 
@@ -175,7 +194,10 @@ void launch_sort(const Geo &g, Work &w, const float *px, const float *py, ll np,
     k_scan_top<<<1, 1024, 0, st>>>(w.scan_tmp, nb, w.cell_start + g.ncell);
     k_scan_add<<<div_up(g.ncell, 256), 256, 0, st>>>(w.cell_start, g.ncell, w.scan_tmp);
     if (np > 0) k_place<<<div_up(np, 256), 256, 0, st>>>(np, w.key, w.slot, w.cell_start, w.tmp);
-    k_canon<<<div_up(g.ncell, 128), 128, 0, st>>>(g, np, w.cell_start, w.tmp, w.fx, vals, vals ? F : 0, w.perm,
-                                                   w.pos, w.vals, w.maxabs, w.status);
-    count_launches(np > 0 ? 6 : 4);
+    if (np > 0) {
+        k_canon<<<div_up(g.ncell, 128), 128, 0, st>>>(g, np, w.cell_start, w.tmp, w.fx);
+        k_gather<<<div_up(np, GATHER_BLK), GATHER_BLK, 0, st>>>(np, w.tmp, w.fx, vals, vals ? F : 0, w.perm, w.pos, w.vals,
+                                                  w.maxabs, w.status);
+    }
+    count_launches(np > 0 ? 7 : 3);
 }

@@ -289,6 +289,16 @@ def test_triangulation_high_degree_retry(built):
     (dv,) = to_dev(torch, vals)
     out, info = c.assign_mass(dpx, dpy, dv)
     assert np.abs(out.cpu().numpy() - 1.0).max() <= 1e-5
+    # the counting build: every centre outgrows the main pass's 9 slots, the
+    # four of degree > 12 also the first retry pass's 12; the counting build
+    # gives the same stars
+    c.profile(True, count_work=True)
+    tri2, off2 = c.triangulate(dpx, dpy)
+    w = c.work_read()
+    c.profile(False)
+    assert canon_tris(tri2.cpu().numpy(), off2.cpu().numpy()) == got
+    assert w["retried"] >= 6 and 4 <= w["retried_last"] <= w["retried"]
+    assert w["clips"] > 0 and w["cell_size_sum"] >= 3 * w["clips"]
 
 
 def test_triangulation_degree_above_capacity(built):
