@@ -23,10 +23,12 @@ Every function restates a definition of the paper in plain double precision
 * ``interpolate_mass``     full mass: m_p Abb = c, Eq. proj2 (phi_mu of
                        Eq. phi_def on the particles), solved by FP64 CG
 
-Parity unpinned: the App. B quadrature in 2D (mode 1) follows a reading of a
-garbled passage (the paper's text describes six-point quadratic fits on
-triangles; this build's mesh is bilinear), so it is checked only against its
-own exactness property, not against a value the paper prints.
+The App. B quadrature in 2D (mode 1) follows a reading of a garbled passage
+(the paper's text describes six-point quadratic fits on triangles; this
+build's mesh is bilinear). Its implementation is pinned by closed forms
+(exact for fields affine over a node's support; with particles at all 3 x 3
+sample points, exact for quadratic fields, which fixes the point weights);
+the reading itself has no value printed in the paper to compare with.
 """
 from __future__ import annotations
 

@@ -281,6 +281,58 @@ def test_1d_appendix_b_quadrature_exact_without_particles_inside():
     np.testing.assert_allclose(oracle.rhs(1, n, L, px, None, a, mode=1), oracle.rhs(1, n, L, px, None, a, mode=0), atol=1e-14)
 
 
+def test_2d_appendix_b_quadrature_exact_for_affine_fields():
+    """App. B reading in 2D (biquadratic fit through the 3 x 3 points of every
+    cell, integrated exactly against the bilinear hats): where A is affine on
+    every triangle over a node's support, the fit is exact and
+    b_j = int A psi_j = h^2 A(x_j) (psi_j is symmetric about x_j with integral
+    h^2). Nodes at least three cells from the periodic seam qualify, since A
+    jumps only on triangles that cross it. Also A = 1 gives b_j = h^2."""
+    n, L = 16, 1.0
+    h = L / n
+    px, py = W.jittered_lattice(n, sub=2, jitter=0.4, seed=31)
+    X = oracle.fixed_coords(px, L).astype(np.float64) * (L / TWO32)
+    Y = oracle.fixed_coords(py, L).astype(np.float64) * (L / TWO32)
+    a = np.stack([0.3 + 1.7 * X - 0.9 * Y, np.ones_like(X)])
+    T = oracle.triangulate(L, px, py)
+    b1 = oracle.rhs(2, n, L, px, py, a, mode=1, tri=T)
+    jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    inner = ((ii >= 3) & (ii <= n - 3) & (jj >= 3) & (jj <= n - 3)).ravel()
+    want = h * h * (0.3 + 1.7 * ii * h - 0.9 * jj * h).ravel()
+    np.testing.assert_allclose(b1[0][inner], want[inner], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(b1[1], h * h, rtol=1e-12)
+    # a field that is not affine inside the cells differs from the exact integral
+    q = np.stack([np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Y)])
+    b0 = oracle.rhs(2, n, L, px, py, q, mode=0, tri=T)
+    bq = oracle.rhs(2, n, L, px, py, q, mode=1, tri=T)
+    assert np.abs(bq - b0).max() > 1e-9 * np.abs(b0).max()
+
+
+def test_2d_appendix_b_quadrature_weights_on_quadratic_samples():
+    """With a particle at every point of the twice refined mesh (nodes, edge
+    midpoints, cell centres), A is sampled exactly at the 3 x 3 points of each
+    cell, so the App. B fit reproduces any field that is quadratic there. For
+    A = x^2 + 3 y^2 + x y the exact integral against the hat of node j is
+    h^2 A(x_j) + (1 + 3) h^4 / 6 (int x^2 hat = h x_j^2 + h^3 / 6 per
+    dimension): the h^4 term fixes the weights of the 3 points, which a
+    symmetric but wrong weighting of them would miss. Nodes whose samples do
+    not wrap across the seam: 1 <= i, j <= n - 1."""
+    n, L = 16, 1.0
+    h = L / n
+    m = 2 * n
+    iy, ix = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
+    px = (ix.ravel() * (L / m)).astype(np.float32)
+    py = (iy.ravel() * (L / m)).astype(np.float32)
+    X, Y = px.astype(np.float64), py.astype(np.float64)
+    a = (X * X + 3 * Y * Y + X * Y)[None]
+    b = oracle.rhs(2, n, L, px, py, a, mode=1)[0]
+    jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    xj, yj = (ii * h).ravel(), (jj * h).ravel()
+    want = h * h * (xj * xj + 3 * yj * yj + xj * yj) + 4 * h ** 4 / 6
+    inner = ((ii >= 1) & (jj >= 1)).ravel()
+    np.testing.assert_allclose(b[inner], want[inner], rtol=1e-12)
+
+
 def test_1d_mass_conservation_and_stability():
     """Mass assignment is conservative (Eq. cons with v_i = h) and stable in
     the integral form int Ab^2 <= int A^2 (L2 projection is a contraction)."""
