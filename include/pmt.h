@@ -67,6 +67,16 @@ typedef struct pm_ctx pm_ctx;
  * gradients only confirm the residual and set the mean mode exactly. */
 enum { PM_WS_DELTA = 0, PM_WS_ZERO = 1, PM_WS_USER = 2, PM_WS_NET = 3, PM_WS_DIRECT = 4 };
 
+/* Right-hand side of the mass assignment. PM_RHS_EXACT: b_j = int A psi_j
+ * exactly (Eq. proj; conservative to rounding). PM_RHS_APPB: the quadrature
+ * of App. B, read for this mesh as follows: on every mesh element A is
+ * replaced by its quadratic (1D) or biquadratic (2D) interpolant through its
+ * values at the element's nodes, edge midpoints and centre, and that
+ * interpolant is integrated exactly against the hats. This amounts to b_i =
+ * (h/3)^dim times the sum of A over the 3^dim points of the twice refined mesh
+ * around node i. Not conservative (App. B); the solve reports cons_err. */
+enum { PM_RHS_EXACT = 0, PM_RHS_APPB = 1 };
+
 typedef struct pm_net pm_net;
 
 /* Options of the mass solve  M Ab = b  (Sec. 2.4, Eq. phi_def). */
@@ -79,6 +89,7 @@ typedef struct pm_solve_opts {
     pm_net *net;     /* PM_WS_NET: start from delta + alpha c, c the network's
                         correction and alpha the step that minimises the 2-norm
                         of the start's residual (alpha = 0 keeps the delta start) */
+    int rhs_mode;    /* PM_RHS_EXACT (default) or PM_RHS_APPB (pm_assign_mass)   */
 } pm_solve_opts;
 
 /* Per-field report of a mass solve (host memory, one entry per field). */
@@ -177,6 +188,10 @@ pm_status pm_interpolate_mass(pm_ctx *ctx, const float *mesh, int F, const float
  * Eq. proj), exact. Asynchronous. */
 pm_status pm_mass_rhs(pm_ctx *ctx, const float *px, const float *py, long long np, const float *vals, int F,
                       float *b_out);
+/* The same with the quadrature chosen: rhs_mode PM_RHS_EXACT (as pm_mass_rhs)
+ * or PM_RHS_APPB (App. B, see PM_RHS_APPB). PM_EINVAL on another mode. */
+pm_status pm_mass_rhs_mode(pm_ctx *ctx, const float *px, const float *py, long long np, const float *vals, int F,
+                           int rhs_mode, float *b_out);
 
 /* Mesh mass matrix applied to mesh fields: y[f] = M x[f], m_ij = int psi_i psi_j
  * (Sec. 2.4). Asynchronous. */

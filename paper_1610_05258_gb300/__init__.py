@@ -20,12 +20,14 @@ _LIBPATH = os.environ.get("PM_LIBRARY") or os.path.join(
 _lib = None
 
 PM_WS_DELTA, PM_WS_ZERO, PM_WS_USER, PM_WS_NET, PM_WS_DIRECT = 0, 1, 2, 3, 4
+PM_RHS_EXACT, PM_RHS_APPB = 0, 1
+RHS_MODES = {"exact": PM_RHS_EXACT, "appb": PM_RHS_APPB}
 _STATUS = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ENOTCONV", 4: "PM_ETIMEOUT", 5: "PM_EDEGENERATE",
            6: "PM_ECUDA"}
 
 EXPORTS = [
     "pm_ctx_create", "pm_ctx_destroy", "pm_ctx_set_stream", "pm_sync", "pm_last_error", "pm_ctx_workspace_bytes",
-    "pm_interpolate", "pm_interpolate_lumped", "pm_interpolate_mass", "pm_assign_lumped", "pm_assign_delta", "pm_assign_flip", "pm_assign_mass", "pm_mass_rhs", "pm_mass_apply",
+    "pm_interpolate", "pm_interpolate_lumped", "pm_interpolate_mass", "pm_assign_lumped", "pm_assign_delta", "pm_assign_flip", "pm_assign_mass", "pm_mass_rhs", "pm_mass_rhs_mode", "pm_mass_apply",
     "pm_mass_solve", "pm_particle_volumes", "pm_triangulate", "pm_sort", "pm_advect_shift", "pm_advect_rotate",
     "pm_advect_rk2", "pm_profile", "pm_profile_read", "pm_work_read", "pm_phase_name", "pm_kernel_launches",
     "pm_batch_create", "pm_batch_destroy", "pm_batch_last_error", "pm_batch_tuning", "pm_batch_assign_mass",
@@ -44,7 +46,7 @@ class PMError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("warm_start", ctypes.c_int), ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("x0", ctypes.c_void_p), ("net", ctypes.c_void_p)]
+                ("x0", ctypes.c_void_p), ("net", ctypes.c_void_p), ("rhs_mode", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -91,6 +93,7 @@ def load_library(path: str | None = None):
         "pm_assign_flip": [vp, vp, vp, ll, vp, i, vp, vp, ctypes.POINTER(ll)],
         "pm_assign_mass": [vp, vp, vp, ll, vp, i, vp, ctypes.POINTER(_Opts), vp],
         "pm_mass_rhs": [vp, vp, vp, ll, vp, i, vp],
+        "pm_mass_rhs_mode": [vp, vp, vp, ll, vp, i, i, vp],
         "pm_mass_apply": [vp, vp, i, vp],
         "pm_mass_solve": [vp, vp, i, vp, ctypes.POINTER(_Opts), vp],
         "pm_particle_volumes": [vp, vp, vp, ll, vp],
@@ -262,19 +265,21 @@ class Context:
                                             _ptr(node_volume), ctypes.byref(e) if count_empty else None))
         return (out, e.value) if count_empty else out
 
-    def _opts(self, warm_start, rtol, max_iter, x0, net=None):
+    def _opts(self, warm_start, rtol, max_iter, x0, net=None, rhs="exact"):
         ws = {"delta": PM_WS_DELTA, "zero": PM_WS_ZERO, "user": PM_WS_USER, "net": PM_WS_NET,
               "direct": PM_WS_DIRECT}[warm_start]
-        return _Opts(ws, rtol, max_iter, x0.data_ptr() if x0 is not None else None, net.h.value if net else None)
+        return _Opts(ws, rtol, max_iter, x0.data_ptr() if x0 is not None else None, net.h.value if net else None,
+                     RHS_MODES[rhs])
 
     def assign_mass(self, px, py, vals, out=None, warm_start="delta", rtol=1e-6, max_iter=200, x0=None,
-                    info=True, net=None):
+                    info=True, net=None, rhs="exact"):
+        """Mass assignment; rhs "exact" (Eq. proj) or "appb" (App. B quadrature)."""
         px, py, vals, x0 = self._f32(px), self._f32(py), self._f32(vals), self._f32(x0)
         F = vals.numel() // max(1, px.numel())
         out = out if out is not None else self._empty(F, self.nodes)
         if net is not None:
             warm_start = "net"
-        o = self._opts(warm_start, rtol, max_iter, x0, net)
+        o = self._opts(warm_start, rtol, max_iter, x0, net, rhs)
         inf = (_Info * F)() if info else None
         self._stream()
         s = self.lib.pm_assign_mass(self.h, _ptr(px), _ptr(py), px.numel(), _ptr(vals), F, _ptr(out),
@@ -297,12 +302,14 @@ class Context:
                                              _ptr(feat), scale))
         return delta, feat, list(scale)
 
-    def mass_rhs(self, px, py, vals, out=None):
+    def mass_rhs(self, px, py, vals, out=None, rhs="exact"):
+        """b_j = int A psi_j; rhs "exact" (Eq. proj) or "appb" (App. B quadrature)."""
         px, py, vals = self._f32(px), self._f32(py), self._f32(vals)
         F = vals.numel() // max(1, px.numel())
         out = out if out is not None else self._empty(F, self.nodes)
         self._stream()
-        self._check(self.lib.pm_mass_rhs(self.h, _ptr(px), _ptr(py), px.numel(), _ptr(vals), F, _ptr(out)))
+        self._check(self.lib.pm_mass_rhs_mode(self.h, _ptr(px), _ptr(py), px.numel(), _ptr(vals), F,
+                                              RHS_MODES[rhs], _ptr(out)))
         return out
 
     def mass_apply(self, x, out=None):

@@ -315,6 +315,7 @@ static void default_opts(const pm_solve_opts *o, pm_solve_opts &d) {
     d.max_iter = 200;
     d.x0 = nullptr;
     d.net = nullptr;
+    d.rhs_mode = PM_RHS_EXACT;
     if (o) d = *o;
     if (!(d.rtol > 0.0)) d.rtol = 1e-6;
     if (d.max_iter <= 0) d.max_iter = 200;
@@ -348,7 +349,10 @@ static pm_status mass_front(pm_ctx *c, const float *px, const float *py, ll np, 
         Phase ph(c, PM_PH_RHS);
         launch_psum(c->g, c->w, np, F, c->st);
         if ((s = check_launch(c, "particle sums"))) return s;
-        launch_rhs(c->g, c->w, np, F, c->st);
+        if (o.rhs_mode == PM_RHS_APPB)
+            launch_rhs_appb(c->g, c->w, np, F, c->st);
+        else
+            launch_rhs(c->g, c->w, np, F, c->st);
         if ((s = check_launch(c, "right-hand side"))) return s;
     }
     start = true;
@@ -399,6 +403,7 @@ pm_status pm_assign_mass(pm_ctx *c, const float *px, const float *py, long long 
     pm_solve_opts o;
     default_opts(opts, o);
     if (o.warm_start < PM_WS_DELTA || o.warm_start > PM_WS_DIRECT) return fail(c, PM_EINVAL, "unknown warm start");
+    if (o.rhs_mode != PM_RHS_EXACT && o.rhs_mode != PM_RHS_APPB) return fail(c, PM_EINVAL, "unknown rhs_mode");
     if (o.warm_start == PM_WS_USER && !o.x0) return fail(c, PM_EINVAL, "PM_WS_USER without x0");
     if (o.warm_start == PM_WS_NET && (!o.net || !c->w.feat)) return fail(c, PM_EINVAL, "PM_WS_NET needs a network and a 2D mesh with n % 128 == 0");
     bool start = true;
@@ -444,7 +449,7 @@ pm_status pm_interpolate_lumped(pm_ctx *c, const float *mesh, int F, const float
 
 pm_status pm_interpolate_mass(pm_ctx *c, const float *mesh, int F, const float *px, const float *py, long long np,
                               float *out, const pm_solve_opts *opts, pm_solve_info *info) {
-    pm_solve_opts o = opts ? *opts : pm_solve_opts{PM_WS_DELTA, 1e-6, 200, nullptr, nullptr};
+    pm_solve_opts o = opts ? *opts : pm_solve_opts{PM_WS_DELTA, 1e-6, 200, nullptr, nullptr, PM_RHS_EXACT};
     if (!(o.rtol > 0.0) || o.max_iter < 0) return fail(c, PM_EINVAL, "bad solve options");
     pm_status s = proj_front(c, mesh, F, px, py, np, out);
     if (s) return s;
@@ -475,18 +480,27 @@ pm_status pm_assign_lumped(pm_ctx *c, const float *px, const float *py, long lon
     return check_launch(c, "pm_assign_lumped");
 }
 
-pm_status pm_mass_rhs(pm_ctx *c, const float *px, const float *py, long long np, const float *vals, int F,
-                      float *b_out) {
+pm_status pm_mass_rhs_mode(pm_ctx *c, const float *px, const float *py, long long np, const float *vals, int F,
+                           int rhs_mode, float *b_out) {
     pm_status s = check_particles(c, px, py, np, F, vals, c && c->g.dim == 2 ? 3 : 2);
     if (s) return s;
     if (F < 1 || !b_out) return fail(c, PM_EINVAL, "null output or no field");
+    if (rhs_mode != PM_RHS_EXACT && rhs_mode != PM_RHS_APPB) return fail(c, PM_EINVAL, "unknown rhs_mode");
     if ((s = prepare(c, px, py, np, vals, F, true))) return s;
     {
         Phase ph(c, PM_PH_RHS);
-        launch_rhs(c->g, c->w, np, F, c->st);
+        if (rhs_mode == PM_RHS_APPB)
+            launch_rhs_appb(c->g, c->w, np, F, c->st);
+        else
+            launch_rhs(c->g, c->w, np, F, c->st);
         launch_rhs_to_float(c->g, c->w, F, b_out, c->st);
     }
     return check_launch(c, "pm_mass_rhs");
+}
+
+pm_status pm_mass_rhs(pm_ctx *c, const float *px, const float *py, long long np, const float *vals, int F,
+                      float *b_out) {
+    return pm_mass_rhs_mode(c, px, py, np, vals, F, PM_RHS_EXACT, b_out);
 }
 
 pm_status pm_mass_apply(pm_ctx *c, const float *x, int F, float *y) {
@@ -810,6 +824,7 @@ pm_status pm_batch_assign_mass(pm_batch *b, const float *const *px, const float 
     o.max_iter = max_iter > 0 ? max_iter : 200;
     o.x0 = nullptr;
     o.net = nullptr;
+    o.rhs_mode = PM_RHS_EXACT;
     std::vector<char> start(b->ninst, 1);
     // the main stream follows the caller's stream
     cudaEventRecord(b->fork, b->user);

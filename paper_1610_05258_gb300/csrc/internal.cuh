@@ -188,6 +188,7 @@ int launch_pcg(const Geo &g, Work &w, ll np, int F, const float *c, float *out, 
 // Interleaved width of the particle solve's vectors for F fields (2, 4 or PM_MAXF).
 int pcg_width(int F);
 void launch_rhs(const Geo &g, Work &w, ll np, int F, cudaStream_t st);
+void launch_rhs_appb(const Geo &g, Work &w, ll np, int F, cudaStream_t st);
 void launch_rhs_to_float(const Geo &g, Work &w, int F, float *b_out, cudaStream_t st);
 void launch_mass_apply(const Geo &g, const float *x, int F, float *y, cudaStream_t st);
 int launch_cg(const Geo &g, Work &w, int F, const float *b_float, bool b_from_fix, float *x, bool x_has_start,

@@ -129,22 +129,24 @@ __global__ void __launch_bounds__(128, 8) k_delta2d(Geo g, ll np, const uint2 *_
 }
 
 // 1D: node i lies between the last particle at or left of it and the next one.
+// The nodes are those of the mesh refined r times (r n nodes at spacing h/r);
+// node i lies in mesh cell i / r.
 __global__ void k_delta1d(Geo g, ll np, const uint2 *__restrict__ pos, const int *__restrict__ cell_start,
-                          const float *__restrict__ vals, int F, float *__restrict__ mesh) {
+                          const float *__restrict__ vals, int F, float *__restrict__ mesh, int r) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = g.n;
+    const int n = g.n * r;
     if (i >= n) return;
-    const ull node = (ull)i << 32;  // node position times n
-    // last sorted particle with X n <= i 2^32
+    const ull node = (ull)i << 32;  // node position times r n
+    // last sorted particle with X r n <= i 2^32
     ll s = -1;
-    int c = i, steps = 0;
+    int c = i / r, steps = 0;
     {
         int e = cell_start[c + 1];
         for (int t = cell_start[c]; t < e; ++t)
             if ((ull)pos[t].x * (ull)n <= node) s = t;
     }
-    while (s < 0 && steps < n) {
-        c = c == 0 ? n - 1 : c - 1;
+    while (s < 0 && steps < g.n) {
+        c = c == 0 ? g.n - 1 : c - 1;
         ++steps;
         if (cell_start[c + 1] > cell_start[c]) s = cell_start[c + 1] - 1;
     }
@@ -633,6 +635,46 @@ __global__ void k_rhs1d(Geo g, ll np, const uint2 *__restrict__ pos, const float
     }
 }
 
+// App. B quadrature right-hand side from A sampled on the mesh refined twice
+// (A2 [F][(2n)^dim], the delta values at the nodes, edge midpoints and cell
+// centres). On every element A is replaced by its (bi)quadratic interpolant
+// through those samples and integrated exactly against the (bi)linear hats:
+// per dimension the element weights of the left hat at the points 0, h/2, h
+// are h (1/6, 1/3, 0) and of the right hat h (0, 1/3, 1/6), so over the two
+// elements around node i the weights at its refined offsets -1, 0, +1 are all
+// h/3 (and 0 at +-2). b_i is thus h^dim / 3^dim times the sum of A2 over the
+// 3 (1D) or 3 x 3 (2D) refined points around node i. Written once per node in
+// the fixed point of the exact right-hand side.
+template <int DIM>
+__global__ void k_appb_box(Geo g, int F, const float *__restrict__ A2, const unsigned *__restrict__ maxabs,
+                           ll *__restrict__ bfix) {
+    const ll i = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.ncell) return;
+    const int n = g.n, n2 = 2 * n;
+    const ll nn2 = DIM == 2 ? (ll)n2 * n2 : (ll)n2;
+    const float hd = DIM == 2 ? g.h * g.h : g.h;
+    const float w = DIM == 2 ? hd * (1.0f / 9.0f) : hd * (1.0f / 3.0f);
+    const int ix = (int)(i % n), iy = DIM == 2 ? (int)(i / n) : 0;
+    for (int f = 0; f < F; ++f) {
+        const float *a = A2 + (ll)f * nn2;
+        float sum = 0.0f;
+        if (DIM == 2) {
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                const ll row = (ll)wrapi(2 * iy + dy, n2) * n2;
+                float rs = 0.0f;
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) rs += a[row + wrapi(2 * ix + dx, n2)];
+                sum += rs;
+            }
+        } else {
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) sum += a[wrapi(2 * ix + dx, n2)];
+        }
+        bfix[(ll)f * g.ncell + i] = __float2ll_rn(ldexpf(sum * w, fix_exp(maxabs, f, hd)));
+    }
+}
+
 __global__ void k_fix_to_float(Geo g, int F, const ll *__restrict__ bfix, const unsigned *__restrict__ maxabs,
                                float *__restrict__ out) {
     ll i = (ll)blockIdx.x * blockDim.x + threadIdx.x;
@@ -879,8 +921,28 @@ void launch_delta(const Geo &g, Work &w, ll np, int F, float *mesh_out, cudaStre
     if (g.dim == 2)
         k_delta2d<<<div_up(np, 128), 128, 0, st>>>(g, np, w.pos, w.nbr, w.deg, w.vals, F, mesh_out);
     else
-        k_delta1d<<<div_up(g.n, 128), 128, 0, st>>>(g, np, w.pos, w.cell_start, w.vals, F, mesh_out);
+        k_delta1d<<<div_up(g.n, 128), 128, 0, st>>>(g, np, w.pos, w.cell_start, w.vals, F, mesh_out, 1);
     count_launches(1);
+}
+
+// App. B quadrature right-hand side into bfix: delta on the mesh refined
+// twice (into the FLIP partials, free in a mass assignment), then the box sum.
+void launch_rhs_appb(const Geo &g, Work &w, ll np, int F, cudaStream_t st) {
+    float *A2 = w.part;  // [F][(2n)^dim] <= (2^dim)(F + 1) n^dim floats
+    if (g.dim == 2) {
+        Geo g2 = g;
+        g2.n = 2 * g.n;
+        g2.ncell = 4 * g.ncell;
+        g2.h = 0.5f * g.h;
+        cudaMemsetAsync(A2, 0, sizeof(float) * F * g2.ncell, st);
+        if (np > 0) k_delta2d<<<div_up(np, 128), 128, 0, st>>>(g2, np, w.pos, w.nbr, w.deg, w.vals, F, A2);
+        k_appb_box<2><<<div_up(g.ncell, 256), 256, 0, st>>>(g, F, A2, w.maxabs, w.bfix);
+    } else {
+        cudaMemsetAsync(A2, 0, sizeof(float) * F * 2 * g.n, st);
+        if (np > 0) k_delta1d<<<div_up(2 * g.n, 128), 128, 0, st>>>(g, np, w.pos, w.cell_start, w.vals, F, A2, 2);
+        k_appb_box<1><<<div_up(g.ncell, 256), 256, 0, st>>>(g, F, A2, w.maxabs, w.bfix);
+    }
+    count_launches(np > 0 ? 2 : 1);
 }
 
 void launch_flip(const Geo &g, Work &w, ll np, int F, float *mesh_out, float *node_vol, cudaStream_t st) {
