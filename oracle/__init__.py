@@ -112,32 +112,50 @@ def sort_by_cell(dim, n, L, px, py=None):
     return perm, cs
 
 
-def interpolate(dim, n, L, mesh, px, py=None):
+def _p1(dim, kind):
+    """Mesh functions: "q1" (linear in 1D, bilinear in 2D) or "p1" (2D: cells
+    split by the diagonal from (0,0) to (1,1), linear hats on the triangles;
+    in 1D the same as q1)."""
+    if kind not in ("q1", "p1"):
+        raise ValueError(f"unknown mesh functions {kind!r}")
+    return 1 if (kind == "p1" and dim == 2) else 0
+
+
+def interpolate(dim, n, L, mesh, px, py=None, kind="q1"):
     px = _f32(px)
     py = _f32(py) if py is not None else px
     m = _f64(mesh).reshape(-1, n ** dim)
     F = m.shape[0]
     out = np.empty((F, px.shape[0]))
     _check(lib().or_interpolate(dim, n, ctypes.c_double(L), _p(m), F, _p(px), _p(py),
-                                ctypes.c_longlong(px.shape[0]), _p(out)), "interpolate")
+                                ctypes.c_longlong(px.shape[0]), _p(out), _p1(dim, kind)), "interpolate")
     return out
 
 
-def mass_apply(dim, n, L, x):
+def mass_apply(dim, n, L, x, kind="q1"):
     x = _f64(x).reshape(-1, n ** dim)
     y = np.empty_like(x)
-    lib().or_mass_apply(dim, n, ctypes.c_double(L), _p(x), x.shape[0], _p(y))
+    lib().or_mass_apply(dim, n, ctypes.c_double(L), _p(x), x.shape[0], _p(y), _p1(dim, kind))
     return y
 
 
-def mass_solve(dim, n, L, b):
+def mass_solve(dim, n, L, b, kind="q1"):
+    """M x = b. Q1: direct tensor-product periodic tridiagonal solve. P1 (2D):
+    M is circulant on the periodic grid, so it is diagonalised by the 2D FFT;
+    its eigenvalues are the FFT of M applied to a unit impulse."""
     b = _f64(b).reshape(-1, n ** dim)
+    if _p1(dim, kind):
+        e0 = np.zeros(n * n)
+        e0[0] = 1.0
+        lam = np.fft.fft2(mass_apply(2, n, L, e0, "p1").reshape(n, n))
+        x = np.fft.ifft2(np.fft.fft2(b.reshape(-1, n, n)) / lam).real
+        return x.reshape(b.shape)
     x = np.empty_like(b)
     _check(lib().or_mass_solve_direct(dim, n, ctypes.c_double(L), _p(b), b.shape[0], _p(x)), "mass_solve")
     return x
 
 
-def mass_solve_cg(dim, n, L, b, x0=None, rtol=1e-12, max_iter=10000):
+def mass_solve_cg(dim, n, L, b, x0=None, rtol=1e-12, max_iter=10000, kind="q1"):
     b = _f64(b).reshape(-1, n ** dim)
     x = np.empty_like(b)
     F = b.shape[0]
@@ -145,7 +163,7 @@ def mass_solve_cg(dim, n, L, b, x0=None, rtol=1e-12, max_iter=10000):
     res = np.zeros(F)
     x0p = _p(_f64(x0).reshape(b.shape)) if x0 is not None else None
     _check(lib().or_mass_solve_cg(dim, n, ctypes.c_double(L), _p(b), F, _p(x), x0p, ctypes.c_double(rtol), max_iter,
-                                  _p(it), _p(res)), "mass_solve_cg")
+                                  _p(it), _p(res), _p1(dim, kind)), "mass_solve_cg")
     return x, it, res
 
 
@@ -202,7 +220,7 @@ def delta(dim, n, L, px, py, vals, tri=None):
     return out
 
 
-def flip(dim, n, L, px, py, vals, v=None):
+def flip(dim, n, L, px, py, vals, v=None, kind="q1"):
     """FLIP assignment; returns (mesh values, FLIP node volumes, #empty nodes)."""
     px = _f32(px)
     py = _f32(py) if py is not None else px
@@ -215,12 +233,13 @@ def flip(dim, n, L, px, py, vals, v=None):
     vol = np.empty(n ** dim)
     e = ctypes.c_longlong(0)
     _check(lib().or_flip(dim, n, ctypes.c_double(L), _p(px), _p(py), ctypes.c_longlong(px.shape[0]), _p(a), F, _p(v),
-                         _p(out), _p(vol), ctypes.byref(e)), "flip")
+                         _p(out), _p(vol), ctypes.byref(e), _p1(dim, kind)), "flip")
     return out, vol, e.value
 
 
-def rhs(dim, n, L, px, py, vals, mode=0, tri=None):
-    """b_j = int A psi_j (mode 0 exact, mode 1 App. B quadrature)."""
+def rhs(dim, n, L, px, py, vals, mode=0, tri=None, kind="q1"):
+    """b_j = int A psi_j (mode 0 exact, mode 1 App. B quadrature; the P1 mesh
+    has mode 0 only)."""
     px = _f32(px)
     a = _fields(vals, px.shape[0])
     F = a.shape[0]
@@ -231,13 +250,13 @@ def rhs(dim, n, L, px, py, vals, mode=0, tri=None):
     py = _f32(py)
     t, o, _ = tri if tri is not None else triangulate(L, px, py)
     _check(lib().or2_rhs(n, ctypes.c_double(L), _p(px), _p(py), ctypes.c_longlong(px.shape[0]), _p(a), F, _p(t), _p(o),
-                         ctypes.c_longlong(t.shape[0]), mode, _p(b)), "rhs")
+                         ctypes.c_longlong(t.shape[0]), mode, _p(b), _p1(dim, kind)), "rhs")
     return b
 
 
-def assign_mass(dim, n, L, px, py, vals, mode=0, tri=None):
+def assign_mass(dim, n, L, px, py, vals, mode=0, tri=None, kind="q1"):
     """Mass assignment (Sec. 2.4): Ab = M^-1 b."""
-    return mass_solve(dim, n, L, rhs(dim, n, L, px, py, vals, mode, tri))
+    return mass_solve(dim, n, L, rhs(dim, n, L, px, py, vals, mode, tri, kind), kind)
 
 
 def tri_monomial(x, y, a, b):
@@ -254,7 +273,7 @@ def _tri_or_none(dim, L, px, py, tri):
     return t, o, t.shape[0]
 
 
-def g2p_integral(dim, n, L, mesh, px, py=None, tri=None):
+def g2p_integral(dim, n, L, mesh, px, py=None, tri=None, kind="q1"):
     """c_mu = int Ab(r) psi_mu(r) dr with Ab the mesh interpolant of `mesh`
     ([F][n^dim]); exact (Simpson on merged breakpoints in 1D, clipped
     polygons with a degree-3 rule in 2D)."""
@@ -271,7 +290,7 @@ def g2p_integral(dim, n, L, mesh, px, py=None, tri=None):
     py = _f32(py)
     t, o, nt = _tri_or_none(2, L, px, py, tri)
     _check(lib().or2_g2p_int(n, ctypes.c_double(L), _p(px), _p(py), ctypes.c_longlong(npt), _p(m), F, _p(t), _p(o),
-                             ctypes.c_longlong(nt), _p(c)), "g2p_int")
+                             ctypes.c_longlong(nt), _p(c), _p1(2, kind)), "g2p_int")
     return c
 
 
@@ -289,9 +308,9 @@ def particle_mass_apply(dim, L, px, py, x, tri=None):
     return y
 
 
-def interpolate_lumped(dim, n, L, mesh, px, py=None, tri=None):
+def interpolate_lumped(dim, n, L, mesh, px, py=None, tri=None, kind="q1"):
     """Lumped mesh -> particle projection, Abb_mu = c_mu / v_mu (Eq. lumped)."""
-    c = g2p_integral(dim, n, L, mesh, px, py, tri)
+    c = g2p_integral(dim, n, L, mesh, px, py, tri, kind)
     if dim == 1:
         v = particle_volumes(1, L, px)
     else:
@@ -299,13 +318,13 @@ def interpolate_lumped(dim, n, L, mesh, px, py=None, tri=None):
     return c / v
 
 
-def interpolate_mass(dim, n, L, mesh, px, py=None, tri=None, rtol=1e-13, max_iter=20000):
+def interpolate_mass(dim, n, L, mesh, px, py=None, tri=None, rtol=1e-13, max_iter=20000, kind="q1"):
     """Full mass mesh -> particle projection (Eq. proj2): M_p Abb = c."""
     px = _f32(px)
     py_ = _f32(py) if py is not None else px
     if dim == 2 and tri is None:
         tri = triangulate(L, px, py_)
-    c = g2p_integral(dim, n, L, mesh, px, py_, tri)
+    c = g2p_integral(dim, n, L, mesh, px, py_, tri, kind)
     F, npt = c.shape
     t, o, nt = _tri_or_none(dim, L, px, py_, tri)
     x = np.empty_like(c)

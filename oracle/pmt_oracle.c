@@ -111,13 +111,32 @@ int or_sort_by_cell(int dim, int n, double L, const float *px, const float *py, 
 
 static int wrapi(ll i, int n) { ll r = i % n; return (int)(r < 0 ? r + n : r); }
 
+/* The four mesh functions that are non-zero on a 2D cell, at local
+ * coordinates (s, t) in [0,1]^2, in the corner order (0,0), (1,0), (0,1),
+ * (1,1).
+ *   Q1 (p1 = 0): bilinear, (1-s)(1-t), s(1-t), (1-s)t, st.
+ *   P1 (p1 = 1): the cell is split by its diagonal from (0,0) to (1,1) into
+ *     the triangles {(0,0),(1,0),(1,1)} (s >= t) and {(0,0),(1,1),(0,1)}
+ *     (s <= t); on each, the hats are the barycentric coordinates of its three
+ *     corners and the fourth corner's hat is zero. */
+static void cell_hats(int p1, double s, double t, double w[4]) {
+    if (!p1) {
+        w[0] = (1 - s) * (1 - t); w[1] = s * (1 - t); w[2] = (1 - s) * t; w[3] = s * t;
+    } else if (s >= t) {
+        w[0] = 1 - s; w[1] = s - t; w[2] = 0.0; w[3] = t;
+    } else {
+        w[0] = 1 - t; w[1] = 0.0; w[2] = t - s; w[3] = s;
+    }
+}
+
 /* Linear (1D) / bilinear (2D) hat of node i evaluated at local coordinate s
  * in [0,1) of the cell whose left node is i (s) or i+1 (1-s). */
 
 /* m_ij = int psi_i psi_j (Sec. 2.4), assembled element by element with a
  * Gauss-Legendre rule that is exact for the element products (degree 2 per
- * axis), then applied: y_i = sum_j m_ij x_j. */
-void or_mass_apply(int dim, int n, double L, const double *x, int F, double *y) {
+ * axis), then applied: y_i = sum_j m_ij x_j. 2D P1 (p1 = 1): each cell is two
+ * triangles of area h^2/2 with the P1 element matrix (area/12)(1 + delta_ab). */
+void or_mass_apply(int dim, int n, double L, const double *x, int F, double *y, int p1) {
     const double h = L / n;
     const double g[2] = {0.5 - 0.5 / sqrt(3.0), 0.5 + 0.5 / sqrt(3.0)}; /* on [0,1], weights 1/2 */
     if (dim == 1) {
@@ -141,7 +160,14 @@ void or_mass_apply(int dim, int n, double L, const double *x, int F, double *y) 
     }
     double me[4][4];
     memset(me, 0, sizeof(me));
-    for (int qx = 0; qx < 2; ++qx)
+    if (p1) {
+        /* corners in cell order (0,0), (1,0), (0,1), (1,1); triangles
+         * {0, 1, 3} and {0, 3, 2} */
+        const int tv[2][3] = {{0, 1, 3}, {0, 3, 2}};
+        for (int e = 0; e < 2; ++e)
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) me[tv[e][a]][tv[e][b]] += (0.5 * h * h / 12.0) * (a == b ? 2.0 : 1.0);
+    } else for (int qx = 0; qx < 2; ++qx)
         for (int qy = 0; qy < 2; ++qy) {
             double s = g[qx], t = g[qy];
             double sh[4] = {(1 - s) * (1 - t), s * (1 - t), (1 - s) * t, s * t};
@@ -221,7 +247,7 @@ int or_mass_solve_direct(int dim, int n, double L, const double *b, int F, doubl
 /* Plain FP64 conjugate gradients on or_mass_apply; used to cross-check the
  * direct solve. Stops when ||b - M x|| <= rtol ||b||. */
 int or_mass_solve_cg(int dim, int n, double L, const double *b, int F, double *x, const double *x0,
-                     double rtol, int max_iter, int *iters, double *rel_resid) {
+                     double rtol, int max_iter, int *iters, double *rel_resid, int p1) {
     ll nn = dim == 1 ? n : (ll)n * n;
     double *r = malloc(sizeof(double) * nn * 3);
     if (!r) return OR_ENOMEM;
@@ -230,13 +256,13 @@ int or_mass_solve_cg(int dim, int n, double L, const double *b, int F, double *x
         const double *bf = b + f * nn;
         double *xf = x + f * nn;
         for (ll i = 0; i < nn; ++i) xf[i] = x0 ? x0[f * nn + i] : 0.0;
-        or_mass_apply(dim, n, L, xf, 1, q);
+        or_mass_apply(dim, n, L, xf, 1, q, p1);
         double bb = 0, rr = 0;
         for (ll i = 0; i < nn; ++i) { r[i] = bf[i] - q[i]; p[i] = r[i]; bb += bf[i] * bf[i]; rr += r[i] * r[i]; }
         int it = 0;
         if (bb == 0.0) { for (ll i = 0; i < nn; ++i) xf[i] = 0.0; rr = 0.0; bb = 1.0; }
         while (it < max_iter && sqrt(rr) > rtol * sqrt(bb)) {
-            or_mass_apply(dim, n, L, p, 1, q);
+            or_mass_apply(dim, n, L, p, 1, q, p1);
             double pq = 0;
             for (ll i = 0; i < nn; ++i) pq += p[i] * q[i];
             double alpha = rr / pq, rr2 = 0;
@@ -246,7 +272,7 @@ int or_mass_solve_cg(int dim, int n, double L, const double *b, int F, double *x
             for (ll i = 0; i < nn; ++i) p[i] = r[i] + beta * p[i];
             ++it;
         }
-        or_mass_apply(dim, n, L, xf, 1, q);
+        or_mass_apply(dim, n, L, xf, 1, q, p1);
         double tr = 0;
         for (ll i = 0; i < nn; ++i) tr += (bf[i] - q[i]) * (bf[i] - q[i]);
         if (iters) iters[f] = it;
@@ -259,7 +285,7 @@ int or_mass_solve_cg(int dim, int n, double L, const double *b, int F, double *x
 /* G2P (Sec. 2.2, Eq. delta2): Abb_mu = sum_i Ab_i psi_i(r_mu). Only the nodes
  * of the particle's cell have psi_i(r_mu) != 0. */
 int or_interpolate(int dim, int n, double L, const double *mesh, int F, const float *px,
-                   const float *py, ll np, double *out) {
+                   const float *py, ll np, double *out, int p1) {
     ll nn = dim == 1 ? n : (ll)n * n;
     for (ll k = 0; k < np; ++k) {
         uint32_t X, Y = 0;
@@ -273,10 +299,12 @@ int or_interpolate(int dim, int n, double L, const double *mesh, int F, const fl
             int cy = cell_of(Y, n);
             double t = frac_of(Y, n);
             int x1 = wrapi(cx + 1, n), y1 = wrapi(cy + 1, n);
+            double w[4];
+            cell_hats(p1, s, t, w);
             for (int f = 0; f < F; ++f) {
                 const double *m = mesh + f * nn;
-                out[f * np + k] = m[(ll)cy * n + cx] * (1 - s) * (1 - t) + m[(ll)cy * n + x1] * s * (1 - t) +
-                                  m[(ll)y1 * n + cx] * (1 - s) * t + m[(ll)y1 * n + x1] * s * t;
+                out[f * np + k] = m[(ll)cy * n + cx] * w[0] + m[(ll)cy * n + x1] * w[1] +
+                                  m[(ll)y1 * n + cx] * w[2] + m[(ll)y1 * n + x1] * w[3];
             }
         }
     }
@@ -359,7 +387,7 @@ int or1_delta(int n, double L, const float *px, ll np, const double *vals, int F
 /* FLIP (Sec. 2.3, Eqs. PIC and FLIP_vol) with particle volumes v (caller
  * computed, Eq. part_v). Nodes with no particle in their support get 0. */
 int or_flip(int dim, int n, double L, const float *px, const float *py, ll np, const double *vals, int F,
-            const double *v, double *mesh, double *node_vol, ll *empty) {
+            const double *v, double *mesh, double *node_vol, ll *empty, int p1) {
     ll nn = dim == 1 ? n : (ll)n * n;
     double *num = calloc((size_t)(nn * F + nn), sizeof(double));
     if (!num) return OR_ENOMEM;
@@ -379,7 +407,8 @@ int or_flip(int dim, int n, double L, const float *px, const float *py, ll np, c
             double t = frac_of(Y, n);
             int x1 = wrapi(cx + 1, n), y1 = wrapi(cy + 1, n);
             nd[0] = (ll)cy * n + cx; nd[1] = (ll)cy * n + x1; nd[2] = (ll)y1 * n + cx; nd[3] = (ll)y1 * n + x1;
-            w[0] = (1 - s) * (1 - t); w[1] = s * (1 - t); w[2] = (1 - s) * t; w[3] = s * t; m = 4;
+            cell_hats(p1, s, t, w);
+            m = 4;
         }
         for (int a = 0; a < m; ++a) {
             den[nd[a]] += v[k] * w[a];
@@ -784,12 +813,15 @@ double or_tri_monomial(const double *x, const double *y, int a, int b) {
  * clipped polygon is exact. mode 1 (App. B analogue for bilinear cells): A is
  * sampled on the 3x3 points of every cell (corners, edge midpoints, centre),
  * replaced by its biquadratic interpolant, and the overlap integrals of that
- * interpolant with the four bilinear hats are taken exactly. */
+ * interpolant with the four bilinear hats are taken exactly.
+ * P1 mesh (p1 = 1, mode 0 only): every clipped polygon is cut again by the
+ * cell's diagonal, so that the hats are linear on each part (degree 2). */
 int or2_rhs(int n, double L, const float *px, const float *py, ll np, const double *vals, int F,
-            const ll *tri, const int *off, ll ntri, int mode, double *b) {
+            const ll *tri, const int *off, ll ntri, int mode, double *b, int p1) {
     const ll nn = (ll)n * n;
     const double h = L / n;
     for (ll i = 0; i < nn * F; ++i) b[i] = 0.0;
+    if (mode == 1 && p1) return OR_EINVAL;
     if (mode == 1) {
         ll n2 = (ll)2 * n;
         double *A2 = malloc(sizeof(double) * n2 * n2 * F);
@@ -833,21 +865,30 @@ int or2_rhs(int n, double L, const float *px, const float *py, ll np, const doub
                 if (m < 3) continue;
                 ll nd[4] = {(ll)wrapi(cy, n) * n + wrapi(cx, n), (ll)wrapi(cy, n) * n + wrapi(cx + 1, n),
                             (ll)wrapi(cy + 1, n) * n + wrapi(cx, n), (ll)wrapi(cy + 1, n) * n + wrapi(cx + 1, n)};
-                for (int k = 1; k + 1 < m; ++k) {
-                    double fx[3] = {ax[0], ax[k], ax[k + 1]}, fy[3] = {ay[0], ay[k], ay[k + 1]};
-                    double area = 0.5 * fabs((fx[1] - fx[0]) * (fy[2] - fy[0]) - (fx[2] - fx[0]) * (fy[1] - fy[0]));
-                    for (int q = 0; q < 4; ++q) {
-                        double qx = HMS_L[q][0] * fx[0] + HMS_L[q][1] * fx[1] + HMS_L[q][2] * fx[2];
-                        double qy = HMS_L[q][0] * fy[0] + HMS_L[q][1] * fy[1] + HMS_L[q][2] * fy[2];
-                        double l[3];
-                        bary(x, y, qx, qy, l);
-                        double s = (qx - cx * h) / h, tt = (qy - cy * h) / h;
-                        double psi[4] = {(1 - s) * (1 - tt), s * (1 - tt), (1 - s) * tt, s * tt};
-                        double w = area * HMS_W[q];
-                        for (int f = 0; f < F; ++f) {
-                            const double *vf = vals + f * np;
-                            double A = l[0] * vf[tri[3 * t]] + l[1] * vf[tri[3 * t + 1]] + l[2] * vf[tri[3 * t + 2]];
-                            for (int c = 0; c < 4; ++c) b[f * nn + nd[c]] += w * A * psi[c];
+                for (int half = 0; half < (p1 ? 2 : 1); ++half) {
+                    double hx[16], hy[16];
+                    int mh = m;
+                    if (p1)  /* half 0: s >= t, half 1: s <= t */
+                        mh = half == 0 ? clip_half(ax, ay, m, -1, 1, (double)(cy - cx) * h, hx, hy)
+                                       : clip_half(ax, ay, m, 1, -1, (double)(cx - cy) * h, hx, hy);
+                    else
+                        for (int k = 0; k < m; ++k) { hx[k] = ax[k]; hy[k] = ay[k]; }
+                    for (int k = 1; k + 1 < mh; ++k) {
+                        double fx[3] = {hx[0], hx[k], hx[k + 1]}, fy[3] = {hy[0], hy[k], hy[k + 1]};
+                        double area = 0.5 * fabs((fx[1] - fx[0]) * (fy[2] - fy[0]) - (fx[2] - fx[0]) * (fy[1] - fy[0]));
+                        for (int q = 0; q < 4; ++q) {
+                            double qx = HMS_L[q][0] * fx[0] + HMS_L[q][1] * fx[1] + HMS_L[q][2] * fx[2];
+                            double qy = HMS_L[q][0] * fy[0] + HMS_L[q][1] * fy[1] + HMS_L[q][2] * fy[2];
+                            double l[3];
+                            bary(x, y, qx, qy, l);
+                            double psi[4];
+                            cell_hats(p1, (qx - cx * h) / h, (qy - cy * h) / h, psi);
+                            double w = area * HMS_W[q];
+                                for (int f = 0; f < F; ++f) {
+                                    const double *vf = vals + f * np;
+                                    double A = l[0] * vf[tri[3 * t]] + l[1] * vf[tri[3 * t + 1]] + l[2] * vf[tri[3 * t + 2]];
+                                    for (int c = 0; c < 4; ++c) b[f * nn + nd[c]] += w * A * psi[c];
+                                }
                         }
                     }
                 }
@@ -911,9 +952,10 @@ int or1_g2p_int(int n, double L, const float *px, ll np, const double *mesh, int
 
 /* 2D: c_mu by clipping every particle triangle against every cell and
  * integrating Ab psi_mu (bilinear x linear, degree 3) with the
- * Hammer-Marlowe-Stroud rule on a fan of each clipped polygon. */
+ * Hammer-Marlowe-Stroud rule on a fan of each clipped polygon. P1 mesh
+ * (p1 = 1): every clipped polygon is cut again by the cell's diagonal. */
 int or2_g2p_int(int n, double L, const float *px, const float *py, ll np, const double *mesh, int F,
-                const ll *tri, const int *off, ll ntri, double *c) {
+                const ll *tri, const int *off, ll ntri, double *c, int p1) {
     const ll nn = (ll)n * n;
     const double h = L / n;
     for (ll i = 0; i < (ll)F * np; ++i) c[i] = 0.0;
@@ -938,21 +980,30 @@ int or2_g2p_int(int n, double L, const float *px, const float *py, ll np, const 
                 if (m < 3) continue;
                 ll nd[4] = {(ll)wrapi(cy, n) * n + wrapi(cx, n), (ll)wrapi(cy, n) * n + wrapi(cx + 1, n),
                             (ll)wrapi(cy + 1, n) * n + wrapi(cx, n), (ll)wrapi(cy + 1, n) * n + wrapi(cx + 1, n)};
-                for (int k = 1; k + 1 < m; ++k) {
-                    double fx[3] = {ax[0], ax[k], ax[k + 1]}, fy[3] = {ay[0], ay[k], ay[k + 1]};
-                    double area = 0.5 * fabs((fx[1] - fx[0]) * (fy[2] - fy[0]) - (fx[2] - fx[0]) * (fy[1] - fy[0]));
-                    for (int q = 0; q < 4; ++q) {
-                        double qx = HMS_L[q][0] * fx[0] + HMS_L[q][1] * fx[1] + HMS_L[q][2] * fx[2];
-                        double qy = HMS_L[q][0] * fy[0] + HMS_L[q][1] * fy[1] + HMS_L[q][2] * fy[2];
-                        double l[3];
-                        bary(x, y, qx, qy, l);
-                        double s = (qx - cx * h) / h, tt = (qy - cy * h) / h;
-                        double psi[4] = {(1 - s) * (1 - tt), s * (1 - tt), (1 - s) * tt, s * tt};
-                        double w = area * HMS_W[q];
-                        for (int f = 0; f < F; ++f) {
-                            double Ab = 0;
-                            for (int cc = 0; cc < 4; ++cc) Ab += mesh[f * nn + nd[cc]] * psi[cc];
-                            for (int k2 = 0; k2 < 3; ++k2) c[f * np + tri[3 * t + k2]] += w * Ab * l[k2];
+                for (int half = 0; half < (p1 ? 2 : 1); ++half) {
+                    double hx[16], hy[16];
+                    int mh = m;
+                    if (p1)  /* half 0: s >= t, half 1: s <= t */
+                        mh = half == 0 ? clip_half(ax, ay, m, -1, 1, (double)(cy - cx) * h, hx, hy)
+                                       : clip_half(ax, ay, m, 1, -1, (double)(cx - cy) * h, hx, hy);
+                    else
+                        for (int k = 0; k < m; ++k) { hx[k] = ax[k]; hy[k] = ay[k]; }
+                    for (int k = 1; k + 1 < mh; ++k) {
+                        double fx[3] = {hx[0], hx[k], hx[k + 1]}, fy[3] = {hy[0], hy[k], hy[k + 1]};
+                        double area = 0.5 * fabs((fx[1] - fx[0]) * (fy[2] - fy[0]) - (fx[2] - fx[0]) * (fy[1] - fy[0]));
+                        for (int q = 0; q < 4; ++q) {
+                            double qx = HMS_L[q][0] * fx[0] + HMS_L[q][1] * fx[1] + HMS_L[q][2] * fx[2];
+                            double qy = HMS_L[q][0] * fy[0] + HMS_L[q][1] * fy[1] + HMS_L[q][2] * fy[2];
+                            double l[3];
+                            bary(x, y, qx, qy, l);
+                            double psi[4];
+                            cell_hats(p1, (qx - cx * h) / h, (qy - cy * h) / h, psi);
+                            double w = area * HMS_W[q];
+                                for (int f = 0; f < F; ++f) {
+                                    double Ab = 0;
+                                    for (int cc = 0; cc < 4; ++cc) Ab += mesh[f * nn + nd[cc]] * psi[cc];
+                                    for (int k2 = 0; k2 < 3; ++k2) c[f * np + tri[3 * t + k2]] += w * Ab * l[k2];
+                                }
                         }
                     }
                 }
