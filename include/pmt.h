@@ -106,9 +106,25 @@ typedef struct pm_solve_info {
 /* Create a context for one periodic mesh (dim 1 or 2, n >= 4 nodes per side,
  * box length L > 0) able to take up to max_particles particles and max_fields
  * fields per call. stream is a cudaStream_t (NULL = legacy default stream).
- * Allocates all device workspace now. *out is set only on success. */
+ * Allocates all device workspace now. *out is set only on success. The mesh
+ * functions are linear (1D) / bilinear (2D), as pm_ctx_create_mesh with
+ * PM_MESH_Q1. */
 pm_status pm_ctx_create(pm_ctx **out, int dim, int n, double L, long long max_particles, int max_fields,
                         void *stream);
+
+/* Mesh functions psi_i of a 2D context (Sec. 3.2 uses linear FE functions on
+ * a triangulation of the node grid). PM_MESH_Q1: bilinear on the square cells
+ * (mass matrix (h^2/36)[1 4 1; 4 16 4; 1 4 1]). PM_MESH_P1: every cell split
+ * by its diagonal from node (i, j) to (i+1, j+1), hats linear on the
+ * triangles (mass matrix (h^2/12) times 6 at the node and 1 at its six
+ * neighbours (i+-1, j), (i, j+-1), (i+1, j+1), (i-1, j-1)). G2P, FLIP, the
+ * exact right-hand side, the mesh solve and the mesh -> particle integrals
+ * follow the kind; delta does not depend on it. PM_RHS_APPB, PM_WS_DIRECT and
+ * the network start exist for PM_MESH_Q1 only (PM_EINVAL otherwise). In 1D
+ * both kinds are the linear hats. */
+enum { PM_MESH_Q1 = 0, PM_MESH_P1 = 1 };
+pm_status pm_ctx_create_mesh(pm_ctx **out, int dim, int n, double L, long long max_particles, int max_fields,
+                             int mesh_kind, void *stream);
 void pm_ctx_destroy(pm_ctx *ctx);
 pm_status pm_ctx_set_stream(pm_ctx *ctx, void *stream);
 /* Wait for the context's stream; return the device status word and clear it. */

@@ -21,12 +21,14 @@ _lib = None
 
 PM_WS_DELTA, PM_WS_ZERO, PM_WS_USER, PM_WS_NET, PM_WS_DIRECT = 0, 1, 2, 3, 4
 PM_RHS_EXACT, PM_RHS_APPB = 0, 1
+PM_MESH_Q1, PM_MESH_P1 = 0, 1
+MESH_KINDS = {"q1": PM_MESH_Q1, "p1": PM_MESH_P1}
 RHS_MODES = {"exact": PM_RHS_EXACT, "appb": PM_RHS_APPB}
 _STATUS = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ENOTCONV", 4: "PM_ETIMEOUT", 5: "PM_EDEGENERATE",
            6: "PM_ECUDA"}
 
 EXPORTS = [
-    "pm_ctx_create", "pm_ctx_destroy", "pm_ctx_set_stream", "pm_sync", "pm_last_error", "pm_ctx_workspace_bytes",
+    "pm_ctx_create", "pm_ctx_create_mesh", "pm_ctx_destroy", "pm_ctx_set_stream", "pm_sync", "pm_last_error", "pm_ctx_workspace_bytes",
     "pm_interpolate", "pm_interpolate_lumped", "pm_interpolate_mass", "pm_assign_lumped", "pm_assign_delta", "pm_assign_flip", "pm_assign_mass", "pm_mass_rhs", "pm_mass_rhs_mode", "pm_mass_apply",
     "pm_mass_solve", "pm_particle_volumes", "pm_triangulate", "pm_sort", "pm_advect_shift", "pm_advect_rotate",
     "pm_advect_rk2", "pm_profile", "pm_profile_read", "pm_work_read", "pm_phase_name", "pm_kernel_launches",
@@ -80,6 +82,7 @@ def load_library(path: str | None = None):
     vp, ll, i, d = ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int, ctypes.c_double
     sig = {
         "pm_ctx_create": [ctypes.POINTER(vp), i, i, d, ll, i, vp],
+        "pm_ctx_create_mesh": [ctypes.POINTER(vp), i, i, d, ll, i, i, vp],
         "pm_ctx_destroy": [vp],
         "pm_ctx_set_stream": [vp, vp],
         "pm_sync": [vp],
@@ -152,9 +155,12 @@ def _ptr(t):
 
 class Context:
     """One periodic mesh (dim 1 or 2, n nodes per side, box length L) with
-    workspace for up to max_particles particles and max_fields fields."""
+    workspace for up to max_particles particles and max_fields fields; mesh
+    functions "q1" (bilinear) or "p1" (linear on cells split by the (0,0)-(1,1)
+    diagonal), pm_ctx_create_mesh."""
 
-    def __init__(self, dim: int, n: int, L: float, max_particles: int, max_fields: int = 1, device=None):
+    def __init__(self, dim: int, n: int, L: float, max_particles: int, max_fields: int = 1, device=None,
+                 mesh: str = "q1"):
         import torch
 
         if not torch.cuda.is_available():
@@ -167,8 +173,8 @@ class Context:
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             st = torch.cuda.current_stream().cuda_stream
-            s = self.lib.pm_ctx_create(ctypes.byref(h), dim, n, ctypes.c_double(L), max_particles, max_fields,
-                                       ctypes.c_void_p(st))
+            s = self.lib.pm_ctx_create_mesh(ctypes.byref(h), dim, n, ctypes.c_double(L), max_particles, max_fields,
+                                            MESH_KINDS[mesh], ctypes.c_void_p(st))
         if s != 0:
             raise PMError(s, "pm_ctx_create failed")
         self.h = h

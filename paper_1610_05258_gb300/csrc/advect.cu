@@ -61,7 +61,8 @@ __global__ void __launch_bounds__(256) k_rk2(Geo g, const float *__restrict__ me
         float t = frac_f(Y, n);
         int y1 = cy + 1 == n ? 0 : cy + 1;
         const ll i00 = (ll)cy * n + cx, i10 = (ll)cy * n + x1, i01 = (ll)y1 * n + cx, i11 = (ll)y1 * n + x1;
-        const float w00 = (1.0f - s) * (1.0f - t), w10 = s * (1.0f - t), w01 = (1.0f - s) * t, w11 = s * t;
+        float w00, w10, w01, w11;
+        cell_weights(g.p1 != 0, s, t, w00, w10, w01, w11);
         const float *mu = mesh, *mv = mesh + g.ncell;
         um = w00 * __ldg(mu + i00) + w10 * __ldg(mu + i10) + w01 * __ldg(mu + i01) + w11 * __ldg(mu + i11);
         vm = w00 * __ldg(mv + i00) + w10 * __ldg(mv + i10) + w01 * __ldg(mv + i01) + w11 * __ldg(mv + i11);

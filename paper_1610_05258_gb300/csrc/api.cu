@@ -169,10 +169,15 @@ extern "C" {
 
 pm_status pm_ctx_create(pm_ctx **out, int dim, int n, double L, long long max_particles, int max_fields,
                         void *stream) {
+    return pm_ctx_create_mesh(out, dim, n, L, max_particles, max_fields, PM_MESH_Q1, stream);
+}
+
+pm_status pm_ctx_create_mesh(pm_ctx **out, int dim, int n, double L, long long max_particles, int max_fields,
+                             int mesh_kind, void *stream) {
     if (!out) return PM_EINVAL;
     *out = nullptr;
     if ((dim != 1 && dim != 2) || n < 4 || !(L > 0.0) || max_particles < 0 || max_fields < 1 ||
-        max_fields > PM_MAXF)
+        max_fields > PM_MAXF || (mesh_kind != PM_MESH_Q1 && mesh_kind != PM_MESH_P1))
         return PM_EINVAL;
     if (max_particles >= (1LL << 28) - 16) return PM_EINVAL;  // star entries: 28-bit index, top 16 reserved
     if (dim == 2 && (ll)n * n > (1LL << 30)) return PM_EINVAL;
@@ -187,6 +192,7 @@ pm_status pm_ctx_create(pm_ctx **out, int dim, int n, double L, long long max_pa
     g.invL = (float)(1.0 / L);
     g.h = (float)(L / n);
     g.ncell = dim == 1 ? n : (ll)n * n;
+    g.p1 = dim == 2 && mesh_kind == PM_MESH_P1 ? 1 : 0;
     Work &w = c->w;
     memset(&w, 0, sizeof(w));
     w.np_max = max_particles;
@@ -207,7 +213,7 @@ pm_status pm_ctx_create(pm_ctx **out, int dim, int n, double L, long long max_pa
               alloc(c, &w.pq, pcg_width((int)F) * np) && alloc(c, &w.prp, 2LL * pcg_width((int)F) * np);
     w.cfix = (ll *)w.prp;
     if (ok && dim == 2) ok = alloc(c, &w.nbr, (ll)PM_MAXDEG * np) && alloc(c, &w.pcoef, (ll)PM_MAXDEG * np);
-    if (ok && dim == 2 && n % 128 == 0)
+    if (ok && dim == 2 && n % 128 == 0 && !g.p1)  // the network start: bilinear meshes
         ok = alloc(c, &w.feat, 2 * F * nc) && alloc(c, &w.corr, F * nc);
     if (ok && cudaMallocHost((void **)&w.hstatus, sizeof(int)) != cudaSuccess) ok = false;
     if (!ok) {
@@ -404,8 +410,10 @@ pm_status pm_assign_mass(pm_ctx *c, const float *px, const float *py, long long 
     default_opts(opts, o);
     if (o.warm_start < PM_WS_DELTA || o.warm_start > PM_WS_DIRECT) return fail(c, PM_EINVAL, "unknown warm start");
     if (o.rhs_mode != PM_RHS_EXACT && o.rhs_mode != PM_RHS_APPB) return fail(c, PM_EINVAL, "unknown rhs_mode");
+    if (c->g.p1 && (o.rhs_mode == PM_RHS_APPB || o.warm_start == PM_WS_DIRECT))
+        return fail(c, PM_EINVAL, "PM_RHS_APPB and PM_WS_DIRECT need the bilinear mesh");
     if (o.warm_start == PM_WS_USER && !o.x0) return fail(c, PM_EINVAL, "PM_WS_USER without x0");
-    if (o.warm_start == PM_WS_NET && (!o.net || !c->w.feat)) return fail(c, PM_EINVAL, "PM_WS_NET needs a network and a 2D mesh with n % 128 == 0");
+    if (o.warm_start == PM_WS_NET && (!o.net || !c->w.feat)) return fail(c, PM_EINVAL, "PM_WS_NET needs a network and a 2D bilinear mesh with n % 128 == 0");
     bool start = true;
     if ((s = mass_front(c, px, py, np, vals, F, mesh_out, o, start))) return s;
     if ((s = mass_solve_launch(c, F, mesh_out, start, o))) return s;
@@ -486,6 +494,7 @@ pm_status pm_mass_rhs_mode(pm_ctx *c, const float *px, const float *py, long lon
     if (s) return s;
     if (F < 1 || !b_out) return fail(c, PM_EINVAL, "null output or no field");
     if (rhs_mode != PM_RHS_EXACT && rhs_mode != PM_RHS_APPB) return fail(c, PM_EINVAL, "unknown rhs_mode");
+    if (c->g.p1 && rhs_mode == PM_RHS_APPB) return fail(c, PM_EINVAL, "PM_RHS_APPB needs the bilinear mesh");
     if ((s = prepare(c, px, py, np, vals, F, true))) return s;
     {
         Phase ph(c, PM_PH_RHS);
@@ -523,6 +532,7 @@ pm_status pm_mass_solve(pm_ctx *c, const float *b, int F, float *x, const pm_sol
         start = true;
     } else if (o.warm_start == PM_WS_DIRECT) {
         if (b == x) return fail(c, PM_EINVAL, "PM_WS_DIRECT needs distinct b and x");
+        if (c->g.p1) return fail(c, PM_EINVAL, "PM_WS_DIRECT needs the bilinear mesh");
         launch_mass_direct(c->g, b, F, x, c->w.r, c->st);
         start = true;
     }

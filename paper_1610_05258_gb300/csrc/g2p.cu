@@ -1,6 +1,6 @@
 // Mesh -> particle interpolation, Sec. 2.2 Eq. delta2:
 //   Abb_mu = sum_i Ab_i psi_i(r_mu),
-// psi_i linear (1D) / bilinear (2D). Only the 2^dim nodes of the particle's
+// psi_i linear (1D) / bilinear or P1 on split cells (2D). Only the 2^dim nodes of the particle's
 // cell contribute. One thread per particle in caller order: positions and
 // outputs stream coalesced; the mesh (a few MB to tens of MB per field) is
 // read through L1/L2, where the four corner loads of neighbouring particles
@@ -39,7 +39,8 @@ __global__ void __launch_bounds__(256) k_g2p(Geo g, const float *__restrict__ me
     float t = frac_f(Y, n);
     int y1 = cy + 1 == n ? 0 : cy + 1;
     const ll i00 = (ll)cy * n + cx, i10 = (ll)cy * n + x1, i01 = (ll)y1 * n + cx, i11 = (ll)y1 * n + x1;
-    const float w00 = (1.0f - s) * (1.0f - t), w10 = s * (1.0f - t), w01 = (1.0f - s) * t, w11 = s * t;
+    float w00, w10, w01, w11;
+    cell_weights(g.p1 != 0, s, t, w00, w10, w01, w11);
     const ll nn = g.ncell;
     for (int f = 0; f < F; ++f) {
         const float *m = mesh + (ll)f * nn;

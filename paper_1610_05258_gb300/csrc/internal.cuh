@@ -34,7 +34,32 @@ struct Geo {
     float invL;    // fl32(1/L), defines the torus coordinate
     float h;       // fl32(L/n)
     ll ncell;      // n^dim
+    int p1;        // 2D mesh functions: 0 bilinear, 1 P1 on cells split by the (0,0)-(1,1) diagonal
 };
+
+// The four mesh functions non-zero on a 2D cell at local (s, t), corner order
+// (0,0), (1,0), (0,1), (1,1): bilinear, or P1 on the triangles s >= t and
+// s <= t of the cell's (0,0)-(1,1) diagonal (barycentric coordinates of their
+// corners; the fourth corner's hat is zero there).
+__device__ __forceinline__ void cell_weights(bool p1, float s, float t, float &w00, float &w10, float &w01,
+                                             float &w11) {
+    if (!p1) {
+        w00 = (1.0f - s) * (1.0f - t);
+        w10 = s * (1.0f - t);
+        w01 = (1.0f - s) * t;
+        w11 = s * t;
+    } else if (s >= t) {
+        w00 = 1.0f - s;
+        w10 = s - t;
+        w01 = 0.0f;
+        w11 = t;
+    } else {
+        w00 = 1.0f - t;
+        w10 = 0.0f;
+        w01 = t - s;
+        w11 = s;
+    }
+}
 
 // Device workspace of a context (all sized at creation).
 struct Work {

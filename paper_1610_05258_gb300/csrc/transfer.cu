@@ -181,10 +181,7 @@ __global__ void __launch_bounds__(128) k_flip_cells(Geo g, ll np, const int *__r
         float w[NC];
         if (DIM == 2) {
             float ty = frac_f(X.y, g.n);
-            w[0] = (1.0f - sx) * (1.0f - ty);
-            w[1] = sx * (1.0f - ty);
-            w[NC - 2] = (1.0f - sx) * ty;
-            w[NC - 1] = sx * ty;
+            cell_weights(g.p1 != 0, sx, ty, w[0], w[1], w[NC - 2], w[NC - 1]);
         } else {
             w[0] = 1.0f - sx;
             w[1] = sx;
@@ -315,6 +312,108 @@ __device__ __forceinline__ Mom tri_cell_moments(const float tx[3], const float t
     return M;
 }
 
+// Moments of (triangle T) intersected with the lower half of the unit cell
+// (s >= t: the triangle (0,0), (1,0), (1,1) of the P1 split), relative to
+// (ox, oy); T counter-clockwise in cell coordinates. As for the cell: T's
+// edges inside the half plus the half's edges inside T. An edge of T on a
+// line of the half's boundary is left to the half's edge; when T lies on the
+// far side of the diagonal with an edge on it, the intersection is a segment
+// and the moments are zero.
+__device__ __forceinline__ Mom tri_lower_moments(const float tx[3], const float ty[3], float ox, float oy) {
+    Mom M;
+    float ex[3], ey[3], rx[3], ry[3], rd[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int k1 = k == 2 ? 0 : k + 1;
+        ex[k] = tx[k1] - tx[k];
+        ey[k] = ty[k1] - ty[k];
+        rx[k] = __frcp_rn(ex[k]);
+        ry[k] = __frcp_rn(ey[k]);
+        rd[k] = __frcp_rn(ex[k] - ey[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int k1 = k == 2 ? 0 : k + 1, k2 = k == 0 ? 2 : k - 1;
+        if (tx[k] == ty[k] && tx[k1] == ty[k1] && tx[k2] < ty[k2]) return M;
+    }
+    for (int k = 0; k < 3; ++k) {
+        const float px = tx[k], py = ty[k], dx = ex[k], dy = ey[k];
+        if ((dy == 0.0f && py == 0.0f) || (dx == 0.0f && px == 1.0f) || (dx == dy && px == py)) continue;
+        float t0 = 0.0f, t1 = 1.0f;
+        // y >= 0, x <= 1, x - y >= 0
+        if (!lb(-dy, py, -ry[k], t0, t1) || !lb(dx, 1.0f - px, rx[k], t0, t1) ||
+            !lb(dy - dx, px - py, -rd[k], t0, t1))
+            continue;
+        if (!(t0 < t1)) continue;
+        M.seg(px + t0 * dx - ox, py + t0 * dy - oy, px + t1 * dx - ox, py + t1 * dy - oy);
+    }
+    // the half's edges (0,0)->(1,0), (1,0)->(1,1), (1,1)->(0,0)
+    const float hxs[4] = {0.0f, 1.0f, 1.0f, 0.0f}, hys[4] = {0.0f, 0.0f, 1.0f, 0.0f};
+    for (int e = 0; e < 3; ++e) {
+        const float ux = hxs[e], uy = hys[e], vx = hxs[e + 1], vy = hys[e + 1];
+        float t0 = 0.0f, t1 = 1.0f;
+        bool ok = true;
+        for (int k = 0; k < 3 && ok; ++k) {
+            const float q0 = ex[k] * (uy - ty[k]) - ey[k] * (ux - tx[k]);
+            // directions (1,0), (0,1), (-1,-1): dq = -ey, ex, ey - ex
+            const float dq = e == 0 ? -ey[k] : (e == 1 ? ex[k] : ey[k] - ex[k]);
+            const float rdq = e == 0 ? -ry[k] : (e == 1 ? rx[k] : -rd[k]);
+            ok = lb(-dq, q0, -rdq, t0, t1);
+        }
+        if (!ok || !(t0 < t1)) continue;
+        M.seg(ux + t0 * (vx - ux) - ox, uy + t0 * (vy - uy) - oy, ux + t1 * (vx - ux) - ox, uy + t1 * (vy - uy) - oy);
+    }
+    return M;
+}
+
+// Integrals K0 = int psi_c, K1 = int X psi_c, K2 = int Y psi_c of the four
+// corner functions over one piece, in local coordinates X = s - ox,
+// Y = t - oy. Bilinear: from the piece's moments up to degree 3. P1: on each
+// half of the split cell the three non-zero hats are affine, P + Q X + R Y,
+// so the moments up to degree 2 of the two halves suffice (the upper half's
+// are the piece's minus the lower half's).
+template <int P1>
+__device__ __forceinline__ void corner_integrals(const Mom &Mm, const float tx[3], const float ty[3], float ox,
+                                                 float oy, float K0[4], float K1[4], float K2[4]) {
+    const float M00 = Mm.a0 * 0.5f, M10 = Mm.a10 * (1.0f / 6.0f), M01 = Mm.a01 * (1.0f / 6.0f);
+    const float M20 = Mm.a20 * (1.0f / 12.0f), M11 = Mm.a11 * (1.0f / 24.0f);
+    const float M02 = Mm.a02 * (1.0f / 12.0f);
+    if (!P1) {
+        const float M21 = Mm.a21 * (1.0f / 60.0f), M12 = Mm.a12 * (1.0f / 60.0f);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float A1 = (c & 1) ? ox : 1.0f - ox, B1 = (c & 1) ? 1.0f : -1.0f;
+            const float A2 = (c & 2) ? oy : 1.0f - oy, B2 = (c & 2) ? 1.0f : -1.0f;
+            const float aa = A1 * A2, ab = A1 * B2, ba = B1 * A2, bb = B1 * B2;
+            K0[c] = aa * M00 + ab * M01 + ba * M10 + bb * M11;
+            K1[c] = aa * M10 + ab * M11 + ba * M20 + bb * M21;
+            K2[c] = aa * M01 + ab * M02 + ba * M11 + bb * M12;
+        }
+        return;
+    }
+    const Mom Ml = tri_lower_moments(tx, ty, ox, oy);
+    const float L00 = Ml.a0 * 0.5f, L10 = Ml.a10 * (1.0f / 6.0f), L01 = Ml.a01 * (1.0f / 6.0f);
+    const float L20 = Ml.a20 * (1.0f / 12.0f), L11 = Ml.a11 * (1.0f / 24.0f), L02 = Ml.a02 * (1.0f / 12.0f);
+    const float U00 = M00 - L00, U10 = M10 - L10, U01 = M01 - L01;
+    const float U20 = M20 - L20, U11 = M11 - L11, U02 = M02 - L02;
+    // lower half: (0,0): 1 - s; (1,0): s - t; (1,1): t
+    // upper half: (0,0): 1 - t; (0,1): t - s; (1,1): s
+    const float pl0 = 1.0f - ox, pl1 = ox - oy, pl3 = oy;
+    const float pu0 = 1.0f - oy, pu2 = oy - ox, pu3 = ox;
+    K0[0] = pl0 * L00 - L10 + pu0 * U00 - U01;
+    K1[0] = pl0 * L10 - L20 + pu0 * U10 - U11;
+    K2[0] = pl0 * L01 - L11 + pu0 * U01 - U02;
+    K0[1] = pl1 * L00 + L10 - L01;
+    K1[1] = pl1 * L10 + L20 - L11;
+    K2[1] = pl1 * L01 + L11 - L02;
+    K0[2] = pu2 * U00 - U10 + U01;
+    K1[2] = pu2 * U10 - U20 + U11;
+    K2[2] = pu2 * U01 - U11 + U02;
+    K0[3] = pl3 * L00 + L01 + pu3 * U00 + U10;
+    K1[3] = pl3 * L10 + L11 + pu3 * U10 + U20;
+    K2[3] = pl3 * L01 + L02 + pu3 * U01 + U11;
+}
+
 #define RTS 16                      // cells per tile side
 #define RHALO 2                     // window halo in cells
 #define RWIN (RTS + 2 * RHALO + 1)  // window side in nodes
@@ -368,7 +467,7 @@ __device__ __forceinline__ void add64_split(unsigned *lo, unsigned *hi, ull v) {
 // 64-bit fixed-point sums cfix (global atomics; order-free integer sums).
 // maxabs then holds max|Ab| per field, and the fixed-point scale keeps 10
 // bits of headroom for particle volumes up to 1024 h^2.
-template <int FF, int MODE>
+template <int FF, int MODE, int P1>
 __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__restrict__ pos,
                                                const int *__restrict__ cell_start, const int *__restrict__ nbr,
                                                const unsigned char *__restrict__ deg, const float *__restrict__ vals,
@@ -494,10 +593,8 @@ __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__rest
             const float oy = 0.5f * (fmaxf(0.0f, ymin - fcj) + fminf(1.0f, ymax - fcj));
             Mom Mm = tri_cell_moments(tx, ty, ox, oy);
             if (!(Mm.a0 > 0.0f)) continue;
-            const float M00 = Mm.a0 * 0.5f, M10 = Mm.a10 * (1.0f / 6.0f), M01 = Mm.a01 * (1.0f / 6.0f);
-            const float M20 = Mm.a20 * (1.0f / 12.0f), M11 = Mm.a11 * (1.0f / 24.0f);
-            const float M02 = Mm.a02 * (1.0f / 12.0f), M21 = Mm.a21 * (1.0f / 60.0f);
-            const float M12 = Mm.a12 * (1.0f / 60.0f);
+            float K0[4], K1[4], K2[4];
+            corner_integrals<P1>(Mm, tx, ty, ox, oy, K0, K1, K2);
             // A on the triangle: value at p plus gradient (cell units)
             const float e1x = T.vx[1] - T.vx[0], e1y = T.vy[1] - T.vy[0];
             const float e2x = T.vx[2] - T.vx[0], e2y = T.vy[2] - T.vy[0];
@@ -511,12 +608,6 @@ __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__rest
                 for (int f = 0; f < FF; ++f) W0[f] = W1[f] = W2[f] = 0.0f;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    const float A1 = (c & 1) ? ox : 1.0f - ox, B1 = (c & 1) ? 1.0f : -1.0f;
-                    const float A2 = (c & 2) ? oy : 1.0f - oy, B2 = (c & 2) ? 1.0f : -1.0f;
-                    const float aa = A1 * A2, ab = A1 * B2, ba = B1 * A2, bb = B1 * B2;
-                    const float K0 = aa * M00 + ab * M01 + ba * M10 + bb * M11;
-                    const float K1 = aa * M10 + ab * M11 + ba * M20 + bb * M21;
-                    const float K2 = aa * M01 + ab * M02 + ba * M11 + bb * M12;
                     const int nx = gcx + (c & 1), ny = gcy + ((c >> 1) & 1);
                     const ll node = (ll)wrapi(ny, n) * n + wrapi(nx, n);
                     PM_CHK(node >= 0 && node < g.ncell, 309, continue)
@@ -524,9 +615,9 @@ __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__rest
                     for (int f = 0; f < FF; ++f) {
                         if (f >= F) break;
                         const float ab_c = __ldg(mesh + (ll)f * g.ncell + node);
-                        W0[f] = fmaf(ab_c, K0, W0[f]);
-                        W1[f] = fmaf(ab_c, K1, W1[f]);
-                        W2[f] = fmaf(ab_c, K2, W2[f]);
+                        W0[f] = fmaf(ab_c, K0[c], W0[f]);
+                        W1[f] = fmaf(ab_c, K1[c], W1[f]);
+                        W2[f] = fmaf(ab_c, K2[c], W2[f]);
                     }
                 }
                 // barycentric functions about the local origin: lambda = l0 + lx X' + ly Y'
@@ -562,12 +653,6 @@ __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__rest
             }
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const float A1 = (c & 1) ? ox : 1.0f - ox, B1 = (c & 1) ? 1.0f : -1.0f;
-                const float A2 = (c & 2) ? oy : 1.0f - oy, B2 = (c & 2) ? 1.0f : -1.0f;
-                const float aa = A1 * A2, ab = A1 * B2, ba = B1 * A2, bb = B1 * B2;
-                const float K0 = aa * M00 + ab * M01 + ba * M10 + bb * M11;
-                const float K1 = aa * M10 + ab * M11 + ba * M20 + bb * M21;
-                const float K2 = aa * M01 + ab * M02 + ba * M11 + bb * M12;
                 const int nx = gcx + (c & 1), ny = gcy + ((c >> 1) & 1);
                 const int lx = nx - wx0, ly = ny - wy0;
                 const bool inwin = lx >= 0 && lx < RWIN && ly >= 0 && ly < RWIN;
@@ -576,7 +661,7 @@ __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__rest
 #pragma unroll
                 for (int f = 0; f < FF; ++f) {
                     if (f >= F) break;
-                    const float val = (al[f] * K0 + gx[f] * K1 + gy[f] * K2) * hd;
+                    const float val = (al[f] * K0[c] + gx[f] * K1[c] + gy[f] * K2[c]) * hd;
                     const ll iv = __float2ll_rn(ldexpf(val, E[f]));
                     if (!iv) continue;
                     if (inwin)
@@ -966,8 +1051,10 @@ static size_t rhs2d_smem() {
 // device (called when a context is created, outside any stream capture).
 template <int FF>
 static void rhs_attr() {
-    cudaFuncSetAttribute(k_rhs2d<FF, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs2d_smem<FF>());
-    cudaFuncSetAttribute(k_rhs2d<FF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs2d_smem<FF>());
+    cudaFuncSetAttribute(k_rhs2d<FF, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs2d_smem<FF>());
+    cudaFuncSetAttribute(k_rhs2d<FF, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs2d_smem<FF>());
+    cudaFuncSetAttribute(k_rhs2d<FF, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs2d_smem<FF>());
+    cudaFuncSetAttribute(k_rhs2d<FF, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs2d_smem<FF>());
 }
 
 void rhs_prepare_device() {
@@ -979,16 +1066,24 @@ void rhs_prepare_device() {
 template <int FF>
 static void launch_rhs2d(const Geo &g, Work &w, ll np, int F, int nt, int tx, cudaStream_t st) {
     const size_t bytes = rhs2d_smem<FF>();
-    k_rhs2d<FF, 0><<<nt, 256, bytes, st>>>(g, np, w.pos, w.cell_start, w.nbr, w.deg, w.vals, F, w.maxabs, w.bfix,
-                                           tx, nullptr, nullptr);
+    if (g.p1)
+        k_rhs2d<FF, 0, 1><<<nt, 256, bytes, st>>>(g, np, w.pos, w.cell_start, w.nbr, w.deg, w.vals, F, w.maxabs,
+                                                  w.bfix, tx, nullptr, nullptr);
+    else
+        k_rhs2d<FF, 0, 0><<<nt, 256, bytes, st>>>(g, np, w.pos, w.cell_start, w.nbr, w.deg, w.vals, F, w.maxabs,
+                                                  w.bfix, tx, nullptr, nullptr);
 }
 
 template <int FF>
 static void launch_g2pint2d(const Geo &g, Work &w, ll np, int F, const float *mesh, int nt, int tx,
                             cudaStream_t st) {
     const size_t bytes = rhs2d_smem<FF>();
-    k_rhs2d<FF, 1><<<nt, 256, bytes, st>>>(g, np, w.pos, w.cell_start, w.nbr, w.deg, nullptr, F, w.meshmax,
-                                           nullptr, tx, mesh, w.cfix);
+    if (g.p1)
+        k_rhs2d<FF, 1, 1><<<nt, 256, bytes, st>>>(g, np, w.pos, w.cell_start, w.nbr, w.deg, nullptr, F, w.meshmax,
+                                                  nullptr, tx, mesh, w.cfix);
+    else
+        k_rhs2d<FF, 1, 0><<<nt, 256, bytes, st>>>(g, np, w.pos, w.cell_start, w.nbr, w.deg, nullptr, F, w.meshmax,
+                                                  nullptr, tx, mesh, w.cfix);
 }
 
 void launch_rhs(const Geo &g, Work &w, ll np, int F, cudaStream_t st) {
