@@ -280,6 +280,19 @@ def run_mixture(args, pm, torch, dist, local):
                "d2h_bytes_per_step": bo, "ms_per_step": te}
 
     plain, learned, direct, appb = res["plain"], res["learned"], res["direct"], res["appb"]
+    # the same step with P1 mesh functions (cells split by the (0,0)-(1,1) diagonal)
+    ctx_p1 = pm.Context(2, n, L, N, F, device=dev, mesh="p1")
+    _, p1_info = ctx_p1.assign_mass(px, py, vals, out=out)
+    for _ in range(args.warmup):
+        ctx_p1.assign_mass(px, py, vals, out=out, info=False)
+    torch.cuda.synchronize()
+    ctx_p1.profile(True)
+    ctx_p1.profile_read(reset=True)
+    p1_ms = time_steps(torch, stream, flush, args.steps, lambda: ctx_p1.assign_mass(px, py, vals, out=out, info=False))
+    p1_prof = ctx_p1.profile_read(reset=True)
+    ctx_p1.profile(False)
+    p1_t = max_over_ranks(torch, dist, sum(p1_ms) / len(p1_ms), dev)
+    del ctx_p1
     # mesh -> particle projections of the assigned fields back onto the same
     # particles: full mass (Eq. proj2, CG to 1e-6) and lumped (Eq. lumped)
     mesh_fields = out.clone()
@@ -349,6 +362,11 @@ def run_mixture(args, pm, torch, dist, local):
                      "solve": solve_report(appb["info"]),
                      "what": "the same step with the App. B quadrature right-hand side (delta on the twice refined "
                              "mesh, 3x3 box sum) instead of the exact one; not conservative"},
+        "p1_mesh": {"value": args.world * N * F / (p1_t * 1e-3), "ms_per_step": p1_t,
+                    "phase_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in p1_prof.items() if v[0] > 0},
+                    "solve": solve_report(p1_info),
+                    "what": "the same step with P1 mesh functions on cells split by the (0,0)-(1,1) diagonal "
+                            "(7-point mass stencil) instead of bilinear ones"},
         "mesh_to_particle": {"what": "the step's mesh fields projected back onto the same particles; each entry is "
                                      "one call per step (full mass includes the sort and triangulation)",
                              **proj},
