@@ -34,13 +34,17 @@ __device__ __forceinline__ void rel_of(int e, uint2 Xp, const uint2 *__restrict_
     ry = (ll)Xq.y + (ll)oy * 4294967296LL - (ll)Xp.y;
 }
 
-// Fixed-point exponent of field f: |b_j| <= max|A| h^dim < 2^(60 - E).
+// Fixed-point exponent E of field f: |b_j| <= max|A| h^dim < 2^(60 - E).
+// Capped so that h^dim 2^E stays below 2^120 (a finite float scale; the cap
+// only binds for max|A| below about 2^-60, where it still leaves over 40
+// bits of the fixed point in use).
 __device__ __forceinline__ int fix_exp(const unsigned *maxabs, int f, float hd) {
     float m = __uint_as_float(maxabs[f]) * hd;
     if (!(m > 0.0f)) return 0;
-    int e;
+    int e, eh;
     frexpf(m, &e);
-    return 60 - e;
+    frexpf(hd, &eh);
+    return min(60 - e, 120 - eh);
 }
 
 // Sign of orient(U, V, Q) with Q perturbed by (eps, eps^2) (ties never zero).
@@ -468,7 +472,7 @@ __device__ __forceinline__ void add64_split(unsigned *lo, unsigned *hi, ull v) {
 // maxabs then holds max|Ab| per field, and the fixed-point scale keeps 10
 // bits of headroom for particle volumes up to 1024 h^2.
 template <int FF, int MODE, int P1>
-__global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__restrict__ pos,
+__global__ void __launch_bounds__(256, 4) k_rhs2d(Geo g, ll np, const uint2 *__restrict__ pos,
                                                const int *__restrict__ cell_start, const int *__restrict__ nbr,
                                                const unsigned char *__restrict__ deg, const float *__restrict__ vals,
                                                int F, const unsigned *__restrict__ maxabs, ll *__restrict__ bfix,
@@ -509,6 +513,10 @@ __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__rest
     const float sc = (float)n * 2.3283064365386963e-10f;
     int E[FF];
     for (int f = 0; f < FF; ++f) E[f] = f < F ? fix_exp(maxabs, f, hd) - (MODE == 1 ? 10 : 0) : 0;
+    // h^dim 2^E as one float factor: scaling by a power of two is exact, so
+    // round(x (h^dim 2^E)) equals round(x h^dim) 2^E
+    float S[FF];
+    for (int f = 0; f < FF; ++f) S[f] = ldexpf(hd, E[f]);
     const int total = rowpre[RTS];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int tcol = threadIdx.x;
@@ -631,8 +639,7 @@ __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__rest
 #pragma unroll
                     for (int f = 0; f < FF; ++f) {
                         if (f >= F) break;
-                        const float val = (L0[v] * W0[f] + LX[v] * W1[f] + LY[v] * W2[f]) * hd;
-                        const ll iv = __float2ll_rn(ldexpf(val, E[f]));
+                        const ll iv = __float2ll_rn((L0[v] * W0[f] + LX[v] * W1[f] + LY[v] * W2[f]) * S[f]);
                         if (iv) atomicAdd((ull *)&cfix[(ll)f * np + who[v]], (ull)iv);
                     }
                 }
@@ -661,8 +668,7 @@ __global__ void __launch_bounds__(256) k_rhs2d(Geo g, ll np, const uint2 *__rest
 #pragma unroll
                 for (int f = 0; f < FF; ++f) {
                     if (f >= F) break;
-                    const float val = (al[f] * K0[c] + gx[f] * K1[c] + gy[f] * K2[c]) * hd;
-                    const ll iv = __float2ll_rn(ldexpf(val, E[f]));
+                    const ll iv = __float2ll_rn((al[f] * K0[c] + gx[f] * K1[c] + gy[f] * K2[c]) * S[f]);
                     if (!iv) continue;
                     if (inwin)
                         add64_split(&acc_lo[f][ly * RWIN + lx], &acc_hi[f][ly * RWIN + lx], (ull)iv);
