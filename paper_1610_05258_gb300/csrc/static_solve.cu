@@ -71,7 +71,7 @@ extern "C" pm_status pm_mass_solve_noalloc(int dim, int n, double L, const float
     if (scratch_address(&base) != cudaSuccess) return PM_ECUDA;
     cudaStream_t st = (cudaStream_t)stream;
 
-    Geo g;
+    Geo g{};  // value-initialised: bilinear (p1 = 0)
     g.dim = dim;
     g.n = n;
     g.L = L;
