@@ -173,9 +173,9 @@ DELAUNAY_OP_WEIGHTS = {"candidates": 10, "tested": 5, "vertex_tests": 5, "clips"
 ALU_LANES = 152 * 128
 # DRAM traffic of one k_delaunay launch per particle: dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture on the 1024^2 mixture (4,194,304
-# particles: 99.46 MB read + 103.85 MB written), scaled to a launch by its
+# particles: 100.62 MB read + 100.76 MB written), scaled to a launch by its
 # particle count (the kernel's traffic grows in proportion to it).
-DELAUNAY_DRAM_BYTES_PER_PARTICLE = (99.463680e6 + 103.848704e6) / 4194304
+DELAUNAY_DRAM_BYTES_PER_PARTICLE = (100.624128e6 + 100.764928e6) / 4194304
 
 
 def alu_roofline(kernel, counts, ms, sm_mhz, n_particles):
