@@ -41,6 +41,7 @@ CASES_2D = [
     ("uniform_n64_ppc7_F3", lambda: W.uniform_instance(64, 7, F=3, seed=103)),
     ("taylor_green_n33", lambda: W.taylor_green(33, 4, seed=105)),
     ("mixture_n32_F4", lambda: W.mixture(32, 4, 4)),
+    ("uniform_n24_ppc3_F8", lambda: W.uniform_instance(24, 3, F=8, seed=108)),
 ]
 CASES_1D = [
     ("tophat_128", lambda: W.tophat_1d(128, 128, seed=16101)),

@@ -41,6 +41,7 @@ CASES = [
     ("uniform_n64_ppc7_F3", lambda: W.uniform_instance(64, 7, F=3, seed=103)),
     ("zalesak_n48", lambda: W.zalesak(48, seed=104)),
     ("mixture_n32_F4", lambda: W.mixture(32, 4, 4)),
+    ("uniform_n24_ppc3_F8", lambda: W.uniform_instance(24, 3, F=8, seed=108)),
 ]
 
 
@@ -124,3 +125,16 @@ def test_p1_differs_from_q1_and_rejects_q1_only_options(built):
     # the context stays usable
     out, info = c.assign_mass(dpx, dpy, dv)
     assert info[0].rel_resid <= 1e-6
+
+
+def test_p1_is_the_linear_mesh_in_1d(built):
+    """In 1D both mesh kinds are the linear hats: identical results."""
+    from paper_1610_05258_gb300 import Context
+    inst = W.tophat_1d(203, 517, seed=7)
+    px, vals = to_dev(torch, inst.px, inst.vals)
+    outs = []
+    for kind in ("q1", "p1"):
+        c = Context(1, inst.n, inst.L, inst.np, 1, mesh=kind)
+        m, _ = c.assign_mass(px, None, vals)
+        outs.append(m.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
