@@ -228,7 +228,7 @@ def run_mixture(args, pm, torch, dist, local):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     arms = {"plain": {"warm_start": "delta"}, "learned": {"net": net}, "direct": {"warm_start": "direct"},
-            "appb": {"warm_start": "delta", "rhs": "appb"}}
+            "appb": {"warm_start": "delta", "rhs": "appb"}, "cheb": {"warm_start": "delta", "solver": "chebyshev"}}
     res = {}
     clocks = Clocks(local)
     for name, kw in arms.items():
@@ -279,7 +279,7 @@ def run_mixture(args, pm, torch, dist, local):
         e2e = {"value": args.world * N * F / (te * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo, "ms_per_step": te}
 
-    plain, learned, direct, appb = res["plain"], res["learned"], res["direct"], res["appb"]
+    plain, learned, direct, appb, cheb = res["plain"], res["learned"], res["direct"], res["appb"], res["cheb"]
     # the same step with P1 mesh functions (cells split by the (0,0)-(1,1) diagonal)
     ctx_p1 = pm.Context(2, n, L, N, F, device=dev, mesh="p1")
     _, p1_info = ctx_p1.assign_mass(px, py, vals, out=out)
@@ -362,6 +362,11 @@ def run_mixture(args, pm, torch, dist, local):
                      "solve": solve_report(appb["info"]),
                      "what": "the same step with the App. B quadrature right-hand side (delta on the twice refined "
                              "mesh, 3x3 box sum) instead of the exact one; not conservative"},
+        "chebyshev": {"value": args.world * N * F / (cheb["ms"] * 1e-3), "ms_per_step": cheb["ms"],
+                      "phase_ms_per_step": {k: round(v, 4) for k, v in cheb["phase_ms"].items()},
+                      "solve": solve_report(cheb["info"]),
+                      "what": "the same step with the mesh system solved by Chebyshev iteration on the closed-form "
+                              "spectrum (no inner products) instead of CG"},
         "p1_mesh": {"value": args.world * N * F / (p1_t * 1e-3), "ms_per_step": p1_t,
                     "phase_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in p1_prof.items() if v[0] > 0},
                     "solve": solve_report(p1_info),

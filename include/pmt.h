@@ -77,6 +77,17 @@ enum { PM_WS_DELTA = 0, PM_WS_ZERO = 1, PM_WS_USER = 2, PM_WS_NET = 3, PM_WS_DIR
  * around node i. Not conservative (App. B); the solve reports cons_err. */
 enum { PM_RHS_EXACT = 0, PM_RHS_APPB = 1 };
 
+/* Solver of the mesh system M Ab = b (Sec. 2.4, Eq. phi_def). PM_SOLVER_CG:
+ * conjugate gradients with FP64 inner products. PM_SOLVER_CHEBYSHEV:
+ * Chebyshev iteration on the closed-form spectrum of the periodic mass
+ * matrix ([h/3, h] in 1D, [h^2/9, h^2] bilinear, [h^2/4, h^2] P1), with no
+ * inner products; the step count follows from ||b - M x0|| and the Chebyshev
+ * bound, and the true residual is checked at the end. Both set the mean mode
+ * exactly (conservative to rounding) and report the same pm_solve_info
+ * (iters = Chebyshev steps). The particle-side full-mass solve always uses
+ * conjugate gradients. */
+enum { PM_SOLVER_CG = 0, PM_SOLVER_CHEBYSHEV = 1 };
+
 typedef struct pm_net pm_net;
 
 /* Options of the mass solve  M Ab = b  (Sec. 2.4, Eq. phi_def). */
@@ -90,6 +101,7 @@ typedef struct pm_solve_opts {
                         correction and alpha the step that minimises the 2-norm
                         of the start's residual (alpha = 0 keeps the delta start) */
     int rhs_mode;    /* PM_RHS_EXACT (default) or PM_RHS_APPB (pm_assign_mass)   */
+    int solver;      /* PM_SOLVER_CG (default) or PM_SOLVER_CHEBYSHEV (mesh solve) */
 } pm_solve_opts;
 
 /* Per-field report of a mass solve (host memory, one entry per field). */

@@ -24,6 +24,8 @@ PM_RHS_EXACT, PM_RHS_APPB = 0, 1
 PM_MESH_Q1, PM_MESH_P1 = 0, 1
 MESH_KINDS = {"q1": PM_MESH_Q1, "p1": PM_MESH_P1}
 RHS_MODES = {"exact": PM_RHS_EXACT, "appb": PM_RHS_APPB}
+PM_SOLVER_CG, PM_SOLVER_CHEBYSHEV = 0, 1
+SOLVERS = {"cg": PM_SOLVER_CG, "chebyshev": PM_SOLVER_CHEBYSHEV}
 _STATUS = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ENOTCONV", 4: "PM_ETIMEOUT", 5: "PM_EDEGENERATE",
            6: "PM_ECUDA"}
 
@@ -48,7 +50,8 @@ class PMError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("warm_start", ctypes.c_int), ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("x0", ctypes.c_void_p), ("net", ctypes.c_void_p), ("rhs_mode", ctypes.c_int)]
+                ("x0", ctypes.c_void_p), ("net", ctypes.c_void_p), ("rhs_mode", ctypes.c_int),
+                ("solver", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -271,21 +274,22 @@ class Context:
                                             _ptr(node_volume), ctypes.byref(e) if count_empty else None))
         return (out, e.value) if count_empty else out
 
-    def _opts(self, warm_start, rtol, max_iter, x0, net=None, rhs="exact"):
+    def _opts(self, warm_start, rtol, max_iter, x0, net=None, rhs="exact", solver="cg"):
         ws = {"delta": PM_WS_DELTA, "zero": PM_WS_ZERO, "user": PM_WS_USER, "net": PM_WS_NET,
               "direct": PM_WS_DIRECT}[warm_start]
         return _Opts(ws, rtol, max_iter, x0.data_ptr() if x0 is not None else None, net.h.value if net else None,
-                     RHS_MODES[rhs])
+                     RHS_MODES[rhs], SOLVERS[solver])
 
     def assign_mass(self, px, py, vals, out=None, warm_start="delta", rtol=1e-6, max_iter=200, x0=None,
-                    info=True, net=None, rhs="exact"):
-        """Mass assignment; rhs "exact" (Eq. proj) or "appb" (App. B quadrature)."""
+                    info=True, net=None, rhs="exact", solver="cg"):
+        """Mass assignment; rhs "exact" (Eq. proj) or "appb" (App. B quadrature);
+        solver "cg" or "chebyshev" for the mesh system."""
         px, py, vals, x0 = self._f32(px), self._f32(py), self._f32(vals), self._f32(x0)
         F = vals.numel() // max(1, px.numel())
         out = out if out is not None else self._empty(F, self.nodes)
         if net is not None:
             warm_start = "net"
-        o = self._opts(warm_start, rtol, max_iter, x0, net, rhs)
+        o = self._opts(warm_start, rtol, max_iter, x0, net, rhs, solver)
         inf = (_Info * F)() if info else None
         self._stream()
         s = self.lib.pm_assign_mass(self.h, _ptr(px), _ptr(py), px.numel(), _ptr(vals), F, _ptr(out),
@@ -326,12 +330,12 @@ class Context:
         self._check(self.lib.pm_mass_apply(self.h, _ptr(x), F, _ptr(out)))
         return out
 
-    def mass_solve(self, b, out=None, rtol=1e-6, max_iter=200, x0=None, info=True, warm_start=None):
+    def mass_solve(self, b, out=None, rtol=1e-6, max_iter=200, x0=None, info=True, warm_start=None, solver="cg"):
         b, x0 = self._f32(b), self._f32(x0)
         F = b.numel() // self.nodes
         out = out if out is not None else self._empty(F, self.nodes)
         ws = warm_start or ("user" if x0 is not None else "zero")
-        o = self._opts(ws, rtol, max_iter, x0)
+        o = self._opts(ws, rtol, max_iter, x0, solver=solver)
         inf = (_Info * F)() if info else None
         self._stream()
         self._check(self.lib.pm_mass_solve(self.h, _ptr(b), F, _ptr(out), ctypes.byref(o), inf))

@@ -322,6 +322,7 @@ static void default_opts(const pm_solve_opts *o, pm_solve_opts &d) {
     d.x0 = nullptr;
     d.net = nullptr;
     d.rhs_mode = PM_RHS_EXACT;
+    d.solver = PM_SOLVER_CG;
     if (o) d = *o;
     if (!(d.rtol > 0.0)) d.rtol = 1e-6;
     if (d.max_iter <= 0) d.max_iter = 200;
@@ -395,7 +396,8 @@ static pm_status mass_solve_launch(pm_ctx *c, int F, float *mesh_out, bool start
     int e;
     {
         Phase ph(c, PM_PH_SOLVE);
-        e = launch_cg(c->g, c->w, F, nullptr, true, mesh_out, start, o.rtol, o.max_iter, c->st);
+        e = (o.solver == PM_SOLVER_CHEBYSHEV ? launch_cheb : launch_cg)(c->g, c->w, F, nullptr, true, mesh_out,
+                                                                       start, o.rtol, o.max_iter, c->st);
     }
     if (e) return cuda_fail(c, (cudaError_t)e, "pm_assign_mass solve launch");
     return check_launch(c, "solve");
@@ -410,6 +412,7 @@ pm_status pm_assign_mass(pm_ctx *c, const float *px, const float *py, long long 
     default_opts(opts, o);
     if (o.warm_start < PM_WS_DELTA || o.warm_start > PM_WS_DIRECT) return fail(c, PM_EINVAL, "unknown warm start");
     if (o.rhs_mode != PM_RHS_EXACT && o.rhs_mode != PM_RHS_APPB) return fail(c, PM_EINVAL, "unknown rhs_mode");
+    if (o.solver != PM_SOLVER_CG && o.solver != PM_SOLVER_CHEBYSHEV) return fail(c, PM_EINVAL, "unknown solver");
     if (c->g.p1 && (o.rhs_mode == PM_RHS_APPB || o.warm_start == PM_WS_DIRECT))
         return fail(c, PM_EINVAL, "PM_RHS_APPB and PM_WS_DIRECT need the bilinear mesh");
     if (o.warm_start == PM_WS_USER && !o.x0) return fail(c, PM_EINVAL, "PM_WS_USER without x0");
@@ -457,7 +460,7 @@ pm_status pm_interpolate_lumped(pm_ctx *c, const float *mesh, int F, const float
 
 pm_status pm_interpolate_mass(pm_ctx *c, const float *mesh, int F, const float *px, const float *py, long long np,
                               float *out, const pm_solve_opts *opts, pm_solve_info *info) {
-    pm_solve_opts o = opts ? *opts : pm_solve_opts{PM_WS_DELTA, 1e-6, 200, nullptr, nullptr, PM_RHS_EXACT};
+    pm_solve_opts o = opts ? *opts : pm_solve_opts{PM_WS_DELTA, 1e-6, 200, nullptr, nullptr, PM_RHS_EXACT, PM_SOLVER_CG};
     if (!(o.rtol > 0.0) || o.max_iter < 0) return fail(c, PM_EINVAL, "bad solve options");
     pm_status s = proj_front(c, mesh, F, px, py, np, out);
     if (s) return s;
@@ -525,6 +528,7 @@ pm_status pm_mass_solve(pm_ctx *c, const float *b, int F, float *x, const pm_sol
     if (F < 1 || F > c->w.F_max || !b || !x) return fail(c, PM_EINVAL, "bad mass_solve arguments");
     pm_solve_opts o;
     default_opts(opts, o);
+    if (o.solver != PM_SOLVER_CG && o.solver != PM_SOLVER_CHEBYSHEV) return fail(c, PM_EINVAL, "unknown solver");
     bool start = false;
     if (o.warm_start == PM_WS_USER) {
         if (!o.x0) return fail(c, PM_EINVAL, "PM_WS_USER without x0");
@@ -539,7 +543,8 @@ pm_status pm_mass_solve(pm_ctx *c, const float *b, int F, float *x, const pm_sol
     int e;
     {
         Phase ph(c, PM_PH_SOLVE);
-        e = launch_cg(c->g, c->w, F, b, false, x, start, o.rtol, o.max_iter, c->st);
+        e = (o.solver == PM_SOLVER_CHEBYSHEV ? launch_cheb : launch_cg)(c->g, c->w, F, b, false, x, start, o.rtol,
+                                                                       o.max_iter, c->st);
     }
     if (e) return cuda_fail(c, (cudaError_t)e, "pm_mass_solve launch");
     if (info) return fill_info(c, F, info);
@@ -835,6 +840,7 @@ pm_status pm_batch_assign_mass(pm_batch *b, const float *const *px, const float 
     o.x0 = nullptr;
     o.net = nullptr;
     o.rhs_mode = PM_RHS_EXACT;
+    o.solver = PM_SOLVER_CG;
     std::vector<char> start(b->ninst, 1);
     // the main stream follows the caller's stream
     cudaEventRecord(b->fork, b->user);

@@ -37,6 +37,20 @@ struct Geo {
     int p1;        // 2D mesh functions: 0 bilinear, 1 P1 on cells split by the (0,0)-(1,1) diagonal
 };
 
+// Exponent E of the 64-bit fixed point in which the right-hand side of a
+// field with max|A| = amax is accumulated: |b_j| <= amax h^dim < 2^(60 - E).
+// Capped so that h^dim 2^E stays below 2^120, a finite float scale; the cap
+// binds only for amax below about 2^-60, where over 40 bits of the fixed
+// point remain in use. Every producer and reader of the fixed point uses it.
+__device__ __forceinline__ int fixed_point_exp(float amax, float hd) {
+    const float m = amax * hd;
+    if (!(m > 0.0f)) return 0;
+    int e, eh;
+    frexpf(m, &e);
+    frexpf(hd, &eh);
+    return min(60 - e, 120 - eh);
+}
+
 // The four mesh functions non-zero on a 2D cell at local (s, t), corner order
 // (0,0), (1,0), (0,1), (1,1): bilinear, or P1 on the triangles s >= t and
 // s <= t of the cell's (0,0)-(1,1) diagonal (barycentric coordinates of their
@@ -217,6 +231,8 @@ void launch_rhs_appb(const Geo &g, Work &w, ll np, int F, cudaStream_t st);
 void launch_rhs_to_float(const Geo &g, Work &w, int F, float *b_out, cudaStream_t st);
 void launch_mass_apply(const Geo &g, const float *x, int F, float *y, cudaStream_t st);
 int launch_cg(const Geo &g, Work &w, int F, const float *b_float, bool b_from_fix, float *x, bool x_has_start,
+              double rtol, int max_iter, cudaStream_t st);
+int launch_cheb(const Geo &g, Work &w, int F, const float *b_float, bool b_from_fix, float *x, bool x_has_start,
               double rtol, int max_iter, cudaStream_t st);
 void launch_scatter_sorted(ll np, const int *perm, const float *src, float *dst, cudaStream_t st);
 void launch_export_tris(const Geo &g, Work &w, ll np, int *tri, int *off, ll max_tri, cudaStream_t st);

@@ -173,6 +173,13 @@ __device__ __forceinline__ void stencil(const float *__restrict__ xf, int n, ll 
     lo = acc.lo;
 }
 
+// Power of two 2^-ilogb(m) that scales a field of mean absolute value m to
+// order one (1 for m = 0).
+__device__ __forceinline__ float solve_scale(double m) {
+    if (!(m > 0.0)) return 1.0f;
+    return ldexpf(1.0f, min(120, max(-120, -ilogb(m))));
+}
+
 template <int DIM, int P1>
 __global__ void __launch_bounds__(256) k_cg(CG a) {
     const Geo g = a.g;
@@ -185,45 +192,52 @@ __global__ void __launch_bounds__(256) k_cg(CG a) {
     double bb[PM_MAXF], rr[PM_MAXF], alpha[PM_MAXF], beta[PM_MAXF];
     bool act[PM_MAXF];
     int it_f[PM_MAXF];
-    // --- phase 0: right-hand side as float, its sum and norm, sum of start
+    // --- phase 0: right-hand side as float, its sum and sum of |b|, sum of start
     for (int f = 0; f < F; ++f) {
-        Dot2 sb, s2, sx;
-        float hd32 = DIM == 1 ? g.h : g.h * g.h;
-        int E = 0;
-        if (a.bfix) {
-            float m = __uint_as_float(a.maxabs[f]) * hd32;
-            if (m > 0.0f) { frexpf(m, &E); E = 60 - E; }
-        }
+        Dot2 sb, sa, sx;
+        const float hd32 = DIM == 1 ? g.h : g.h * g.h;
+        const int E = a.bfix ? fixed_point_exp(__uint_as_float(a.maxabs[f]), hd32) : 0;
         for (ll i = tid; i < nn; i += nth) {
             float bv = a.bfix ? ldexpf((float)a.bfix[(ll)f * nn + i], -E) : a.bsrc[(ll)f * nn + i];
             a.b[(ll)f * nn + i] = bv;
             sb.add(bv);
-            s2.fma_acc(bv, bv);
+            sa.add(fabsf(bv));
             if (a.has_start) sx.add(a.x[(ll)f * nn + i]);
         }
         v[f] = (double)sb.hi + (double)sb.lo;
-        w[f] = (double)s2.hi + (double)s2.lo;
-        double t = (double)sx.hi + (double)sx.lo;
-        alpha[f] = t;
+        w[f] = (double)sa.hi + (double)sa.lo;
+        alpha[f] = (double)sx.hi + (double)sx.lo;
     }
     block_partial(v, F, a.red, 0);
     block_partial(w, F, a.red, 1);
     block_partial(alpha, F, a.red, 2);
     if (!grid_sync(a.bar, a.status)) return;
-    double sumb[PM_MAXF], sumx[PM_MAXF];
+    double sumb[PM_MAXF], sumx[PM_MAXF], suma[PM_MAXF];
     grid_total(a.red, F, 0, sumb);
-    grid_total(a.red, F, 1, bb);
+    grid_total(a.red, F, 1, suma);
     grid_total(a.red, F, 2, sumx);
-    // exact mean mode: mean(x) = sum b / (nn h^dim)
+    // The system is solved for S b with S a power of two that brings the mean
+    // |b| to order one (exact scaling: FP32 inner products of any field stay
+    // in range); x is scaled by S on entry and by 1/S on exit. Then the exact
+    // mean mode: mean(x) = sum b / (nn h^dim), and the norm of S b.
+    float S[PM_MAXF];
     for (int f = 0; f < F; ++f) {
-        double shift = sumb[f] / ((double)nn * hd) - (a.has_start ? sumx[f] / (double)nn : 0.0);
-        float sh = (float)shift;
+        S[f] = solve_scale(suma[f] / (double)nn);
+        const double shift = (double)S[f] * (sumb[f] / ((double)nn * hd) - (a.has_start ? sumx[f] / (double)nn : 0.0));
+        const float sh = (float)shift;
+        Dot2 s2;
         for (ll i = tid; i < nn; i += nth) {
-            float xv = a.has_start ? a.x[(ll)f * nn + i] : 0.0f;
+            const float xv = a.has_start ? a.x[(ll)f * nn + i] * S[f] : 0.0f;
             a.x[(ll)f * nn + i] = xv + sh;
+            const float bv = a.b[(ll)f * nn + i] * S[f];
+            a.b[(ll)f * nn + i] = bv;
+            s2.fma_acc(bv, bv);
         }
+        w[f] = (double)s2.hi + (double)s2.lo;
     }
+    block_partial(w, F, a.red, 3);
     if (!grid_sync(a.bar, a.status)) return;
+    grid_total(a.red, F, 3, bb);
     // --- r = b - M x, p = r
     for (int f = 0; f < F; ++f) {
         Dot2 s;
@@ -378,7 +392,7 @@ __global__ void __launch_bounds__(256) k_cg(CG a) {
             double res = bb[f] > 0.0 ? sqrt(tr[f] / bb[f]) : 0.0;
             a.scal[f * 16 + S_ITERS] = it_f[f];
             a.scal[f * 16 + S_RESID] = res;
-            a.scal[f * 16 + S_SUMMESH] = sx[f] * hd;
+            a.scal[f * 16 + S_SUMMESH] = sx[f] * hd / (double)S[f];
             if (a.psum) {
                 a.scal[f * 16 + S_SUMPART] = ps1[f];
                 a.scal[f * 16 + S_SUMABS] = ps2[f];
@@ -389,6 +403,178 @@ __global__ void __launch_bounds__(256) k_cg(CG a) {
             if (res > a.rtol) bad = true;
         }
         if (bad) atomicOr(a.status, ST_NOTCONV);
+    }
+    for (int f = 0; f < F; ++f) {
+        const float inv = 1.0f / S[f];  // a power of two: exact
+        for (ll i = tid; i < nn; i += nth) a.x[(ll)f * nn + i] *= inv;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Chebyshev iteration for M x = b. The spectrum of the periodic mass matrix
+// is known in closed form (Fourier modes): [h/3, h] in 1D, [h^2/9, h^2] on
+// the bilinear mesh, [h^2/4, h^2] on the P1 mesh. With theta and delta the
+// centre and half-width of that interval, sigma = theta / delta, the
+// iteration
+//   d_0 = r_0 / theta, rho_0 = 1 / sigma,
+//   x += d_k, r -= M d_k, rho_{k+1} = 1 / (2 sigma - rho_k),
+//   d_{k+1} = rho_{k+1} rho_k d_k + (2 rho_{k+1} / delta) r
+// reduces the residual by the scaled Chebyshev polynomial, whose maximum on
+// the interval is at most 2 q^k, q = (sqrt(kappa) - 1) / (sqrt(kappa) + 1).
+// It needs no inner products: the number of steps for the tolerance follows
+// from ||r_0|| and that bound, one grid barrier per step; the true residual
+// is then recomputed and, if rounding left it above the tolerance, the
+// iteration restarts from it (at most three times). The mean mode is set
+// exactly first, as for CG, and every update d_k has zero mean, so the result
+// is conservative to rounding.
+// ---------------------------------------------------------------------------
+template <int DIM, int P1>
+__global__ void __launch_bounds__(256) k_cheb(CG a) {
+    const Geo g = a.g;
+    const int F = a.F, n = g.n;
+    const ll nn = g.ncell;
+    const ll tid = (ll)blockIdx.x * blockDim.x + threadIdx.x, nth = (ll)gridDim.x * blockDim.x;
+    const float c = DIM == 1 ? g.h / 6.0f : (P1 ? g.h * g.h / 12.0f : g.h * g.h / 36.0f);
+    const double hd = DIM == 1 ? (double)g.h : (double)g.h * g.h;
+    // spectrum bounds, widened by 1e-6 against rounding of the operator
+    const double lmin = hd * (DIM == 1 ? 1.0 / 3.0 : (P1 ? 0.25 : 1.0 / 9.0)) * (1.0 - 1e-6);
+    const double lmax = hd * (1.0 + 1e-6);
+    const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+    const double kap = lmax / lmin, q = (sqrt(kap) - 1.0) / (sqrt(kap) + 1.0);
+    double v[PM_MAXF], w[PM_MAXF], u[PM_MAXF], bb[PM_MAXF], rr[PM_MAXF];
+    // --- right-hand side as float, its sum and sum of |b|, sum of the start
+    for (int f = 0; f < F; ++f) {
+        Dot2 sb, sa, sx;
+        const float hd32 = DIM == 1 ? g.h : g.h * g.h;
+        const int E = a.bfix ? fixed_point_exp(__uint_as_float(a.maxabs[f]), hd32) : 0;
+        for (ll i = tid; i < nn; i += nth) {
+            const float bv = a.bfix ? ldexpf((float)a.bfix[(ll)f * nn + i], -E) : a.bsrc[(ll)f * nn + i];
+            a.b[(ll)f * nn + i] = bv;
+            sb.add(bv);
+            sa.add(fabsf(bv));
+            if (a.has_start) sx.add(a.x[(ll)f * nn + i]);
+        }
+        v[f] = (double)sb.hi + (double)sb.lo;
+        w[f] = (double)sa.hi + (double)sa.lo;
+        u[f] = (double)sx.hi + (double)sx.lo;
+    }
+    block_partial(v, F, a.red, 0);
+    block_partial(w, F, a.red, 1);
+    block_partial(u, F, a.red, 2);
+    if (!grid_sync(a.bar, a.status)) return;
+    double sumb[PM_MAXF], sumx[PM_MAXF], suma[PM_MAXF];
+    grid_total(a.red, F, 0, sumb);
+    grid_total(a.red, F, 1, suma);
+    grid_total(a.red, F, 2, sumx);
+    // solve for S b (S a power of two, as in k_cg), exact mean mode, |S b|^2
+    float S[PM_MAXF];
+    for (int f = 0; f < F; ++f) {
+        S[f] = solve_scale(suma[f] / (double)nn);
+        const double shift = (double)S[f] * (sumb[f] / ((double)nn * hd) - (a.has_start ? sumx[f] / (double)nn : 0.0));
+        const float sh = (float)shift;
+        Dot2 s2;
+        for (ll i = tid; i < nn; i += nth) {
+            const float xv = a.has_start ? a.x[(ll)f * nn + i] * S[f] : 0.0f;
+            a.x[(ll)f * nn + i] = xv + sh;
+            const float bv = a.b[(ll)f * nn + i] * S[f];
+            a.b[(ll)f * nn + i] = bv;
+            s2.fma_acc(bv, bv);
+        }
+        w[f] = (double)s2.hi + (double)s2.lo;
+    }
+    block_partial(w, F, a.red, 3);
+    if (!grid_sync(a.bar, a.status)) return;
+    grid_total(a.red, F, 3, bb);
+    const double tol2 = a.rtol * a.rtol;
+    int steps_done = 0, steps_f[PM_MAXF];
+    for (int f = 0; f < PM_MAXF; ++f) steps_f[f] = 0;
+    for (int pass = 0;; ++pass) {
+        // --- r = b - M x (the true residual), d = r / theta, (r, r), sum x
+        for (int f = 0; f < F; ++f) {
+            Dot2 s, sx;
+            const float *xf = a.x + (ll)f * nn;
+            for (ll i = tid; i < nn; i += nth) {
+                float hi, lo;
+                stencil<DIM, P1>(xf, n, i, hi, lo);
+                const float rv = fmaf(-c, hi, a.b[(ll)f * nn + i]) - c * lo;
+                a.r[(ll)f * nn + i] = rv;
+                a.p[(ll)f * nn + i] = (float)(rv / theta);
+                s.fma_acc(rv, rv);
+                sx.add(xf[i]);
+            }
+            v[f] = (double)s.hi + (double)s.lo;
+            u[f] = (double)sx.hi + (double)sx.lo;
+        }
+        block_partial(v, F, a.red, 0);
+        block_partial(u, F, a.red, 1);
+        if (!grid_sync(a.bar, a.status)) return;
+        grid_total(a.red, F, 0, rr);
+        double sx[PM_MAXF];
+        grid_total(a.red, F, 1, sx);
+        if (pass == 0 && blockIdx.x == 0 && threadIdx.x == 0)
+            for (int f = 0; f < F; ++f) a.scal[f * 16 + S_INIT] = bb[f] > 0.0 ? sqrt(rr[f] / bb[f]) : 0.0;
+        // steps of each field for the bound 2 q^k ||r_0|| <= rtol ||b||; the
+        // pass runs the largest, a field stops updating after its own
+        int K = 0, Kf[PM_MAXF];
+        for (int f = 0; f < F; ++f) {
+            Kf[f] = 0;
+            if (!(bb[f] > 0.0) || rr[f] <= tol2 * bb[f]) continue;
+            const double ratio = a.rtol * sqrt(bb[f]) / (2.0 * sqrt(rr[f]));
+            Kf[f] = min((int)ceil(log(ratio) / log(q)), a.max_iter - steps_done);
+            K = max(K, Kf[f]);
+        }
+        if (K <= 0 || pass == 4) {
+            // report: this pass computed the true residual of the final x
+            double ps1[PM_MAXF], ps2[PM_MAXF];
+            if (blockIdx.x == 0 && a.psum) particle_sums(a.psum, a.nblk_psum, F, ps1, ps2);
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                bool bad = false;
+                for (int f = 0; f < F; ++f) {
+                    const double res = bb[f] > 0.0 ? sqrt(rr[f] / bb[f]) : 0.0;
+                    a.scal[f * 16 + S_ITERS] = steps_f[f];
+                    a.scal[f * 16 + S_RESID] = res;
+                    a.scal[f * 16 + S_SUMMESH] = sx[f] * hd / (double)S[f];
+                    a.scal[f * 16 + S_SUMPART] = a.psum ? ps1[f] : sumb[f];
+                    a.scal[f * 16 + S_SUMABS] = a.psum ? ps2[f] : 0.0;
+                    if (res > a.rtol) bad = true;
+                }
+                if (bad) atomicOr(a.status, ST_NOTCONV);
+            }
+            for (int f = 0; f < F; ++f) {
+                const float inv = 1.0f / S[f];  // a power of two: exact
+                for (ll i = tid; i < nn; i += nth) a.x[(ll)f * nn + i] *= inv;
+            }
+            break;
+        }
+        // the residual partials must be read by every block before reuse
+        if (!grid_sync(a.bar, a.status)) return;
+        double rho = 1.0 / sigma;
+        float *dc = a.p, *dn = a.q;
+        for (int k = 0; k < K; ++k) {
+            const double rho1 = 1.0 / (2.0 * sigma - rho);
+            const float c1 = (float)(rho1 * rho), c2 = (float)(2.0 * rho1 / delta);
+            for (int f = 0; f < F; ++f) {
+                if (k >= Kf[f]) continue;
+                const float *df = dc + (ll)f * nn;
+                for (ll i = tid; i < nn; i += nth) {
+                    float hi, lo;
+                    stencil<DIM, P1>(df, n, i, hi, lo);
+                    const ll o = (ll)f * nn + i;
+                    const float dv = df[i];
+                    a.x[o] += dv;
+                    const float rv = a.r[o] - fmaf(c, hi, c * lo);
+                    a.r[o] = rv;
+                    dn[o] = fmaf(c1, dv, c2 * rv);
+                }
+            }
+            rho = rho1;
+            float *t = dc;
+            dc = dn;
+            dn = t;
+            if (!grid_sync(a.bar, a.status)) return;
+        }
+        steps_done += K;
+        for (int f = 0; f < F; ++f) steps_f[f] += Kf[f];
     }
 }
 
@@ -469,13 +655,9 @@ __global__ void __launch_bounds__(256) k_cg2v(CG a) {
     float *__restrict__ B = a.b;
     // --- phase 0: right-hand side as float, its sum and norm, sum of start
     for (int f = 0; f < F; ++f) {
-        Dot2 sb, s2, sx;
+        Dot2 sb, sa, sx;
         const float hd32 = g.h * g.h;
-        int E = 0;
-        if (a.bfix) {
-            float m = __uint_as_float(a.maxabs[f]) * hd32;
-            if (m > 0.0f) { frexpf(m, &E); E = 60 - E; }
-        }
+        const int E = a.bfix ? fixed_point_exp(__uint_as_float(a.maxabs[f]), hd32) : 0;
         for (ll qd = tid; qd < nq; qd += nth) {
             const ll o = (ll)f * nn + qd * 4;
             Q4 bv;
@@ -492,7 +674,7 @@ __global__ void __launch_bounds__(256) k_cg2v(CG a) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 sb.add(bv.v[j]);
-                s2.fma_acc(bv.v[j], bv.v[j]);
+                sa.add(fabsf(bv.v[j]));
             }
             if (a.has_start) {
                 const Q4 xv = ld4(X + o);
@@ -501,30 +683,42 @@ __global__ void __launch_bounds__(256) k_cg2v(CG a) {
             }
         }
         v[f] = (double)sb.hi + (double)sb.lo;
-        w[f] = (double)s2.hi + (double)s2.lo;
+        w[f] = (double)sa.hi + (double)sa.lo;
         alpha[f] = (double)sx.hi + (double)sx.lo;
     }
     block_partial(v, F, a.red, 0);
     block_partial(w, F, a.red, 1);
     block_partial(alpha, F, a.red, 2);
     if (!grid_sync(a.bar, a.status)) return;
-    double sumb[PM_MAXF], sumx[PM_MAXF];
+    double sumb[PM_MAXF], sumx[PM_MAXF], suma[PM_MAXF];
     grid_total(a.red, F, 0, sumb);
-    grid_total(a.red, F, 1, bb);
+    grid_total(a.red, F, 1, suma);
     grid_total(a.red, F, 2, sumx);
-    // exact mean mode: mean(x) = sum b / (nn h^2)
+    // solve for S b (S a power of two, as in k_cg), exact mean mode, |S b|^2
+    float S[PM_MAXF];
     for (int f = 0; f < F; ++f) {
-        const double shift = sumb[f] / ((double)nn * hd) - (a.has_start ? sumx[f] / (double)nn : 0.0);
+        S[f] = solve_scale(suma[f] / (double)nn);
+        const double shift = (double)S[f] * (sumb[f] / ((double)nn * hd) - (a.has_start ? sumx[f] / (double)nn : 0.0));
         const float sh = (float)shift;
+        Dot2 s2;
         for (ll qd = tid; qd < nq; qd += nth) {
             const ll o = (ll)f * nn + qd * 4;
             Q4 xv = a.has_start ? ld4(X + o) : Q4{{0.0f, 0.0f, 0.0f, 0.0f}};
+            Q4 bv = ld4(B + o);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) xv.v[j] += sh;
+            for (int j = 0; j < 4; ++j) {
+                xv.v[j] = fmaf(xv.v[j], S[f], sh);
+                bv.v[j] *= S[f];
+                s2.fma_acc(bv.v[j], bv.v[j]);
+            }
             st4(X + o, xv);
+            st4(B + o, bv);
         }
+        w[f] = (double)s2.hi + (double)s2.lo;
     }
+    block_partial(w, F, a.red, 3);
     if (!grid_sync(a.bar, a.status)) return;
+    grid_total(a.red, F, 3, bb);
     // --- r = b - M x, p = r
     for (int f = 0; f < F; ++f) {
         Dot2 s;
@@ -702,7 +896,7 @@ __global__ void __launch_bounds__(256) k_cg2v(CG a) {
             double res = bb[f] > 0.0 ? sqrt(tr[f] / bb[f]) : 0.0;
             a.scal[f * 16 + S_ITERS] = it_f[f];
             a.scal[f * 16 + S_RESID] = res;
-            a.scal[f * 16 + S_SUMMESH] = sx[f] * hd;
+            a.scal[f * 16 + S_SUMMESH] = sx[f] * hd / (double)S[f];
             if (a.psum) {
                 a.scal[f * 16 + S_SUMPART] = ps1[f];
                 a.scal[f * 16 + S_SUMABS] = ps2[f];
@@ -713,6 +907,16 @@ __global__ void __launch_bounds__(256) k_cg2v(CG a) {
             if (res > a.rtol) bad = true;
         }
         if (bad) atomicOr(a.status, ST_NOTCONV);
+    }
+    for (int f = 0; f < F; ++f) {
+        const float inv = 1.0f / S[f];  // a power of two: exact
+        for (ll qd = tid; qd < nq; qd += nth) {
+            const ll o = (ll)f * nn + qd * 4;
+            Q4 xv = ld4(X + o);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) xv.v[j] *= inv;
+            st4(X + o, xv);
+        }
     }
 }
 
@@ -1130,6 +1334,53 @@ int launch_cg(const Geo &g, Work &w, int F, const float *b_float, bool b_from_fi
     }
     int grid = g_cg_grid[di];
     ll need = ((quad ? g.ncell / 4 : g.ncell) + 255) / 256;
+    if (need < grid) grid = (int)(need < 1 ? 1 : need);
+    cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st);
+    void *args[] = {&a};
+    cudaError_t e = cudaLaunchCooperativeKernel((void *)kern, dim3(grid), dim3(256), args, 0, st);
+    count_launches(1);
+    return (int)e;
+}
+
+// Chebyshev solve: same arguments, workspace and report as launch_cg.
+int g_cheb_grid[3] = {0, 0, 0};
+
+int launch_cheb(const Geo &g, Work &w, int F, const float *b_float, bool b_from_fix, float *x, bool x_has_start,
+                double rtol, int max_iter, cudaStream_t st) {
+    CG a;
+    a.g = g;
+    a.F = F;
+    a.bsrc = b_float;
+    a.bfix = b_from_fix ? w.bfix : nullptr;
+    a.maxabs = w.maxabs;
+    a.x = x;
+    a.r = w.r;
+    a.p = w.p;
+    a.q = w.q;
+    a.b = w.b;
+    a.red = w.red;
+    a.scal = w.scal;
+    a.bar = w.bar;
+    a.status = w.status;
+    a.rtol = rtol;
+    a.max_iter = max_iter;
+    a.has_start = x_has_start ? 1 : 0;
+    a.psum = b_from_fix ? w.psum : nullptr;
+    a.nblk_psum = w.nblk_psum;
+    const bool p1 = g.dim == 2 && g.p1;
+    const int di = g.dim == 1 ? 0 : (p1 ? 2 : 1);
+    void (*kern)(CG) = g.dim == 1 ? k_cheb<1, 0> : (p1 ? k_cheb<2, 1> : k_cheb<2, 0>);
+    if (!g_cheb_grid[di]) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, 0);
+        if (per < 1) per = 1;
+        if (per > 4) per = 4;
+        g_cheb_grid[di] = sms * per;
+    }
+    int grid = g_cheb_grid[di];
+    const ll need = (g.ncell + 255) / 256;
     if (need < grid) grid = (int)(need < 1 ? 1 : need);
     cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st);
     void *args[] = {&a};

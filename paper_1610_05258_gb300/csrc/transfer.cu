@@ -34,17 +34,9 @@ __device__ __forceinline__ void rel_of(int e, uint2 Xp, const uint2 *__restrict_
     ry = (ll)Xq.y + (ll)oy * 4294967296LL - (ll)Xp.y;
 }
 
-// Fixed-point exponent E of field f: |b_j| <= max|A| h^dim < 2^(60 - E).
-// Capped so that h^dim 2^E stays below 2^120 (a finite float scale; the cap
-// only binds for max|A| below about 2^-60, where it still leaves over 40
-// bits of the fixed point in use).
+// Fixed-point exponent of field f (fixed_point_exp of its max|A|).
 __device__ __forceinline__ int fix_exp(const unsigned *maxabs, int f, float hd) {
-    float m = __uint_as_float(maxabs[f]) * hd;
-    if (!(m > 0.0f)) return 0;
-    int e, eh;
-    frexpf(m, &e);
-    frexpf(hd, &eh);
-    return min(60 - e, 120 - eh);
+    return fixed_point_exp(__uint_as_float(maxabs[f]), hd);
 }
 
 // Sign of orient(U, V, Q) with Q perturbed by (eps, eps^2) (ties never zero).

@@ -336,3 +336,20 @@ def test_delta_degenerate_lattice(built):
         got = c.assign_delta(dpx, dpy, dv).cpu().numpy()
         want = oracle.delta(2, n, 1.0, px, py, vals)
         assert rel_l2(got, want) <= TOL, n
+
+
+def test_tiny_amplitude_fields_scale_exactly(built):
+    """A field of amplitude 1e-25 (max|A| near 2^-83, where the fixed-point
+    exponent is capped) is assigned as 1e-25 times the unit field: the
+    right-hand side and the solve read the fixed point at the same scale."""
+    from paper_1610_05258_gb300 import Context
+    inst = W.uniform_instance(40, 4, F=1, seed=111)
+    c = Context(2, inst.n, inst.L, inst.np, 2)
+    px, py = to_dev(torch, inst.px, inst.py)
+    v = torch.from_numpy(np.concatenate([inst.vals, inst.vals * np.float32(1e-25)])).cuda()
+    out, info = c.assign_mass(px, py, v)
+    o = out.cpu().numpy().reshape(2, -1).astype(np.float64)
+    assert rel_l2(o[1] * 1e25, o[0]) <= 1e-5
+    assert info[1].rel_resid <= 1e-6 and info[1].cons_err <= 1e-6
+    b = c.mass_rhs(px, py, v).cpu().numpy().reshape(2, -1).astype(np.float64)
+    assert rel_l2(b[1] * 1e25, b[0]) <= 1e-5
