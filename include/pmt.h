@@ -113,6 +113,10 @@ typedef struct pm_solve_info {
     double sum_particles;  /* sum_mu v_mu A_mu  (Eq. cons, particle side)              */
     double sum_mesh;       /* sum_i v_i Ab_i with v_i = h^dim (Eq. cons, mesh side)     */
     double cons_err;       /* |sum_mesh - sum_particles| / sum_mu v_mu |A_mu|          */
+    double energy_mesh;    /* int Ab^2 = Ab^T M Ab of the mesh fields (stability, Sec. 2.1
+                              Eq. stab in integral form)                               */
+    double energy_particles; /* int A^2 = A^T M_p A, (M_p)_{mu nu} = int psi_mu psi_nu, of
+                              the particle fields (0 when the call has none)           */
 } pm_solve_info;
 
 /* Create a context for one periodic mesh (dim 1 or 2, n >= 4 nodes per side,
@@ -167,6 +171,15 @@ pm_status pm_assign_delta(pm_ctx *ctx, const float *px, const float *py, long lo
 pm_status pm_assign_flip(pm_ctx *ctx, const float *px, const float *py, long long np, const float *vals, int F,
                          float *mesh_out, float *node_volume_out, long long *empty_nodes);
 
+/* PIC assignment, Sec. 2.3 Eq. PIC with the mesh volumes of Eq. mesh_v:
+ *   Ab_i = sum_mu A_mu v_mu psi_i(r_mu) / v_i,  v_i = int psi_i = h^dim,
+ * v_mu = int psi_mu (Eq. part_v). Conservative with the mesh volumes
+ * (sum_i h^dim Ab_i = sum_mu v_mu A_mu); unlike FLIP it does not reproduce a
+ * constant field where the particle volumes around a node do not add up to
+ * h^dim. Layouts, ownership and errors as pm_assign_delta. Asynchronous. */
+pm_status pm_assign_pic(pm_ctx *ctx, const float *px, const float *py, long long np, const float *vals, int F,
+                        float *mesh_out);
+
 /* Mass assignment ("mass-delta" particle -> mesh direction), Sec. 2.4
  * Eqs. proj and phi_def:  Ab = M^-1 b  with  m_ij = int psi_i psi_j  and
  * b_j = int A(r) psi_j(r) dr,  A the particle interpolant (Eq. part_interp).
@@ -175,7 +188,8 @@ pm_status pm_assign_flip(pm_ctx *ctx, const float *px, const float *py, long lon
  * vectors with compensated sums, FP64 reductions; the mean mode of Ab is set
  * exactly from sum_j b_j first, so the result is conservative (Eq. cons) to
  * rounding whatever the iteration count. info (host, F entries, may be NULL)
- * makes the call wait for the stream. */
+ * makes the call wait for the stream; it also runs the stability
+ * diagnostics (energy_mesh of the result, energy_particles of the input). */
 pm_status pm_assign_mass(pm_ctx *ctx, const float *px, const float *py, long long np, const float *vals, int F,
                          float *mesh_out, const pm_solve_opts *opts, pm_solve_info *info);
 
@@ -205,7 +219,10 @@ pm_status pm_assign_lumped(pm_ctx *ctx, const float *px, const float *py, long l
  * px/py [np] (np >= 3 in 2D, >= 2 in 1D), out [F][np] caller order, device
  * pointers. info (host, F entries, may be NULL): iters, start and final
  * relative residual, sum_mesh = int Ab, sum_particles = sum v_mu out_mu,
- * cons_err relative to sum |c_mu|; passing it makes the call wait. Errors as
+ * cons_err relative to sum |c_mu|, energy_mesh = int Ab^2 of the input mesh,
+ * energy_particles = int Abb^2 of the result (full mass only: the
+ * projection keeps energy_particles <= energy_mesh); passing it makes the
+ * call wait. Errors as
  * pm_assign_mass (PM_ENOTCONV when the iteration cap is reached). */
 pm_status pm_interpolate_lumped(pm_ctx *ctx, const float *mesh, int F, const float *px, const float *py, long long np,
                                 float *out);
@@ -227,7 +244,8 @@ pm_status pm_mass_apply(pm_ctx *ctx, const float *x, int F, float *y);
 
 /* Solve M x[f] = b[f] (Sec. 2.4, Eq. phi_def) by conjugate gradients; the
  * start vector is zero or opts->x0 (PM_WS_DELTA is read as zero here).
- * info as in pm_assign_mass (sum_particles = sum_j b_j there). */
+ * info as in pm_assign_mass (sum_particles = sum_j b_j there; energy_mesh of
+ * x, energy_particles 0). */
 pm_status pm_mass_solve(pm_ctx *ctx, const float *b, int F, float *x, const pm_solve_opts *opts,
                         pm_solve_info *info);
 
@@ -254,16 +272,23 @@ pm_status pm_sort(pm_ctx *ctx, const float *px, const float *py, long long np, i
  * Particle advection: the driver step between mesh->particle and
  * particle->mesh in the paper's experiments (Sec. 3.1 dx/dt = u, Sec. 3.2
  * rigid rotation, Sec. 3.3 motion with the interpolated velocity). Positions
- * are updated in place and wrapped into [0, L). Asynchronous.
+ * are updated in place and wrapped into [0, L). The shift and the rotation
+ * compute the new position in FP64 from the float32 one, in the expression
+ * order stated below with one rounding per operation, wrap it into [0, L) and
+ * round it to float32 (a value that rounds to L becomes 0): the result is a
+ * plain function of the inputs, reproducible bit for bit. Asynchronous.
  * ------------------------------------------------------------------------- */
-/* x += dx (and y += dy in 2D). */
+/* x += dx (and y += dy in 2D), as x' = wrap(x + dx). */
 pm_status pm_advect_shift(pm_ctx *ctx, float *px, float *py, long long np, double dx, double dy);
-/* Rotate every particle about (cx, cy) by `angle` radians (2D only). */
+/* Rotate every particle about (cx, cy) by `angle` radians (2D only):
+ * x' = cx + (c X - s Y), y' = cy + (s X + c Y) with X = x - cx, Y = y - cy,
+ * c = cos(angle), s = sin(angle) from the host's libm. */
 pm_status pm_advect_rotate(pm_ctx *ctx, float *px, float *py, long long np, double cx, double cy, double angle);
 /* Explicit midpoint step  r += dt u(r + dt/2 vel)  with u interpolated from
  * the mesh velocity mesh_vel [dim][n^dim] (Eq. delta2) and vel [dim][np] the
  * particle velocity at the current position; vals [F][np] (may be NULL) are
- * multiplied by `factor` in the same pass. */
+ * multiplied by `factor` in the same pass. FP32 arithmetic (the midpoint is
+ * a float32 position, as every particle position). */
 pm_status pm_advect_rk2(pm_ctx *ctx, const float *mesh_vel, const float *vel, float *px, float *py, long long np,
                         double dt, float *vals, int F, double factor);
 
@@ -342,27 +367,31 @@ pm_status pm_batch_assign_mass(pm_batch *b, const float *const *px, const float 
 /* ---------------------------------------------------------------------------
  * Allocation-free mass solve (no counterpart in the paper).
  *
- * For callers that cannot allocate device memory when they need the solve:
- * work recorded into a CUDA graph by stream capture (cudaMalloc is not a
- * stream-ordered operation), latency-critical loops that cannot afford the
- * implicit device synchronisation of cudaMalloc/cudaFree, and host frameworks
- * that own all device memory through their own pool. Same result as
- * pm_mass_solve() (conjugate gradients on M x[f] = b[f], mean mode set
- * exactly, true residual checked), but it needs no context: its scratch is
- * one file-scope device array of about 16.2 MB that every GPU loading the
- * library holds until exit. The caller passes b [F][n^dim] and x [F][n^dim]
- * (device); x is the start vector when use_x0 != 0, else the solve starts
- * from zero. Limit: F * n^dim <= 2^20 values (e.g. F = 1 at 1024^2, F = 4 at
- * 512^2); larger sizes, dim not 1 or 2, n < 4, L <= 0 or F outside 1..8
- * return PM_EINVAL before any GPU work. The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture. All calls share the one array, so calls whose
- * work overlaps on the GPU (different streams or threads without ordering)
- * race and give wrong results; serialise them. iters and rel_resid (host,
- * F entries each, may be NULL) make the call wait for the stream and receive
- * the iteration count and true relative residual per field; then
- * PM_ENOTCONV / PM_ETIMEOUT are reported too. Errors are status codes only
- * (there is no context for pm_last_error()). No call allocates memory. */
+ * For callers that cannot call cudaMalloc when they need the solve: host
+ * applications and plugin frameworks that own all device memory through their
+ * own pool and forbid allocations by the libraries they load, and
+ * latency-critical loops that cannot take the implicit device synchronisation
+ * of cudaMalloc/cudaFree. Same result as pm_mass_solve() (conjugate gradients
+ * on M x[f] = b[f], mean mode set exactly, true residual checked), but it
+ * needs no context: its scratch is one file-scope device array of about
+ * 16.2 MB that every GPU loading the library holds until exit. The caller
+ * passes b [F][n^dim] and x [F][n^dim] (device); x is the start vector when
+ * use_x0 != 0, else the solve starts from zero. Limit: F * n^dim <= 2^20
+ * values (e.g. F = 1 at 1024^2, F = 4 at 512^2); larger sizes, dim not 1 or 2,
+ * n < 4, L <= 0 or F outside 1..8 return PM_EINVAL before any GPU work. The
+ * solve's grid is clamped to the 1024 blocks whose reduction partials the
+ * array holds. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture. All
+ * calls share the one array and each call leaves its contents behind, so calls
+ * whose work overlaps on the GPU (different streams or threads without
+ * ordering) race and give wrong results; serialise them. iters and rel_resid
+ * (host, F entries each, may be NULL) make the call wait for the stream and
+ * receive the iteration count and true relative residual per field; then
+ * PM_ENOTCONV / PM_ETIMEOUT are reported too. With both NULL the call returns
+ * as soon as the work is queued, and a solve that times out or does not
+ * converge is NOT reported: the next call overwrites the status word. Errors
+ * are status codes only (there is no context for pm_last_error()). No call
+ * allocates memory. */
 pm_status pm_mass_solve_noalloc(int dim, int n, double L, const float *b, int F, float *x, double rtol, int max_iter,
                                 int use_x0, void *stream, int *iters, double *rel_resid);
 

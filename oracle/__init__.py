@@ -10,6 +10,9 @@ Every function restates a definition of the paper in plain double precision
 * ``interpolate``      G2P, Sec. 2.2 Eq. delta2
 * ``delta``            delta assignment, Sec. 2.2 Eq. delta
 * ``flip``             FLIP assignment, Sec. 2.3 Eqs. PIC and FLIP_vol
+* ``pic``              PIC assignment, Sec. 2.3 Eq. PIC with mesh volumes
+* ``energy_mesh``, ``energy_particles``  int Ab^2 = Ab^T M Ab and
+                       int A^2 = A^T M_p A (stability, Eq. stab)
 * ``rhs``              mass right-hand side, Sec. 2.4 Eqs. proj and phi_def
                        (mode 0 exact overlay integral, mode 1 App. B quadrature)
 * ``mass_apply``       m_ij = int psi_i psi_j, Sec. 2.4
@@ -22,6 +25,8 @@ Every function restates a definition of the paper in plain double precision
 * ``interpolate_lumped``   Abb_mu = c_mu / v_mu, Eq. lumped
 * ``interpolate_mass``     full mass: m_p Abb = c, Eq. proj2 (phi_mu of
                        Eq. phi_def on the particles), solved by FP64 CG
+* ``advect``           the driver steps of Sec. 3.1-3.3 (shift, rigid
+                       rotation, midpoint rule with the mesh velocity)
 
 The App. B quadrature in 2D (mode 1) follows a reading of a garbled passage
 (the paper's text describes six-point quadratic fits on triangles; this
@@ -205,7 +210,10 @@ def stars(L, px, py, which):
     return [(nbr[k, : deg[k]].copy(), nof[k, : deg[k]].copy()) for k in range(w.shape[0])]
 
 
-def delta(dim, n, L, px, py, vals, tri=None):
+def delta(dim, n, L, px, py, vals, tri=None, partial=False):
+    """delta assignment (Eq. delta). partial=True (2D, a subset of the
+    triangles given in `tri`): nodes that no given triangle covers are NaN
+    instead of an error."""
     px = _f32(px)
     v = _fields(vals, px.shape[0])
     F = v.shape[0]
@@ -215,8 +223,14 @@ def delta(dim, n, L, px, py, vals, tri=None):
         return out
     py = _f32(py)
     t, o, _ = tri if tri is not None else triangulate(L, px, py)
-    _check(lib().or2_delta(n, ctypes.c_double(L), _p(px), _p(py), ctypes.c_longlong(px.shape[0]), _p(v), F, _p(t),
-                           _p(o), ctypes.c_longlong(t.shape[0]), _p(out)), "delta")
+    t = np.ascontiguousarray(t, dtype=np.int64)
+    o = np.ascontiguousarray(o, dtype=np.int32)
+    if partial:
+        out.fill(np.nan)
+    st = lib().or2_delta(n, ctypes.c_double(L), _p(px), _p(py), ctypes.c_longlong(px.shape[0]), _p(v), F, _p(t),
+                         _p(o), ctypes.c_longlong(t.shape[0]), _p(out))
+    if not (partial and st == 5):  # 5: some node not covered
+        _check(st, "delta")
     return out
 
 
@@ -235,6 +249,26 @@ def flip(dim, n, L, px, py, vals, v=None, kind="q1"):
     _check(lib().or_flip(dim, n, ctypes.c_double(L), _p(px), _p(py), ctypes.c_longlong(px.shape[0]), _p(a), F, _p(v),
                          _p(out), _p(vol), ctypes.byref(e), _p1(dim, kind)), "flip")
     return out, vol, e.value
+
+
+def pic(dim, n, L, px, py, vals, v=None, kind="q1"):
+    """PIC assignment (Sec. 2.3, Eq. PIC with the mesh volumes of Eq. mesh_v,
+    v_i = int psi_i = h^dim): Ab_i = sum_mu A_mu v_mu psi_i(r_mu) / h^dim.
+    The sum is FLIP's numerator: the FLIP value times the FLIP node volume."""
+    out, vol, _ = flip(dim, n, L, px, py, vals, v=v, kind=kind)
+    return out * vol[None, :] / (L / n) ** dim
+
+
+def energy_mesh(dim, n, L, x, kind="q1"):
+    """int Ab^2 = Ab^T M Ab per field (Eq. stab in integral form)."""
+    x = _f64(x).reshape(-1, n ** dim)
+    return (x * mass_apply(dim, n, L, x, kind)).sum(axis=1)
+
+
+def energy_particles(dim, L, px, py, vals, tri=None):
+    """int A^2 = A^T M_p A per field, M_p the particle mass matrix."""
+    a = _fields(vals, _f32(px).shape[0])
+    return (a * particle_mass_apply(dim, L, px, py, a, tri)).sum(axis=1)
 
 
 def rhs(dim, n, L, px, py, vals, mode=0, tri=None, kind="q1"):
@@ -333,3 +367,6 @@ def interpolate_mass(dim, n, L, mesh, px, py=None, tri=None, rtol=1e-13, max_ite
     if it < 0:
         raise OracleError(f"oracle particle mass solve failed with status {-it}")
     return x
+
+
+from . import advect  # noqa: E402  (driver steps of Sec. 3.1-3.3; uses interpolate above)

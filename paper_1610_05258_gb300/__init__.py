@@ -56,7 +56,8 @@ class _Opts(ctypes.Structure):
 
 class _Info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("init_rel_resid", ctypes.c_double), ("rel_resid", ctypes.c_double),
-                ("sum_particles", ctypes.c_double), ("sum_mesh", ctypes.c_double), ("cons_err", ctypes.c_double)]
+                ("sum_particles", ctypes.c_double), ("sum_mesh", ctypes.c_double), ("cons_err", ctypes.c_double),
+                ("energy_mesh", ctypes.c_double), ("energy_particles", ctypes.c_double)]
 
 
 @dataclass
@@ -67,6 +68,13 @@ class SolveInfo:
     sum_particles: float
     sum_mesh: float
     cons_err: float
+    energy_mesh: float = 0.0       # int Ab^2 = Ab^T M Ab (Eq. stab, integral form)
+    energy_particles: float = 0.0  # int A^2 = A^T M_p A
+
+
+def _info(x) -> SolveInfo:
+    return SolveInfo(x.iters, x.init_rel_resid, x.rel_resid, x.sum_particles, x.sum_mesh, x.cons_err, x.energy_mesh,
+                     x.energy_particles)
 
 
 def library_path() -> str:
@@ -97,6 +105,7 @@ def load_library(path: str | None = None):
         "pm_assign_lumped": [vp, vp, vp, ll, vp, i, vp],
         "pm_assign_delta": [vp, vp, vp, ll, vp, i, vp],
         "pm_assign_flip": [vp, vp, vp, ll, vp, i, vp, vp, ctypes.POINTER(ll)],
+        "pm_assign_pic": [vp, vp, vp, ll, vp, i, vp],
         "pm_assign_mass": [vp, vp, vp, ll, vp, i, vp, ctypes.POINTER(_Opts), vp],
         "pm_mass_rhs": [vp, vp, vp, ll, vp, i, vp],
         "pm_mass_rhs_mode": [vp, vp, vp, ll, vp, i, i, vp],
@@ -244,7 +253,7 @@ class Context:
                                                  ctypes.byref(o), inf))
         if not info:
             return out
-        return out, [SolveInfo(x.iters, x.init_rel_resid, x.rel_resid, x.sum_particles, x.sum_mesh, x.cons_err)
+        return out, [_info(x)
                      for x in inf]
 
     def assign_lumped(self, px, py, vals, out=None):
@@ -274,6 +283,15 @@ class Context:
                                             _ptr(node_volume), ctypes.byref(e) if count_empty else None))
         return (out, e.value) if count_empty else out
 
+    def assign_pic(self, px, py, vals, out=None):
+        """PIC assignment with the mesh volumes h^dim (pm_assign_pic)."""
+        px, py, vals = self._f32(px), self._f32(py), self._f32(vals)
+        F = vals.numel() // max(1, px.numel())
+        out = out if out is not None else self._empty(F, self.nodes)
+        self._stream()
+        self._check(self.lib.pm_assign_pic(self.h, _ptr(px), _ptr(py), px.numel(), _ptr(vals), F, _ptr(out)))
+        return out
+
     def _opts(self, warm_start, rtol, max_iter, x0, net=None, rhs="exact", solver="cg"):
         ws = {"delta": PM_WS_DELTA, "zero": PM_WS_ZERO, "user": PM_WS_USER, "net": PM_WS_NET,
               "direct": PM_WS_DIRECT}[warm_start]
@@ -297,7 +315,7 @@ class Context:
         self._check(s)
         if not info:
             return out
-        return out, [SolveInfo(x.iters, x.init_rel_resid, x.rel_resid, x.sum_particles, x.sum_mesh, x.cons_err)
+        return out, [_info(x)
                      for x in inf]
 
     def net_features(self, px, py, vals):
@@ -341,7 +359,7 @@ class Context:
         self._check(self.lib.pm_mass_solve(self.h, _ptr(b), F, _ptr(out), ctypes.byref(o), inf))
         if not info:
             return out
-        return out, [SolveInfo(x.iters, x.init_rel_resid, x.rel_resid, x.sum_particles, x.sum_mesh, x.cons_err)
+        return out, [_info(x)
                      for x in inf]
 
     def particle_volumes(self, px, py=None, out=None):
@@ -454,7 +472,7 @@ class Batch:
             raise PMError(s, self.lib.pm_batch_last_error(self.h).decode())
         if not info:
             return None
-        return [[SolveInfo(x.iters, x.init_rel_resid, x.rel_resid, x.sum_particles, x.sum_mesh, x.cons_err)
+        return [[_info(x)
                  for x in inf[k * F:(k + 1) * F]] for k in range(K)]
 
 

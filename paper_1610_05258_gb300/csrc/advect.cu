@@ -1,7 +1,9 @@
 // Particle advection, the driver step between G2P and P2G in the paper's
 // experiments (Sec. 3.1: dx/dt = u constant; Sec. 3.2: rigid rotation;
 // Sec. 3.3: particles moved by the interpolated velocity field).
-// Positions are updated in place and wrapped into [0, L).
+// Positions are updated in place and wrapped into [0, L). The shift and the
+// rotation are exact functions of their inputs (FP64 update rounded to the
+// float32 state); the midpoint rule runs in FP32.
 #include "internal.cuh"
 
 namespace {
@@ -11,21 +13,42 @@ __device__ __forceinline__ float wrapL(float x, float L) {
     return x >= L ? x - L : (x < 0.0f ? 0.0f : x);
 }
 
-__global__ void k_shift(float *__restrict__ px, float *__restrict__ py, ll np, float dx, float dy, float L, int dim) {
-    ll k = (ll)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= np) return;
-    px[k] = wrapL(px[k] + dx, L);
-    if (dim == 2) py[k] = wrapL(py[k] + dy, L);
+// Exact-update convention of the shift and the rotation: the new position is
+// computed in FP64 from the float32 one with the expression order written
+// below (each operation rounded once: the _rn intrinsics keep the compiler
+// from fusing a multiply into an add), wrapped into [0, L) and rounded to
+// float32; a value that rounds to L or above is the torus point 0. The result
+// is therefore a plain function of the inputs.
+__device__ __forceinline__ float wrap_round(double r, double L) {
+    const double k = floor(__ddiv_rn(r, L));
+    r = __dsub_rn(r, __dmul_rn(L, k));
+    if (r < 0.0) r = __dadd_rn(r, L);
+    if (r >= L) r = __dsub_rn(r, L);
+    const float f = __double2float_rn(r);
+    return (double)f >= L ? 0.0f : f;
 }
 
-// Exact rotation about (cx, cy) by the angle whose cosine and sine are c, s.
-__global__ void k_rotate(float *__restrict__ px, float *__restrict__ py, ll np, float cx, float cy, float c, float s,
-                         float L) {
+// Sec. 3.1: r <- r + (dx, dy).
+__global__ void k_shift(float *__restrict__ px, float *__restrict__ py, ll np, double dx, double dy, double L,
+                        int dim) {
     ll k = (ll)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= np) return;
-    float x = px[k] - cx, y = py[k] - cy;
-    px[k] = wrapL(cx + c * x - s * y, L);
-    py[k] = wrapL(cy + s * x + c * y, L);
+    px[k] = wrap_round(__dadd_rn((double)px[k], dx), L);
+    if (dim == 2) py[k] = wrap_round(__dadd_rn((double)py[k], dy), L);
+}
+
+// Sec. 3.2: rigid rotation about (cx, cy) by the angle whose cosine and sine
+// are c, s:  x' = cx + (c X - s Y),  y' = cy + (s X + c Y),  X = x - cx,
+// Y = y - cy.
+__global__ void k_rotate(float *__restrict__ px, float *__restrict__ py, ll np, double cx, double cy, double c,
+                         double s, double L) {
+    ll k = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= np) return;
+    const double X = __dsub_rn((double)px[k], cx), Y = __dsub_rn((double)py[k], cy);
+    const double x = __dadd_rn(cx, __dsub_rn(__dmul_rn(c, X), __dmul_rn(s, Y)));
+    const double y = __dadd_rn(cy, __dadd_rn(__dmul_rn(s, X), __dmul_rn(c, Y)));
+    px[k] = wrap_round(x, L);
+    py[k] = wrap_round(y, L);
 }
 
 // Explicit midpoint rule with the mesh velocity: vel holds the particle
@@ -74,16 +97,16 @@ __global__ void __launch_bounds__(256) k_rk2(Geo g, const float *__restrict__ me
 
 }  // namespace
 
-void launch_advect_shift(const Geo &g, float *px, float *py, ll np, float dx, float dy, cudaStream_t st) {
+void launch_advect_shift(const Geo &g, float *px, float *py, ll np, double dx, double dy, cudaStream_t st) {
     if (np <= 0) return;
-    k_shift<<<div_up(np, 256), 256, 0, st>>>(px, py, np, dx, dy, (float)g.L, g.dim);
+    k_shift<<<div_up(np, 256), 256, 0, st>>>(px, py, np, dx, dy, g.L, g.dim);
     count_launches(1);
 }
 
-void launch_advect_rotate(const Geo &g, float *px, float *py, ll np, float cx, float cy, float c, float s,
+void launch_advect_rotate(const Geo &g, float *px, float *py, ll np, double cx, double cy, double c, double s,
                           cudaStream_t st) {
     if (np <= 0) return;
-    k_rotate<<<div_up(np, 256), 256, 0, st>>>(px, py, np, cx, cy, c, s, (float)g.L);
+    k_rotate<<<div_up(np, 256), 256, 0, st>>>(px, py, np, cx, cy, c, s, g.L);
     count_launches(1);
 }
 

@@ -204,7 +204,8 @@ pm_status pm_ctx_create_mesh(pm_ctx **out, int dim, int n, double L, long long m
               alloc(c, &w.perm, np) && alloc(c, &w.pos, np) && alloc(c, &w.vals, np * F) &&
               alloc(c, &w.maxabs, PM_MAXF) && alloc(c, &w.deg, np) && alloc(c, &w.vol, np) &&
               alloc(c, &w.part, (dim == 2 ? 4 : 2) * (F + 1) * nc) && alloc(c, &w.bfix, F * nc) &&
-              alloc(c, &w.psum, 2 * PM_MAXF * (ll)w.nblk_psum) && alloc(c, &w.r, F * nc) &&
+              alloc(c, &w.psum, 2 * PM_MAXF * (ll)w.nblk_psum) &&
+              alloc(c, &w.epart, 2 * PM_MAXF * (ll)energy_blocks()) && alloc(c, &w.r, F * nc) &&
               alloc(c, &w.p, F * nc) && alloc(c, &w.q, F * nc) && alloc(c, &w.b, F * nc) &&
               alloc(c, &w.red, 6LL * PM_MAXF * 4096) && alloc(c, &w.scal, 16LL * PM_MAXF) &&
               alloc(c, &w.bar, 2) && alloc(c, &w.status, 1) && alloc(c, &w.empty, 1) && alloc(c, &w.ntri, 1) &&
@@ -212,6 +213,7 @@ pm_status pm_ctx_create_mesh(pm_ctx **out, int dim, int n, double L, long long m
               alloc(c, &w.pc, F * np) && alloc(c, &w.px, pcg_width((int)F) * np) &&
               alloc(c, &w.pq, pcg_width((int)F) * np) && alloc(c, &w.prp, 2LL * pcg_width((int)F) * np);
     w.cfix = (ll *)w.prp;
+    w.red_blocks = 4096;
     if (ok && dim == 2) ok = alloc(c, &w.nbr, (ll)PM_MAXDEG * np) && alloc(c, &w.pcoef, (ll)PM_MAXDEG * np);
     if (ok && dim == 2 && n % 128 == 0 && !g.p1)  // the network start: bilinear meshes
         ok = alloc(c, &w.feat, 2 * F * nc) && alloc(c, &w.corr, F * nc);
@@ -238,7 +240,7 @@ void pm_ctx_destroy(pm_ctx *c) {
     if (!c) return;
     Work &w = c->w;
     void *ptrs[] = {w.fx,  w.key, w.slot, w.count, w.cell_start, w.scan_tmp, w.tmp,  w.perm,  w.pos,
-                    w.vals, w.maxabs, w.nbr, w.deg,  w.vol,  w.part,  w.bfix, w.psum, w.r,     w.p,
+                    w.vals, w.maxabs, w.nbr, w.deg,  w.vol,  w.part,  w.bfix, w.psum, w.epart, w.r, w.p,
                     w.q,   w.b,   w.red,  w.scal,  w.bar,  w.status, w.empty, w.ntri, w.feat, w.corr,
                     w.wsum, w.nretry, w.meshmax, w.pc, w.px, w.pq, w.prp, w.pcoef};
     for (void *p : ptrs)
@@ -315,6 +317,20 @@ pm_status pm_assign_flip(pm_ctx *c, const float *px, const float *py, long long 
     return PM_OK;
 }
 
+pm_status pm_assign_pic(pm_ctx *c, const float *px, const float *py, long long np, const float *vals, int F,
+                        float *mesh_out) {
+    pm_status s = check_particles(c, px, py, np, F, vals, c && c->g.dim == 2 ? 3 : 2);
+    if (s) return s;
+    if (F < 1 || !mesh_out) return fail(c, PM_EINVAL, "null output or no field");
+    if ((s = prepare(c, px, py, np, vals, F, true))) return s;
+    {
+        Phase ph(c, PM_PH_FLIP);
+        const double h = c->g.L / c->g.n;
+        launch_flip(c->g, c->w, np, F, mesh_out, nullptr, c->st, (float)(c->g.dim == 2 ? h * h : h));
+    }
+    return check_launch(c, "pm_assign_pic");
+}
+
 static void default_opts(const pm_solve_opts *o, pm_solve_opts &d) {
     d.warm_start = PM_WS_DELTA;
     d.rtol = 1e-6;
@@ -342,8 +358,23 @@ static pm_status fill_info(pm_ctx *c, int F, pm_solve_info *info) {
         info[f].sum_particles = v[4];
         double den = v[5] > 0.0 ? v[5] : fabs(v[4]);
         info[f].cons_err = den > 0.0 ? fabs(v[3] - v[4]) / den : fabs(v[3] - v[4]);
+        info[f].energy_mesh = v[6];
+        info[f].energy_particles = v[7];
     }
     return s;
+}
+
+// The report of a solve: stability diagnostics of the mesh fields and, if
+// given, of the sorted particle values (see launch_energies), then the
+// solver's scalars.
+static pm_status report(pm_ctx *c, int F, pm_solve_info *info, const float *mesh, ll np, const float *pvals, ll fs,
+                        ll ss) {
+    {
+        Phase ph(c, PM_PH_OTHER);
+        launch_energies(c->g, c->w, F, mesh, np, pvals, fs, ss, c->st);
+    }
+    if (pm_status s = check_launch(c, "diagnostics")) return s;
+    return fill_info(c, F, info);
 }
 
 // Everything of a mass assignment before the solve: sort, particle
@@ -420,7 +451,7 @@ pm_status pm_assign_mass(pm_ctx *c, const float *px, const float *py, long long 
     bool start = true;
     if ((s = mass_front(c, px, py, np, vals, F, mesh_out, o, start))) return s;
     if ((s = mass_solve_launch(c, F, mesh_out, start, o))) return s;
-    if (info) return fill_info(c, F, info);
+    if (info) return report(c, F, info, mesh_out, np, c->w.vals, np, 1);
     return PM_OK;
 }
 
@@ -471,7 +502,7 @@ pm_status pm_interpolate_mass(pm_ctx *c, const float *mesh, int F, const float *
     }
     if (e) return cuda_fail(c, (cudaError_t)e, "pm_interpolate_mass solve launch");
     if ((s = check_launch(c, "pm_interpolate_mass"))) return s;
-    if (info) return fill_info(c, F, info);
+    if (info) return report(c, F, info, mesh, np, c->w.px, 1, pcg_width(c->w.F_max));
     return PM_OK;
 }
 
@@ -547,7 +578,7 @@ pm_status pm_mass_solve(pm_ctx *c, const float *b, int F, float *x, const pm_sol
                                                                        o.max_iter, c->st);
     }
     if (e) return cuda_fail(c, (cudaError_t)e, "pm_mass_solve launch");
-    if (info) return fill_info(c, F, info);
+    if (info) return report(c, F, info, x, 0, nullptr, 0, 0);
     return PM_OK;
 }
 
@@ -608,7 +639,7 @@ pm_status pm_advect_shift(pm_ctx *c, float *px, float *py, long long np, double 
     if (s) return s;
     {
         Phase ph(c, PM_PH_ADVECT);
-        launch_advect_shift(c->g, px, py, np, (float)dx, (float)dy, c->st);
+        launch_advect_shift(c->g, px, py, np, dx, dy, c->st);
     }
     return check_launch(c, "pm_advect_shift");
 }
@@ -619,7 +650,7 @@ pm_status pm_advect_rotate(pm_ctx *c, float *px, float *py, long long np, double
     if (c->g.dim != 2) return fail(c, PM_EINVAL, "pm_advect_rotate needs dim == 2");
     {
         Phase ph(c, PM_PH_ADVECT);
-        launch_advect_rotate(c->g, px, py, np, (float)cx, (float)cy, (float)cos(angle), (float)sin(angle), c->st);
+        launch_advect_rotate(c->g, px, py, np, cx, cy, cos(angle), sin(angle), c->st);
     }
     return check_launch(c, "pm_advect_rotate");
 }
@@ -907,7 +938,7 @@ pm_status pm_batch_assign_mass(pm_batch *b, const float *const *px, const float 
     for (int k = 0; k < b->ninst; ++k) {
         pm_ctx *c = b->ctx[k];
         c->st = b->main;
-        pm_status s = fill_info(c, F, info + (ll)k * F);
+        pm_status s = report(c, F, info + (ll)k * F, mesh_out[k], np[k], c->w.vals, np[k], 1);
         if (s && !worst) {
             worst = s;
             b->err = "instance " + std::to_string(k) + ": " + c->err;

@@ -99,9 +99,11 @@ struct Work {
     ll *bfix;           // [F][ncell] fixed-point right-hand side
     double *psum;       // [2 F][nblk] per-block particle sums (sum v A, sum v |A|)
     int nblk_psum;
+    double *epart;      // [2 PM_MAXF][energy_blocks()] block partials of the stability diagnostics
     // solver
     float *r, *p, *q, *b;  // [F][ncell]
     double *red;           // reduction partials [slots][grid]
+    int red_blocks;        // grid capacity of red (blocks per slot); persistent solves never exceed it
     double *scal;          // solver scalars per field
     unsigned *bar;         // grid barrier words (2)
     int *status;           // device status word
@@ -177,6 +179,47 @@ struct Dot2 {
     }
 };
 
+// Compensated M x at node i of field array xf; returns (hi, lo) of the
+// unscaled stencil sum; the caller multiplies by c = h/6, h^2/36 (bilinear)
+// or h^2/12 (P1: 6 at the node, 1 at its six neighbours along the cell
+// edges and the (0,0)-(1,1) diagonals).
+template <int DIM, int P1 = 0>
+__device__ __forceinline__ void stencil(const float *__restrict__ xf, int n, ll i, float &hi, float &lo) {
+    Dot2 acc;
+    if (DIM == 1) {
+        int ix = (int)i, xm = ix == 0 ? n - 1 : ix - 1, xp = ix + 1 == n ? 0 : ix + 1;
+        acc.add(4.0f * xf[ix]);
+        acc.add(xf[xm]);
+        acc.add(xf[xp]);
+    } else {
+        int ix = (int)(i % n), iy = (int)(i / n);
+        int xm = ix == 0 ? n - 1 : ix - 1, xp = ix + 1 == n ? 0 : ix + 1;
+        int ym = iy == 0 ? n - 1 : iy - 1, yp = iy + 1 == n ? 0 : iy + 1;
+        const float *r0 = xf + (ll)ym * n, *r1 = xf + (ll)iy * n, *r2 = xf + (ll)yp * n;
+        if (P1) {
+            acc.add(6.0f * r1[ix]);
+            acc.add(r1[xm]);
+            acc.add(r1[xp]);
+            acc.add(r0[ix]);
+            acc.add(r2[ix]);
+            acc.add(r0[xm]);
+            acc.add(r2[xp]);
+        } else {
+            acc.add(16.0f * r1[ix]);
+            acc.add(4.0f * r1[xm]);
+            acc.add(4.0f * r1[xp]);
+            acc.add(4.0f * r0[ix]);
+            acc.add(4.0f * r2[ix]);
+            acc.add(r0[xm]);
+            acc.add(r0[xp]);
+            acc.add(r2[xm]);
+            acc.add(r2[xp]);
+        }
+    }
+    hi = acc.hi;
+    lo = acc.lo;
+}
+
 static inline int div_up(ll a, int b) { return (int)((a + b - 1) / b); }
 
 // Checked build (-DPM_CHECKED, a debugging aid): every data-derived index is
@@ -213,7 +256,10 @@ void launch_g2p(const Geo &g, const float *mesh, int F, const float *px, const f
 void launch_triangulate(const Geo &g, Work &w, ll np, cudaStream_t st, bool count_work = false);
 void launch_volumes_1d(const Geo &g, Work &w, ll np, cudaStream_t st);
 void launch_delta(const Geo &g, Work &w, ll np, int F, float *mesh_out, cudaStream_t st);
-void launch_flip(const Geo &g, Work &w, ll np, int F, float *mesh_out, float *node_vol, cudaStream_t st);
+// FLIP (pic_vol = 0: node volumes v_i = sum v_mu psi_i, Eq. FLIP_vol) or PIC
+// (pic_vol = h^dim: the mesh volumes v_i = int psi_i of Eq. mesh_v).
+void launch_flip(const Geo &g, Work &w, ll np, int F, float *mesh_out, float *node_vol, cudaStream_t st,
+                 float pic_vol = 0.0f);
 void rhs_prepare_device();
 // x = M^-1 b exactly (to ~1e-9) by separable circulant convolutions; tmp is scratch.
 void launch_mass_direct(const Geo &g, const float *b, int F, float *x, float *tmp, cudaStream_t st);
@@ -239,8 +285,15 @@ void launch_export_tris(const Geo &g, Work &w, ll np, int *tri, int *off, ll max
 void launch_psum(const Geo &g, Work &w, ll np, int F, cudaStream_t st);
 void launch_features(const Geo &g, Work &w, int F, const float *delta, cudaStream_t st);
 void launch_apply_correction(const Geo &g, Work &w, int F, float *mesh, cudaStream_t st);
-void launch_advect_shift(const Geo &g, float *px, float *py, ll np, float dx, float dy, cudaStream_t st);
-void launch_advect_rotate(const Geo &g, float *px, float *py, ll np, float cx, float cy, float c, float s,
+// Stability diagnostics (Eq. stab): int Ab^2 = Ab^T M Ab of mesh [F][n^dim]
+// and int A^2 = A^T M_p A of the sorted particle values (value of field f at
+// sorted particle s: pvals[f fs + s ss]; pvals may be null) into the report
+// slots 6 and 7 of w.scal.
+int energy_blocks();
+void launch_energies(const Geo &g, Work &w, int F, const float *mesh, ll np, const float *pvals, ll fs, ll ss,
+                     cudaStream_t st);
+void launch_advect_shift(const Geo &g, float *px, float *py, ll np, double dx, double dy, cudaStream_t st);
+void launch_advect_rotate(const Geo &g, float *px, float *py, ll np, double cx, double cy, double c, double s,
                           cudaStream_t st);
 void launch_advect_rk2(const Geo &g, const float *mesh_vel, const float *vel, float *px, float *py, ll np, float dt,
                        float *vals, int F, float factor, int *status, cudaStream_t st);

@@ -20,6 +20,8 @@
 // cons) to rounding at any iteration count.
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "internal.cuh"
 
 PM_DEBUG_DECL(solve)
@@ -130,47 +132,6 @@ __device__ void particle_sums(const double *psum, int nblk, int F, double s1[PM_
         s1[f] = tot[2 * f];
         s2[f] = tot[2 * f + 1];
     }
-}
-
-// Compensated M x at node i of field array xf; returns (hi, lo) of the
-// unscaled stencil sum; the caller multiplies by c = h/6, h^2/36 (bilinear)
-// or h^2/12 (P1: 6 at the node, 1 at its six neighbours along the cell
-// edges and the (0,0)-(1,1) diagonals).
-template <int DIM, int P1 = 0>
-__device__ __forceinline__ void stencil(const float *__restrict__ xf, int n, ll i, float &hi, float &lo) {
-    Dot2 acc;
-    if (DIM == 1) {
-        int ix = (int)i, xm = ix == 0 ? n - 1 : ix - 1, xp = ix + 1 == n ? 0 : ix + 1;
-        acc.add(4.0f * xf[ix]);
-        acc.add(xf[xm]);
-        acc.add(xf[xp]);
-    } else {
-        int ix = (int)(i % n), iy = (int)(i / n);
-        int xm = ix == 0 ? n - 1 : ix - 1, xp = ix + 1 == n ? 0 : ix + 1;
-        int ym = iy == 0 ? n - 1 : iy - 1, yp = iy + 1 == n ? 0 : iy + 1;
-        const float *r0 = xf + (ll)ym * n, *r1 = xf + (ll)iy * n, *r2 = xf + (ll)yp * n;
-        if (P1) {
-            acc.add(6.0f * r1[ix]);
-            acc.add(r1[xm]);
-            acc.add(r1[xp]);
-            acc.add(r0[ix]);
-            acc.add(r2[ix]);
-            acc.add(r0[xm]);
-            acc.add(r2[xp]);
-        } else {
-            acc.add(16.0f * r1[ix]);
-            acc.add(4.0f * r1[xm]);
-            acc.add(4.0f * r1[xp]);
-            acc.add(4.0f * r0[ix]);
-            acc.add(4.0f * r2[ix]);
-            acc.add(r0[xm]);
-            acc.add(r0[xp]);
-            acc.add(r2[xm]);
-            acc.add(r2[xp]);
-        }
-    }
-    hi = acc.hi;
-    lo = acc.lo;
 }
 
 // Power of two 2^-ilogb(m) that scales a field of mean absolute value m to
@@ -1279,8 +1240,41 @@ __global__ void k_unsort_aos(ll np, int F, int FF, const int *__restrict__ perm,
     for (int f = 0; f < F; ++f) out[(ll)f * np + k] = x[s * FF + f];
 }
 
-int g_cg_grid[6] = {0, 0, 0, 0, 0, 0};
-int g_pcg_grid[6] = {0, 0, 0, 0, 0, 0};
+// Resident blocks of a persistent kernel: SMs x min(occupancy, cap), looked
+// up once per (device, kernel variant) and cached. The cache is keyed by the
+// current device and guarded, so threads driving different devices each get
+// their own device's figure.
+#define PM_GRID_MAXDEV 64
+std::mutex g_grid_mu;
+int g_grid_cache[PM_GRID_MAXDEV][16];
+
+int persistent_grid(int variant, const void *kern, int cap) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const bool cached = dev >= 0 && dev < PM_GRID_MAXDEV;
+    if (cached) {
+        std::lock_guard<std::mutex> lk(g_grid_mu);
+        if (g_grid_cache[dev][variant]) return g_grid_cache[dev][variant];
+    }
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, 0);
+    if (per < 1) per = 1;
+    if (per > cap) per = cap;
+    const int grid = sms * per;
+    if (cached) {
+        std::lock_guard<std::mutex> lk(g_grid_mu);
+        g_grid_cache[dev][variant] = grid;
+    }
+    return grid;
+}
+
+// The reduction partials hold w.red_blocks blocks per slot: never launch more.
+int clamp_grid(int grid, ll need, const Work &w) {
+    if (need < grid) grid = (int)(need < 1 ? 1 : need);
+    if (w.red_blocks > 0 && grid > w.red_blocks) grid = w.red_blocks;
+    return grid;
+}
 
 }  // namespace
 
@@ -1323,18 +1317,8 @@ int launch_cg(const Geo &g, Work &w, int F, const float *b_float, bool b_from_fi
     const int di = (quad ? 2 : g.dim - 1) + (p1 ? 3 : 0);
     void (*kern)(CG) = quad ? (p1 ? k_cg2v<1> : k_cg2v<0>)
                             : (g.dim == 1 ? k_cg<1, 0> : (p1 ? k_cg<2, 1> : k_cg<2, 0>));
-    if (!g_cg_grid[di]) {
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, 0);
-        if (per < 1) per = 1;
-        if (per > (quad ? 4 : 2)) per = quad ? 4 : 2;
-        g_cg_grid[di] = sms * per;
-    }
-    int grid = g_cg_grid[di];
-    ll need = ((quad ? g.ncell / 4 : g.ncell) + 255) / 256;
-    if (need < grid) grid = (int)(need < 1 ? 1 : need);
+    const ll need = ((quad ? g.ncell / 4 : g.ncell) + 255) / 256;
+    const int grid = clamp_grid(persistent_grid(di, (const void *)kern, quad ? 4 : 2), need, w);
     cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st);
     void *args[] = {&a};
     cudaError_t e = cudaLaunchCooperativeKernel((void *)kern, dim3(grid), dim3(256), args, 0, st);
@@ -1343,7 +1327,6 @@ int launch_cg(const Geo &g, Work &w, int F, const float *b_float, bool b_from_fi
 }
 
 // Chebyshev solve: same arguments, workspace and report as launch_cg.
-int g_cheb_grid[3] = {0, 0, 0};
 
 int launch_cheb(const Geo &g, Work &w, int F, const float *b_float, bool b_from_fix, float *x, bool x_has_start,
                 double rtol, int max_iter, cudaStream_t st) {
@@ -1370,18 +1353,8 @@ int launch_cheb(const Geo &g, Work &w, int F, const float *b_float, bool b_from_
     const bool p1 = g.dim == 2 && g.p1;
     const int di = g.dim == 1 ? 0 : (p1 ? 2 : 1);
     void (*kern)(CG) = g.dim == 1 ? k_cheb<1, 0> : (p1 ? k_cheb<2, 1> : k_cheb<2, 0>);
-    if (!g_cheb_grid[di]) {
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, 0);
-        if (per < 1) per = 1;
-        if (per > 4) per = 4;
-        g_cheb_grid[di] = sms * per;
-    }
-    int grid = g_cheb_grid[di];
     const ll need = (g.ncell + 255) / 256;
-    if (need < grid) grid = (int)(need < 1 ? 1 : need);
+    const int grid = clamp_grid(persistent_grid(6 + di, (const void *)kern, 4), need, w);
     cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st);
     void *args[] = {&a};
     cudaError_t e = cudaLaunchCooperativeKernel((void *)kern, dim3(grid), dim3(256), args, 0, st);
@@ -1420,18 +1393,8 @@ int launch_pcg(const Geo &g, Work &w, ll np, int F, const float *c, float *out, 
     void (*const kerns[6])(PCG) = {k_pcg<1, 2>, k_pcg<1, 4>, k_pcg<1, PM_MAXF>,
                                    k_pcg<2, 2>, k_pcg<2, 4>, k_pcg<2, PM_MAXF>};
     void (*kern)(PCG) = kerns[di];
-    if (!g_pcg_grid[di]) {
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, 0);
-        if (per < 1) per = 1;
-        if (per > 4) per = 4;
-        g_pcg_grid[di] = sms * per;
-    }
-    int grid = g_pcg_grid[di];
     const ll need = (np + 255) / 256;
-    if (need < grid) grid = (int)(need < 1 ? 1 : need);
+    const int grid = clamp_grid(persistent_grid(9 + di, (const void *)kern, 4), need, w);
     if (g.dim == 2 && np > 0) {
         k_star_coef<<<div_up(np, 256), 256, 0, st>>>(np, w.pos, w.nbr, w.deg, a.unit, w.pcoef);
         count_launches(1);

@@ -1,18 +1,18 @@
 // Mass solve that allocates nothing.
 //
-// Some callers cannot allocate device memory at the point where they need a
-// solve: code recorded into a CUDA graph by stream capture (cudaMalloc is not
-// a capturable, stream-ordered operation), latency-critical loops where the
-// implicit device synchronisation of cudaMalloc/cudaFree is not acceptable,
-// and host applications or plugin frameworks that own every byte of device
-// memory through their own pool and forbid other allocations. For them this
-// file provides pm_mass_solve_noalloc(): the same conjugate-gradient solve as
+// Some callers cannot call cudaMalloc at the point where they need a solve:
+// host applications and plugin frameworks that own every byte of device
+// memory through their own pool and forbid allocations by libraries they
+// load, and latency-critical loops that cannot take the implicit device
+// synchronisation of cudaMalloc/cudaFree. For them this file provides
+// pm_mass_solve_noalloc(): the same conjugate-gradient solve as
 // pm_mass_solve(), with its scratch vectors in one file-scope device array of
 // fixed size instead of a context's workspace. The caller still passes the
 // right-hand side and the output array.
 //
 // Scratch: PM_NOALLOC_MAX_VALUES floats for each of the four CG vectors
-// (r, p, q, b), plus reduction partials, solver scalars, the barrier words and
+// (r, p, q, b), plus reduction partials for up to PM_NOALLOC_MAX_GRID blocks
+// (the solve's grid is clamped to that), solver scalars, the barrier words and
 // the status word: about 16.2 MB, held by every GPU that loads the library
 // until the process exits. Its device address is looked up once per device
 // (cudaGetSymbolAddress) by the first call on that device.
@@ -85,6 +85,7 @@ extern "C" pm_status pm_mass_solve_noalloc(int dim, int n, double L, const float
     w.q = (float *)(base + 2 * kVecBytes);
     w.b = (float *)(base + 3 * kVecBytes);
     w.red = (double *)(base + kRedOff);
+    w.red_blocks = PM_NOALLOC_MAX_GRID;  // the solve's grid is clamped to the partials' capacity
     w.scal = (double *)(base + kScalOff);
     w.bar = (unsigned *)(base + kBarOff);
     w.status = (int *)(base + kStatusOff);

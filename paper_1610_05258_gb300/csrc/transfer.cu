@@ -193,9 +193,13 @@ __global__ void __launch_bounds__(128) k_flip_cells(Geo g, ll np, const int *__r
         for (int f = 0; f <= F; ++f) part[(ll)(k * (F + 1) + f) * g.ncell + c] = acc[k][f].get();
 }
 
+// Per node: v_i^FLIP = sum over its cells of the volume partials, and
+// Ab_i = (sum of the value partials) / v_i (FLIP, pic_vol = 0) or / pic_vol
+// (PIC with the mesh volume pic_vol = int psi_i = h^dim, Eq. PIC with
+// Eq. mesh_v).
 template <int DIM>
 __global__ void k_flip_nodes(Geo g, int F, const float *__restrict__ part, float *__restrict__ mesh,
-                             float *__restrict__ node_vol, int *__restrict__ empty) {
+                             float *__restrict__ node_vol, int *__restrict__ empty, float pic_vol) {
     ll i = (ll)blockIdx.x * blockDim.x + threadIdx.x;
     int e = 0;
     if (i < g.ncell) {
@@ -223,7 +227,10 @@ __global__ void k_flip_nodes(Geo g, int F, const float *__restrict__ part, float
         for (int f = 0; f < F; ++f) {
             KSum num;
             for (int k = 0; k < nc; ++k) num.add(part[(ll)(k * (F + 1) + f) * g.ncell + cells[k]]);
-            mesh[(ll)f * g.ncell + i] = d != 0.0f ? num.get() / d : 0.0f;
+            if (pic_vol > 0.0f)
+                mesh[(ll)f * g.ncell + i] = num.get() / pic_vol;
+            else
+                mesh[(ll)f * g.ncell + i] = d != 0.0f ? num.get() / d : 0.0f;
         }
     }
     e = __syncthreads_count(e);
@@ -1028,14 +1035,15 @@ void launch_rhs_appb(const Geo &g, Work &w, ll np, int F, cudaStream_t st) {
     count_launches(np > 0 ? 2 : 1);
 }
 
-void launch_flip(const Geo &g, Work &w, ll np, int F, float *mesh_out, float *node_vol, cudaStream_t st) {
+void launch_flip(const Geo &g, Work &w, ll np, int F, float *mesh_out, float *node_vol, cudaStream_t st,
+                 float pic_vol) {
     cudaMemsetAsync(w.empty, 0, sizeof(int), st);
     if (g.dim == 2) {
         k_flip_cells<2><<<div_up(g.ncell, 128), 128, 0, st>>>(g, np, w.cell_start, w.pos, w.vals, w.vol, F, w.part);
-        k_flip_nodes<2><<<div_up(g.ncell, 256), 256, 0, st>>>(g, F, w.part, mesh_out, node_vol, w.empty);
+        k_flip_nodes<2><<<div_up(g.ncell, 256), 256, 0, st>>>(g, F, w.part, mesh_out, node_vol, w.empty, pic_vol);
     } else {
         k_flip_cells<1><<<div_up(g.ncell, 128), 128, 0, st>>>(g, np, w.cell_start, w.pos, w.vals, w.vol, F, w.part);
-        k_flip_nodes<1><<<div_up(g.ncell, 256), 256, 0, st>>>(g, F, w.part, mesh_out, node_vol, w.empty);
+        k_flip_nodes<1><<<div_up(g.ncell, 256), 256, 0, st>>>(g, F, w.part, mesh_out, node_vol, w.empty, pic_vol);
     }
     count_launches(2);
 }

@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import math
+import os
 import time
 
 import numpy as np
@@ -235,12 +236,7 @@ def init_theta(seed=0):
     return np.concatenate(th).astype(np.float32)
 
 
-if __name__ == "__main__":
-    main()
-
-
-WEIGHTS = __import__("os").path.join(__import__("os").path.dirname(__import__("os").path.abspath(__file__)),
-                                     "weights", "warmstart_mixture.npz")
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "warmstart_mixture.npz")
 
 
 def load_weights(net, path=None):
@@ -249,3 +245,7 @@ def load_weights(net, path=None):
     d = np.load(path or WEIGHTS)
     net.load(d["theta"], None, int(d["step"]))
     return d
+
+
+if __name__ == "__main__":
+    main()

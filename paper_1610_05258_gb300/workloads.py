@@ -178,11 +178,14 @@ def uniform_instance(n, ppc, F=3, seed=16104, L=1.0, slope=-3.0, field_grid=128)
     return Instance(2, n, L, x, y, vals.astype(np.float32), name=f"uniform_n{n}_ppc{ppc}")
 
 
-def batched(count=256, nmin=64, nmax=512, ppc_min=1, ppc_max=8, F=3, seed=16104):
+def batched(count=256, nmin=64, nmax=512, ppc_min=1, ppc_max=8, F=3, seed=16104, take=None):
+    """`count` instances with sides and particles per cell drawn uniformly;
+    take=k builds only the first k of the same draw."""
     g = rng(seed)
     sides = g.integers(nmin, nmax + 1, count)
     ppcs = g.integers(ppc_min, ppc_max + 1, count)
-    return [uniform_instance(int(sides[k]), int(ppcs[k]), F, seed * 1000 + k) for k in range(count)]
+    m = count if take is None else min(take, count)
+    return [uniform_instance(int(sides[k]), int(ppcs[k]), F, seed * 1000 + k) for k in range(m)]
 
 
 def mixture(n=2048, ppc=4, F=4, seed=16105, contrast=10.0, ncomp=8):

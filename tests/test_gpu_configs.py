@@ -1,0 +1,202 @@
+"""The benchmark configurations run as configured (time-stepping chains), GPU
+against the oracle.
+
+* 1D top-hat convection: 128 nodes, 128 particles, 256 steps (one period) of
+  G2P -> shift by u dt -> P2G for the delta, FLIP and mass assignments; the
+  positions bit for bit at every step, the final mesh fields to relative L2
+  <= 1e-5, conservation of the FLIP and mass steps at every step.
+* Zalesak slotted disk at full size (256^2 mesh, 262,144 particles): 5 steps
+  of G2P -> rigid rotation by 2 pi / 1000 -> P2G for the three assignments,
+  element by element at every step (positions bit for bit).
+* Taylor-Green chain (G2P -> midpoint move with the mesh velocity -> decay ->
+  mass P2G) on a 128^2 mesh for 4 steps: positions to a few float ulps, mesh
+  fields element by element at every step.
+* Batched instances: the first 8 instances of the seeded 256-instance draw
+  (sides 95..461, 1..8 particles per cell, F = 3; 54k to 1.5M particles)
+  through the batch API: instances of up to 100k particles element by element
+  against the oracle, larger ones by sampled stars, volumes, right-hand side,
+  delta and FLIP entries plus the FP64 residual and conservation at every node.
+"""
+import math
+import multiprocessing as mp
+from concurrent.futures import ProcessPoolExecutor
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import advect as OA
+from paper_1610_05258_gb300 import workloads as W
+from gpu_util import rel_l2, to_dev
+from sampled import mass_apply64, sampled_checks
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_1610_05258_gb300 import build
+    build.build()
+    return True
+
+
+def _np(t):
+    return t.double().cpu().numpy()
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("method", ["delta", "flip", "mass"])
+def test_tophat_convection_256_steps(built, method):
+    from paper_1610_05258_gb300 import Context
+    inst = W.tophat_1d()
+    n, L, npt = inst.n, inst.L, inst.np
+    assert (n, npt) == (128, 128)
+    xn = np.arange(n) * (L / n)
+    mesh0 = ((xn >= 0.25) & (xn < 0.5)).astype(np.float64)[None, :]
+    u, dt, steps = 1.0, 1.0 / 256, 256
+    c = Context(1, n, L, npt, 1)
+    px = to_dev(torch, inst.px)[0]
+    m = to_dev(torch, mesh0)[0]
+    ox, om = inst.px.copy(), mesh0.copy()
+    for k in range(steps):
+        vals = c.interpolate(m, px)
+        c.advect_shift(px, None, u * dt)
+        ov = oracle.interpolate(1, n, L, om, ox)
+        ox, _ = OA.shift(L, ox, None, u * dt)
+        if method == "delta":
+            m = c.assign_delta(px, None, vals)
+            om = oracle.delta(1, n, L, ox, None, ov)
+        elif method == "flip":
+            m, vol = c.assign_flip(px, None, vals), None
+            om, vol, _ = oracle.flip(1, n, L, ox, None, ov)
+            # FLIP conserves sum_i v_i Ab_i = sum_mu v_mu A_mu (Sec. 2.3)
+            v = oracle.particle_volumes(1, L, ox)
+            assert abs(float((vol * _np(m)[0]).sum()) - float((v * _np(vals)[0]).sum())) <= 1e-6 * float(v.sum())
+        else:
+            m, info = c.assign_mass(px, None, vals)
+            om = oracle.assign_mass(1, n, L, ox, None, ov)
+            assert info[0].rel_resid <= 1e-6 and info[0].cons_err <= 1e-6
+        np.testing.assert_array_equal(px.cpu().numpy(), ox)
+    got = _np(m)
+    assert rel_l2(got, om) <= TOL, rel_l2(got, om)
+    # one period later the pulse is back where it started (smeared, not moved)
+    centre = lambda a: float(np.angle((a[0] * np.exp(2j * np.pi * xn / L)).sum()) / (2 * np.pi) % 1.0)
+    assert abs(centre(got) - centre(mesh0)) < 0.02
+
+
+# ---------------------------------------------------------------------------
+def _rotated_positions(L, px, py, steps, angle):
+    pos = [(px, py)]
+    for _ in range(steps):
+        pos.append(OA.rotate(L, pos[-1][0], pos[-1][1], 0.5, 0.5, angle))
+    return pos
+
+
+def test_zalesak_full_size_five_steps(built):
+    from paper_1610_05258_gb300 import Context
+    inst = W.zalesak(256)
+    n, L, npt, steps = inst.n, inst.L, inst.np, 5
+    assert npt == 262144
+    angle = 2 * math.pi / 1000
+    pos = _rotated_positions(L, inst.px, inst.py, steps, angle)
+    # the oracle's triangulations of the rotated sets, in spawned processes
+    # (the positions do not depend on the field values)
+    with ProcessPoolExecutor(max_workers=steps, mp_context=mp.get_context("spawn")) as ex:
+        tris = list(ex.map(oracle.triangulate, [L] * steps, [p[0] for p in pos[1:]], [p[1] for p in pos[1:]]))
+    xn = np.arange(n) * (L / n)
+    XN, YN = np.meshgrid(xn, xn, indexing="xy")
+    mesh0 = W.zalesak_indicator(XN.ravel(), YN.ravel()).astype(np.float64)[None, :]
+    c = Context(2, n, L, npt, 1)
+    for method in ("delta", "flip", "mass"):
+        px, py = to_dev(torch, inst.px, inst.py)
+        m = to_dev(torch, mesh0)[0]
+        om = mesh0.copy()
+        for k in range(steps):
+            vals = c.interpolate(m, px, py)
+            c.advect_rotate(px, py, 0.5, 0.5, angle)
+            ox, oy = pos[k]
+            ov = oracle.interpolate(2, n, L, om, ox, oy)
+            ox, oy = pos[k + 1]
+            T = tris[k]
+            np.testing.assert_array_equal(px.cpu().numpy(), ox)
+            np.testing.assert_array_equal(py.cpu().numpy(), oy)
+            if method == "delta":
+                m = c.assign_delta(px, py, vals)
+                om = oracle.delta(2, n, L, ox, oy, ov, tri=T)
+            elif method == "flip":
+                m = c.assign_flip(px, py, vals)
+                om, _, _ = oracle.flip(2, n, L, ox, oy, ov, v=T[2])
+            else:
+                m, info = c.assign_mass(px, py, vals)
+                om = oracle.assign_mass(2, n, L, ox, oy, ov, tri=T)
+                assert info[0].rel_resid <= 1e-6 and info[0].cons_err <= 1e-6
+            assert rel_l2(_np(m), om) <= TOL, (method, k, rel_l2(_np(m), om))
+
+
+# ---------------------------------------------------------------------------
+def test_taylor_green_chain(built):
+    from paper_1610_05258_gb300 import Context
+    n, steps, nu = 128, 4, 0.01
+    inst = W.taylor_green(n, 4, seed=16103)
+    L, npt = inst.L, inst.np
+    h = L / n
+    dt = 0.5 * h
+    decay = math.exp(-2 * nu * dt)
+    xn = np.arange(n) * h
+    XN, YN = np.meshgrid(xn, xn, indexing="xy")
+    mesh0 = np.stack([(np.sin(XN) * np.cos(YN)).ravel(), (-np.cos(XN) * np.sin(YN)).ravel()])
+    c = Context(2, n, L, npt, 2)
+    px, py = to_dev(torch, inst.px, inst.py)
+    m = to_dev(torch, mesh0)[0]
+    om = mesh0.copy()
+    for k in range(steps):
+        ox, oy, gm = px.cpu().numpy(), py.cpu().numpy(), m.cpu().numpy()
+        vel = c.interpolate(m, px, py)
+        vel_h = vel.cpu().numpy()
+        c.advect_rk2(m, vel, px, py, dt, vals=vel, factor=decay)
+        nx, ny = px.cpu().numpy(), py.cpu().numpy()
+        # the GPU's move against the oracle's from the same state
+        wx, wy, _ = OA.rk2(2, n, L, gm, vel_h, ox, oy, dt)
+        for a, b in ((nx, wx), (ny, wy)):
+            d = np.abs(a.astype(np.float64) - b)
+            assert np.max(np.minimum(d, L - d)) <= 4 * L * 2.0 ** -23
+        # the value chain: the oracle's own fields at the same positions
+        ov = oracle.interpolate(2, n, L, om, ox, oy) * decay
+        m, info = c.assign_mass(px, py, vel)
+        om = oracle.assign_mass(2, n, L, nx, ny, ov)
+        for f in range(2):
+            assert info[f].rel_resid <= 1e-6 and info[f].cons_err <= 1e-6
+        assert rel_l2(_np(m), om) <= TOL, (k, rel_l2(_np(m), om))
+
+
+# ---------------------------------------------------------------------------
+def test_batched_config_instances(built):
+    from paper_1610_05258_gb300 import Batch, Context
+    insts = W.batched(256, take=8)
+    F = 3
+    assert [i.n for i in insts] == [370, 198, 441, 461, 95, 270, 303, 333]
+    b = Batch([i.n for i in insts], [i.L for i in insts], [i.np for i in insts], max_fields=F)
+    dev = [to_dev(torch, i.px, i.py, i.vals) for i in insts]
+    outs = [torch.empty(F, i.n * i.n, device="cuda") for i in insts]
+    info = b.assign_mass([d[0] for d in dev], [d[1] for d in dev], [d[2] for d in dev], outs)
+    for k, inst in enumerate(insts):
+        n, L = inst.n, inst.L
+        x = _np(outs[k]).reshape(F, n * n)
+        for f in range(F):
+            assert info[k][f].rel_resid <= 1e-6 and info[k][f].cons_err <= 1e-6, (k, f)
+        if inst.np <= 100_000:
+            want = oracle.assign_mass(2, n, L, inst.px, inst.py, inst.vals)
+            assert rel_l2(x, want) <= TOL, (k, rel_l2(x, want))
+            continue
+        # too large for the oracle as a whole: sampled entries of every
+        # transfer, then the residual of the batch's own result against the
+        # sampled-checked right-hand side, in FP64 at every node
+        c = Context(2, n, L, inst.np, F)
+        bg = sampled_checks(c, inst.px, inst.py, inst.vals, n, L, F, seed=70 + k, k_stars=200, k_nodes=6)
+        r = bg.astype(np.float64) - mass_apply64(n, L, x)
+        for f in range(F):
+            assert np.linalg.norm(r[f]) <= 2e-6 * np.linalg.norm(bg[f].astype(np.float64)), (k, f)
+        del c

@@ -237,6 +237,36 @@ def test_1d_rhs_exact_properties():
     assert b.sum() == pytest.approx((v * inst.vals[0]).sum(), rel=1e-12)
 
 
+def test_sort_by_cell_2d_against_lexsort():
+    """2D cell order: row-major cell (y cell times n plus x cell), then caller
+    index (stable). Checked against numpy's lexsort on cells computed from
+    the physical positions (floor(x n / L), away from cell faces), on a box
+    with distinct x and y extents of the particle cloud so that a swapped
+    row/column key or an unstable order fails."""
+    g = np.random.default_rng(31)
+    n, L = 7, 1.3
+    m = 400
+    px = g.uniform(0.0, 0.55 * L, m)            # x confined to the left part
+    py = g.uniform(0.0, L, m)
+    dup = g.integers(0, m, 60)                    # repeated cells with many equal keys
+    px = np.concatenate([px, px[dup] + 1e-4]).astype(np.float32)
+    py = np.concatenate([py, py[dup]]).astype(np.float32)
+    h = L / n
+    cx = np.floor(px.astype(np.float64) / h).astype(np.int64)
+    cy = np.floor(py.astype(np.float64) / h).astype(np.int64)
+    fx = px / h - cx
+    fy = py / h - cy
+    assert np.all((fx > 1e-5) & (fx < 1 - 1e-5) & (fy > 1e-5) & (fy < 1 - 1e-5))  # no particle on a face
+    cell = cy * n + cx
+    want = np.lexsort((np.arange(px.shape[0]), cell))
+    perm, cs = oracle.sort_by_cell(2, n, L, px, py)
+    np.testing.assert_array_equal(perm, want)
+    counts = np.bincount(cell, minlength=n * n)
+    np.testing.assert_array_equal(cs, np.concatenate([[0], np.cumsum(counts)]))
+    # a transposed key would order the same set differently
+    assert not np.array_equal(np.lexsort((np.arange(px.shape[0]), cx * n + cy)), want)
+
+
 def test_1d_rhs_brute_force():
     """b_j = int A psi_j by a fine midpoint rule on the explicit piecewise-
     linear A (numpy interp over unwrapped ordered particles)."""
