@@ -215,6 +215,7 @@ pm_status pm_ctx_create_mesh(pm_ctx **out, int dim, int n, double L, long long m
     w.cfix = (ll *)w.prp;
     w.red_blocks = 4096;
     if (ok && dim == 2) ok = alloc(c, &w.nbr, (ll)PM_MAXDEG * np) && alloc(c, &w.pcoef, (ll)PM_MAXDEG * np);
+    if (ok && F > 1) ok = alloc(c, &w.mesh_il, (ll)g2p_width((int)F) * nc);
     if (ok && dim == 2 && n % 128 == 0 && !g.p1)  // the network start: bilinear meshes
         ok = alloc(c, &w.feat, 2 * F * nc) && alloc(c, &w.corr, F * nc);
     if (ok && cudaMallocHost((void **)&w.hstatus, sizeof(int)) != cudaSuccess) ok = false;
@@ -242,7 +243,7 @@ void pm_ctx_destroy(pm_ctx *c) {
     void *ptrs[] = {w.fx,  w.key, w.slot, w.count, w.cell_start, w.scan_tmp, w.tmp,  w.perm,  w.pos,
                     w.vals, w.maxabs, w.nbr, w.deg,  w.vol,  w.part,  w.bfix, w.psum, w.epart, w.r, w.p,
                     w.q,   w.b,   w.red,  w.scal,  w.bar,  w.status, w.empty, w.ntri, w.feat, w.corr,
-                    w.wsum, w.nretry, w.meshmax, w.pc, w.px, w.pq, w.prp, w.pcoef};
+                    w.wsum, w.nretry, w.meshmax, w.pc, w.px, w.pq, w.prp, w.pcoef, w.mesh_il};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (w.hstatus) cudaFreeHost(w.hstatus);
@@ -276,7 +277,7 @@ pm_status pm_interpolate(pm_ctx *c, const float *mesh, int F, const float *px, c
     if (np > 0 && (!mesh || !out)) return fail(c, PM_EINVAL, "null mesh or output array");
     {
         Phase ph(c, PM_PH_G2P);
-        launch_g2p(c->g, mesh, F, px, py, np, out, c->w.status, c->st);
+        launch_g2p(c->g, mesh, F, px, py, np, out, c->w.mesh_il, c->w.status, c->st);
     }
     return check_launch(c, "pm_interpolate");
 }

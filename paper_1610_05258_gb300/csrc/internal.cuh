@@ -122,6 +122,7 @@ struct Work {
     float *prp;            // [2][np][W] residual and search direction (r, then p)
     ll *cfix;              // = (ll *)prp: fixed-point c before conversion
     float *pcoef;          // [PM_MAXDEG][np] particle mass matrix rows (2D)
+    float *mesh_il;        // [ncell][g2p_width(F_max)] mesh fields interleaved per node (G2P)
 };
 
 // ---------------------------------------------------------------------------
@@ -251,8 +252,11 @@ void count_launches(int k);
 // Launchers (one per translation unit, all asynchronous on `st`).
 void launch_sort(const Geo &g, Work &w, const float *px, const float *py, ll np, const float *vals, int F,
                  cudaStream_t st);
+// G2P; il is workspace for the mesh fields interleaved per node
+// ([n^dim][g2p_width(F)] floats, unused for F = 1).
+int g2p_width(int F);
 void launch_g2p(const Geo &g, const float *mesh, int F, const float *px, const float *py, ll np, float *out,
-                int *status, cudaStream_t st);
+                float *il, int *status, cudaStream_t st);
 void launch_triangulate(const Geo &g, Work &w, ll np, cudaStream_t st, bool count_work = false);
 void launch_volumes_1d(const Geo &g, Work &w, ll np, cudaStream_t st);
 void launch_delta(const Geo &g, Work &w, ll np, int F, float *mesh_out, cudaStream_t st);
