@@ -271,17 +271,24 @@ def run_reference(args):
     if args.world > 1 and args.rank != 0:
         return
     hi = host_info()
-    P = hi["nproc"] or 1
+    P = getattr(args, "ref_procs", 0) or hi["nproc"] or 1
     times = []
     units = 0
-    with ProcessPoolExecutor(max_workers=P, mp_context=mp.get_context("spawn")) as ex:
-        for s in range(args.warmup + args.steps):
-            t0 = time.perf_counter()
-            res = list(ex.map(_oracle_once, [args.workload] * P, range(P)))
-            dt = time.perf_counter() - t0
-            if s >= args.warmup:
-                times.append(dt)
-                units = sum(res)
+
+    def one_step(run):
+        t0 = time.perf_counter()
+        res = run()
+        return time.perf_counter() - t0, sum(res)
+
+    if P == 1:
+        steps = [one_step(lambda: [_oracle_once(args.workload, 0)]) for _ in range(args.warmup + args.steps)]
+    else:
+        with ProcessPoolExecutor(max_workers=P, mp_context=mp.get_context("spawn")) as ex:
+            steps = [one_step(lambda: list(ex.map(_oracle_once, [args.workload] * P, range(P))))
+                     for _ in range(args.warmup + args.steps)]
+    for dt, u in steps[args.warmup:]:
+        times.append(dt)
+        units = u
     t = sum(times) / len(times)
     v = units / t
     s0 = _sample(args.workload, 0)
@@ -777,6 +784,7 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="mesh side (default 2048 mixture, 1024 taylor_green)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-procs", type=int, default=0, help="oracle processes of the reference arm (0 = all cores)")
     args = ap.parse_args()
     if not args.n:
         args.n = 2048 if args.workload == "mixture" else 1024

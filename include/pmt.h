@@ -99,7 +99,10 @@ typedef struct pm_solve_opts {
     const float *x0; /* device [F][n^dim], read when warm_start == PM_WS_USER     */
     pm_net *net;     /* PM_WS_NET: start from delta + alpha c, c the network's
                         correction and alpha the step that minimises the 2-norm
-                        of the start's residual (alpha = 0 keeps the delta start) */
+                        of the start's residual (alpha = 0 keeps the delta start);
+                        only fields whose delta start is above 1e-4 in relative
+                        residual get the network (the others keep delta), which
+                        makes this start wait for the stream once */
     int rhs_mode;    /* PM_RHS_EXACT (default) or PM_RHS_APPB (pm_assign_mass)   */
     int solver;      /* PM_SOLVER_CG (default) or PM_SOLVER_CHEBYSHEV (mesh solve) */
 } pm_solve_opts;
@@ -337,29 +340,41 @@ pm_status pm_net_features(pm_ctx *ctx, const float *px, const float *py, long lo
 /* ---------------------------------------------------------------------------
  * Batches of independent instances (no counterpart in the paper: many
  * periodic problems of uneven mesh and particle sizes advanced together).
+ *
+ * All instances share one packed workspace and every phase of a step (pack,
+ * sort, stars, right-hand side, direct solve, per-instance solve) is one
+ * launch over all instances (about 18 kernels per step in total), captured
+ * once into a CUDA graph and replayed while the arguments stay the same.
  * ------------------------------------------------------------------------- */
 typedef struct pm_batch pm_batch;
 /* ninst 2D instances; instance k has an n[k] x n[k] mesh of box length L[k]
- * and up to max_np[k] particles (all host arrays). Creates one context per
- * instance (all workspace allocated now) and the batch's own streams; stream
- * is the caller's stream the batch synchronises with. streams = number of
- * concurrent streams for the particle phases, 0 = choose by timing on the
- * first call (1, 2, 4, 8 or 16). */
+ * and up to max_np[k] particles (all host arrays; sum of max_np below 2^28).
+ * Allocates the packed workspace now. stream is the caller's stream the
+ * batch synchronises with. tune: 0 = choose, on the first call, by timing
+ * one step for each setting (threads of the per-instance solve block 256,
+ * 512 or 1024, instances packed as given or largest first), cached per
+ * device and size class for the process; 256, 512 or 1024 = that block size,
+ * instances as given. PM_EINVAL on any other value or an invalid instance. */
 pm_status pm_batch_create(pm_batch **out, int ninst, const int *n, const double *L, const long long *max_np,
-                          int max_fields, int streams, void *stream);
+                          int max_fields, int tune, void *stream);
 void pm_batch_destroy(pm_batch *b);
 const char *pm_batch_last_error(const pm_batch *b);
-/* The chosen stream count and the step time measured when choosing it. */
-pm_status pm_batch_tuning(const pm_batch *b, int *streams, double *step_ms);
-/* Mass assignment (as pm_assign_mass with the PM_WS_DIRECT start: the exact
- * inverse of each instance's mass matrix, then conjugate gradients confirm
- * the residual) of every instance.
+/* The chosen solve block threads (negative when the instances are packed
+ * largest first) and the step time measured when choosing (0 if not tuned). */
+pm_status pm_batch_tuning(const pm_batch *b, int *threads, double *step_ms);
+/* Start of the batch's solves: PM_WS_DIRECT (default: the exact inverse of
+ * each instance's mass matrix), PM_WS_DELTA (the delta assignment) or
+ * PM_WS_ZERO; PM_EINVAL otherwise. */
+pm_status pm_batch_set_start(pm_batch *b, int warm_start);
+/* Mass assignment of every instance (as pm_assign_mass from the batch's
+ * start, PM_WS_DIRECT unless pm_batch_set_start chose another; the residual
+ * is checked and conjugate gradients continue only while it is above rtol).
  * px, py, vals, mesh_out are HOST arrays of ninst DEVICE pointers (instance
  * k: px[k][np[k]], vals[k] [F][np[k]], mesh_out[k] [F][n[k]^2]); np is a host
- * array. One step is captured into a CUDA graph (particle phases of all
- * instances spread over the streams, then the solves in order) and replayed
- * while the pointers, counts and options stay the same. info (host,
- * ninst*F entries, instance-major, may be NULL) makes the call wait. */
+ * array (3 <= np[k] <= max_np[k]). Without info the step is a graph replay
+ * (asynchronous on the caller's stream). info (host, ninst*F entries,
+ * instance-major, may be NULL) makes the call run the step with the
+ * stability integrals and wait; errors of any instance are reported then. */
 pm_status pm_batch_assign_mass(pm_batch *b, const float *const *px, const float *const *py, const long long *np,
                                const float *const *vals, int F, float *const *mesh_out, double rtol, int max_iter,
                                pm_solve_info *info);

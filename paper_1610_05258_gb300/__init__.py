@@ -127,6 +127,7 @@ def load_library(path: str | None = None):
         "pm_batch_last_error": [vp],
         "pm_batch_tuning": [vp, ctypes.POINTER(i), ctypes.POINTER(d)],
         "pm_batch_assign_mass": [vp, vp, vp, vp, vp, i, vp, d, i, vp],
+        "pm_batch_set_start": [vp, i],
         "pm_net_num_params": [],
         "pm_net_create": [ctypes.POINTER(vp), i, i, vp],
         "pm_net_destroy": [vp],
@@ -427,9 +428,12 @@ class Context:
 
 
 class Batch:
-    """Many independent 2D instances advanced together (pm_batch_*)."""
+    """Many independent 2D instances advanced together in one packed
+    workspace, one launch per phase (pm_batch_*). tune: 0 = choose the solve
+    block size and packing order by timing the first step; 256, 512 or 1024 =
+    that solve block size."""
 
-    def __init__(self, sizes, Ls, max_particles, max_fields=1, streams=0, device=None):
+    def __init__(self, sizes, Ls, max_particles, max_fields=1, tune=0, device=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -445,7 +449,7 @@ class Batch:
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             st = torch.cuda.current_stream().cuda_stream
-            s = self.lib.pm_batch_create(ctypes.byref(h), self.k, n, L, mp, max_fields, streams, ctypes.c_void_p(st))
+            s = self.lib.pm_batch_create(ctypes.byref(h), self.k, n, L, mp, max_fields, tune, ctypes.c_void_p(st))
         if s != 0:
             raise PMError(s, "pm_batch_create failed")
         self.h = h
@@ -456,9 +460,17 @@ class Batch:
             self.h = None
 
     def tuning(self):
+        """(solve block threads, packed largest first, step ms measured when tuning)."""
         s, ms = ctypes.c_int(0), ctypes.c_double(0.0)
         self.lib.pm_batch_tuning(self.h, ctypes.byref(s), ctypes.byref(ms))
-        return s.value, ms.value
+        return abs(s.value), s.value < 0, ms.value
+
+    def set_start(self, warm_start="direct"):
+        ws = {"direct": PM_WS_DIRECT, "delta": PM_WS_DELTA, "zero": PM_WS_ZERO, "user": PM_WS_USER,
+              "net": PM_WS_NET}.get(warm_start, -1)  # the library rejects all but the first three
+        s = self.lib.pm_batch_set_start(self.h, ws)
+        if s != 0:
+            raise PMError(s, self.lib.pm_batch_last_error(self.h).decode())
 
     def assign_mass(self, pxs, pys, vals, outs, rtol=1e-6, max_iter=200, info=True):
         K = self.k

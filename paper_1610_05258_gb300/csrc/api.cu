@@ -219,6 +219,7 @@ pm_status pm_ctx_create_mesh(pm_ctx **out, int dim, int n, double L, long long m
     if (ok && dim == 2 && n % 128 == 0 && !g.p1)  // the network start: bilinear meshes
         ok = alloc(c, &w.feat, 2 * F * nc) && alloc(c, &w.corr, F * nc);
     if (ok && cudaMallocHost((void **)&w.hstatus, sizeof(int)) != cudaSuccess) ok = false;
+    if (ok && cudaMallocHost((void **)&w.hres, sizeof(double) * PM_MAXF) != cudaSuccess) ok = false;
     if (!ok) {
         pm_ctx_destroy(c);
         cudaGetLastError();
@@ -247,6 +248,7 @@ void pm_ctx_destroy(pm_ctx *c) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (w.hstatus) cudaFreeHost(w.hstatus);
+    if (w.hres) cudaFreeHost(w.hres);
     for (auto &e : c->ev) {
         cudaEventDestroy(e.a);
         cudaEventDestroy(e.b);
@@ -406,9 +408,32 @@ static pm_status mass_front(pm_ctx *c, const float *px, const float *py, ll np, 
         }
         {
             Phase ph(c, PM_PH_NET);
+            // Gate: the network runs only on the fields whose delta start is
+            // still above PM_NET_GATE in relative residual (the others need a
+            // CG iteration or two, far less than the network costs). The
+            // residuals come back to the host, so this start waits once.
+            double *dres = c->w.red + 4LL * PM_MAXF * 608;  // past the residual kernel's partials
+            launch_start_resid(c->g, c->w, F, dres, c->st);
+            cudaMemcpyAsync(c->w.hres, dres, sizeof(double) * F, cudaMemcpyDeviceToHost, c->st);
+            cudaError_t ce = cudaStreamSynchronize(c->st);
+            if (ce != cudaSuccess) return cuda_fail(c, ce, "network gate");
             pm_net_set_stream(o.net, c->st);
-            pm_status s2 = pm_net_forward(o.net, c->w.feat, F, c->g.n, c->w.corr);
-            if (s2) return fail(c, s2, "network forward failed (n must be a multiple of 128 within the net's size)");
+            int f = 0;
+            while (f < F) {
+                const bool on = c->w.hres[f] > PM_NET_GATE;
+                int e = f + 1;
+                while (e < F && (c->w.hres[e] > PM_NET_GATE) == on) ++e;
+                float *corr = c->w.corr + (ll)f * c->g.ncell;
+                if (on) {
+                    pm_status s2 = pm_net_forward(o.net, c->w.feat + 2LL * f * c->g.ncell, e - f, c->g.n, corr);
+                    if (s2)
+                        return fail(c, s2, "network forward failed (n must be a multiple of 128 within the net's size)");
+                } else {
+                    // no correction: alpha = 0 for these fields
+                    cudaMemsetAsync(corr, 0, sizeof(float) * (e - f) * c->g.ncell, c->st);
+                }
+                f = e;
+            }
             launch_apply_correction(c->g, c->w, F, mesh_out, c->st);
         }
     } else if (o.warm_start == PM_WS_DIRECT) {
@@ -729,224 +754,9 @@ int pm_debug_read(int *out) {
 }
 #endif
 
-// ---------------------------------------------------------------------------
-// Batches of independent instances
-// ---------------------------------------------------------------------------
 }  // extern "C"
 
-struct pm_batch {
-    int ninst = 0, F_max = 0, S = 0;
-    std::vector<pm_ctx *> ctx;
-    std::vector<cudaStream_t> streams;
-    cudaStream_t main = nullptr, user = nullptr;
-    std::vector<cudaEvent_t> join;
-    cudaEvent_t fork = nullptr, done = nullptr, t0 = nullptr, t1 = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    std::vector<const void *> key;
-    double tuned_ms = 0.0;
-    long long graph_kernels = 0;  // kernels recorded in the captured step
-    std::string err;
-};
-
-namespace {
-
-pm_status bfail(pm_batch *b, pm_status s, const std::string &m) {
-    b->err = m;
-    return s;
-}
-
-// Queue one step for every instance: particle phases spread over S streams,
-// then every solve in order on the main stream (two persistent cooperative
-// grids never run at the same time).
-pm_status batch_enqueue(pm_batch *b, int S, const float *const *px, const float *const *py, const ll *np,
-                        const float *const *vals, int F, float *const *mesh, const pm_solve_opts &o,
-                        std::vector<char> &start) {
-    cudaEventRecord(b->fork, b->main);
-    for (int j = 0; j < S; ++j) cudaStreamWaitEvent(b->streams[j], b->fork, 0);
-    for (int k = 0; k < b->ninst; ++k) {
-        pm_ctx *c = b->ctx[k];
-        c->st = b->streams[k % S];
-        bool st = true;
-        pm_status s = mass_front(c, px[k], py[k], np[k], vals[k], F, mesh[k], o, st);
-        if (s) return bfail(b, s, c->err);
-        start[k] = st;
-    }
-    for (int j = 0; j < S; ++j) {
-        cudaEventRecord(b->join[j], b->streams[j]);
-        cudaStreamWaitEvent(b->main, b->join[j], 0);
-    }
-    for (int k = 0; k < b->ninst; ++k) {
-        pm_ctx *c = b->ctx[k];
-        c->st = b->main;
-        pm_status s = mass_solve_launch(c, F, mesh[k], start[k] != 0, o);
-        if (s) return bfail(b, s, c->err);
-    }
-    return PM_OK;
-}
-
-}  // namespace
-
 extern "C" {
-
-pm_status pm_batch_create(pm_batch **out, int ninst, const int *n, const double *L, const long long *max_np,
-                          int max_fields, int streams, void *stream) {
-    if (!out || ninst < 1 || !n || !L || !max_np || streams < 0 || streams > 32) return PM_EINVAL;
-    *out = nullptr;
-    pm_batch *b = new pm_batch();
-    b->ninst = ninst;
-    b->F_max = max_fields;
-    b->S = streams;
-    b->user = (cudaStream_t)stream;
-    const int smax = 32;
-    bool ok = cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) == cudaSuccess;
-    for (int j = 0; ok && j < smax; ++j) {
-        cudaStream_t s;
-        cudaEvent_t e;
-        ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
-             cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
-        if (ok) {
-            b->streams.push_back(s);
-            b->join.push_back(e);
-        }
-    }
-    ok = ok && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
-         cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) == cudaSuccess &&
-         cudaEventCreate(&b->t0) == cudaSuccess && cudaEventCreate(&b->t1) == cudaSuccess;
-    for (int k = 0; ok && k < ninst; ++k) {
-        pm_ctx *c = nullptr;
-        pm_status s = pm_ctx_create(&c, 2, n[k], L[k], max_np[k], max_fields, b->main);
-        if (s) {
-            pm_batch_destroy(b);
-            return s;
-        }
-        b->ctx.push_back(c);
-    }
-    if (!ok) {
-        pm_batch_destroy(b);
-        return PM_ECUDA;
-    }
-    *out = b;
-    return PM_OK;
-}
-
-void pm_batch_destroy(pm_batch *b) {
-    if (!b) return;
-    if (b->exec) cudaGraphExecDestroy(b->exec);
-    if (b->graph) cudaGraphDestroy(b->graph);
-    for (pm_ctx *c : b->ctx) pm_ctx_destroy(c);
-    for (auto s : b->streams) cudaStreamDestroy(s);
-    for (auto e : b->join) cudaEventDestroy(e);
-    if (b->fork) cudaEventDestroy(b->fork);
-    if (b->done) cudaEventDestroy(b->done);
-    if (b->t0) cudaEventDestroy(b->t0);
-    if (b->t1) cudaEventDestroy(b->t1);
-    if (b->main) cudaStreamDestroy(b->main);
-    delete b;
-}
-
-const char *pm_batch_last_error(const pm_batch *b) { return b ? b->err.c_str() : "null batch"; }
-
-pm_status pm_batch_tuning(const pm_batch *b, int *streams, double *step_ms) {
-    if (!b) return PM_EINVAL;
-    if (streams) *streams = b->S;
-    if (step_ms) *step_ms = b->tuned_ms;
-    return PM_OK;
-}
-
-pm_status pm_batch_assign_mass(pm_batch *b, const float *const *px, const float *const *py, const long long *np,
-                               const float *const *vals, int F, float *const *mesh_out, double rtol, int max_iter,
-                               pm_solve_info *info) {
-    if (!b || !px || !py || !np || !vals || !mesh_out || F < 1 || F > b->F_max) return PM_EINVAL;
-    for (int k = 0; k < b->ninst; ++k) {
-        pm_status s = check_particles(b->ctx[k], px[k], py[k], np[k], F, vals[k], 3);
-        if (s) return bfail(b, s, "instance " + std::to_string(k) + ": " + b->ctx[k]->err);
-        if (!mesh_out[k]) return bfail(b, PM_EINVAL, "null output");
-    }
-    // start from the exact inverse of each instance's mass matrix: the
-    // solves, which run one after another, then only confirm the residual
-    pm_solve_opts o;
-    o.warm_start = PM_WS_DIRECT;
-    o.rtol = rtol > 0.0 ? rtol : 1e-6;
-    o.max_iter = max_iter > 0 ? max_iter : 200;
-    o.x0 = nullptr;
-    o.net = nullptr;
-    o.rhs_mode = PM_RHS_EXACT;
-    o.solver = PM_SOLVER_CG;
-    std::vector<char> start(b->ninst, 1);
-    // the main stream follows the caller's stream
-    cudaEventRecord(b->fork, b->user);
-    cudaStreamWaitEvent(b->main, b->fork, 0);
-    // autotune the number of concurrent streams once (timed, not captured)
-    if (b->S == 0) {
-        double best = 1e30;
-        int bestS = 1;
-        for (int S : {1, 2, 4, 8, 16}) {
-            for (int rep = 0; rep < 2; ++rep) {
-                cudaEventRecord(b->t0, b->main);
-                pm_status s = batch_enqueue(b, S, px, py, np, vals, F, mesh_out, o, start);
-                if (s) return s;
-                cudaEventRecord(b->t1, b->main);
-            }
-            if (cudaEventSynchronize(b->t1) != cudaSuccess) return bfail(b, PM_ECUDA, "autotune");
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, b->t0, b->t1);
-            if (ms < best) {
-                best = ms;
-                bestS = S;
-            }
-        }
-        b->S = bestS;
-        b->tuned_ms = best;
-    }
-    // capture one step into a CUDA graph, replay it while the arguments match
-    std::vector<const void *> key;
-    key.push_back((const void *)(ll)F);
-    for (int k = 0; k < b->ninst; ++k) {
-        key.push_back(px[k]);
-        key.push_back(py[k]);
-        key.push_back(vals[k]);
-        key.push_back(mesh_out[k]);
-        key.push_back((const void *)np[k]);
-    }
-    key.push_back((const void *)(ll)(o.max_iter));
-    key.push_back((const void *)(ll)(o.rtol * 1e12));
-    if (!b->exec || key != b->key) {
-        if (b->exec) cudaGraphExecDestroy(b->exec);
-        if (b->graph) cudaGraphDestroy(b->graph);
-        b->exec = nullptr;
-        b->graph = nullptr;
-        cudaError_t ce = cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal);
-        if (ce != cudaSuccess) return bfail(b, PM_ECUDA, std::string("capture: ") + cudaGetErrorString(ce));
-        const long long l0 = g_launch_total.load();
-        pm_status s = batch_enqueue(b, b->S, px, py, np, vals, F, mesh_out, o, start);
-        b->graph_kernels = g_launch_total.load() - l0;
-        g_launch_total -= b->graph_kernels;  // counted when the graph runs
-        ce = cudaStreamEndCapture(b->main, &b->graph);
-        if (s) return s;
-        if (ce != cudaSuccess) return bfail(b, PM_ECUDA, std::string("end capture: ") + cudaGetErrorString(ce));
-        ce = cudaGraphInstantiate(&b->exec, b->graph, 0);
-        if (ce != cudaSuccess) return bfail(b, PM_ECUDA, std::string("instantiate: ") + cudaGetErrorString(ce));
-        b->key = key;
-    }
-    cudaError_t ce = cudaGraphLaunch(b->exec, b->main);
-    if (ce != cudaSuccess) return bfail(b, PM_ECUDA, std::string("graph launch: ") + cudaGetErrorString(ce));
-    count_launches((int)b->graph_kernels);
-    cudaEventRecord(b->done, b->main);
-    cudaStreamWaitEvent(b->user, b->done, 0);
-    if (!info) return PM_OK;
-    pm_status worst = PM_OK;
-    for (int k = 0; k < b->ninst; ++k) {
-        pm_ctx *c = b->ctx[k];
-        c->st = b->main;
-        pm_status s = report(c, F, info + (ll)k * F, mesh_out[k], np[k], c->w.vals, np[k], 1);
-        if (s && !worst) {
-            worst = s;
-            b->err = "instance " + std::to_string(k) + ": " + c->err;
-        }
-    }
-    return worst;
-}
 
 pm_status pm_sort(pm_ctx *c, const float *px, const float *py, long long np, int *perm_out, int *cell_start_out) {
     pm_status s = check_particles(c, px, py, np, 0, nullptr, 0);

@@ -480,6 +480,70 @@ __global__ void __launch_bounds__(NB) k_delaunay_retry(Geo g, ll np, const uint2
     add_counts<COUNT>(wc, wsum, 6);  // the first retry pass's give-ups (none in the last)
 }
 
+// Batched passes: the particle's instance comes from the packed offsets; its
+// mesh, cell ranges and volume scale from the instance table. Stars hold
+// packed sorted indices (< 2^28 in total).
+__global__ void __launch_bounds__(DBLK, 11) k_delaunay_b(BTab t, const uint2 *__restrict__ pos,
+                                                     const int *__restrict__ cell_start, const int *__restrict__ perm,
+                                                     int *__restrict__ nbr, unsigned char *__restrict__ deg,
+                                                     float *__restrict__ vol, int *__restrict__ status,
+                                                     int *__restrict__ retry, int *__restrict__ nretry) {
+    __shared__ int4 sq[DCAP][DBLK];
+    __shared__ float4 sv[DCAP][DBLK];
+    const ll pl = (ll)blockIdx.x * DBLK + threadIdx.x;
+    WorkCount wc;
+    if (pl < t.NP) {
+        const int p = (int)pl;
+        const int k = find_slot(t.poff, t.ninst, pl);
+        const Geo g = batch_geo(t, k);
+        PolyS<DBLK> P{sq, sv, (int)threadIdx.x};
+        const int err = star_of<DCAP, DBLK, false>(P, p, g, t.NP, pos, cell_start + __ldg(t.coff + k), perm, nbr, deg,
+                                                   vol, t.inst[k].vol_scale, wc);
+        if (err == ST_OVERFLOW) {
+            const int j = atomicAdd(nretry, 1);
+            PM_CHK(j >= 0 && j < t.NP, 207, j = -1)
+            if (j >= 0) retry[j] = p;
+        } else if (err) {
+            atomicOr(status, err & ~ST_OVERFLOW);
+            deg[p] = 0;
+            vol[p] = 0.0f;
+        }
+    }
+}
+
+template <int CAP, int NB, bool LAST>
+__global__ void __launch_bounds__(NB) k_delaunay_retry_b(BTab t, const uint2 *__restrict__ pos,
+                                                         const int *__restrict__ cell_start,
+                                                         const int *__restrict__ perm, int *__restrict__ nbr,
+                                                         unsigned char *__restrict__ deg, float *__restrict__ vol,
+                                                         int *__restrict__ status, int *__restrict__ retry,
+                                                         const int *__restrict__ nretry) {
+    __shared__ int4 sq[CAP][NB];
+    __shared__ float4 sv[CAP][NB];
+    const int cnt = *nretry;
+    WorkCount wc;
+    PolyS<NB> P{sq, sv, (int)threadIdx.x};
+    for (ll j = (ll)blockIdx.x * NB + threadIdx.x; j < cnt; j += (ll)gridDim.x * NB) {
+        int p = retry[j];
+        if (LAST) {
+            if (p >= 0) continue;
+            p = ~p;
+        }
+        PM_CHK(p >= 0 && p < t.NP, 208, continue)
+        const int k = find_slot(t.poff, t.ninst, (ll)p);
+        const Geo g = batch_geo(t, k);
+        const int err = star_of<CAP, NB, false>(P, p, g, t.NP, pos, cell_start + __ldg(t.coff + k), perm, nbr, deg,
+                                                vol, t.inst[k].vol_scale, wc);
+        if (!LAST && err == ST_OVERFLOW) {
+            retry[j] = ~p;
+        } else if (err) {
+            atomicOr(status, (err & ~ST_OVERFLOW) | (err == ST_OVERFLOW ? ST_DEGREE : 0));
+            deg[p] = 0;
+            vol[p] = 0.0f;
+        }
+    }
+}
+
 // 1D: v_mu = half the distance between the two neighbours on the circle.
 __global__ void k_vol1d(ll np, const uint2 *__restrict__ pos, float *__restrict__ vol, float scale) {
     ll s = (ll)blockIdx.x * blockDim.x + threadIdx.x;
@@ -539,6 +603,19 @@ void launch_triangulate(const Geo &g, Work &w, ll np, cudaStream_t st, bool coun
         k_delaunay_retry<RCAP, RBLK, true, false><<<rgrid, RBLK, 0, st>>>(
             g, np, w.pos, w.cell_start, w.perm, w.nbr, w.deg, w.vol, scale, w.status, w.tmp, w.nretry, nullptr);
     }
+    count_launches(3);
+}
+
+void launch_triangulate_batched(const BTab &t, Work &w, cudaStream_t st) {
+    if (t.NP <= 0) return;
+    cudaMemsetAsync(w.nretry, 0, sizeof(int), st);
+    const int r1grid = 17 * 152, rgrid = 8 * 152;
+    k_delaunay_b<<<div_up(t.NP, DBLK), DBLK, 0, st>>>(t, w.pos, w.cell_start, w.perm, w.nbr, w.deg, w.vol, w.status,
+                                                       w.tmp, w.nretry);
+    k_delaunay_retry_b<R1CAP, R1BLK, false><<<r1grid, R1BLK, 0, st>>>(t, w.pos, w.cell_start, w.perm, w.nbr, w.deg,
+                                                                       w.vol, w.status, w.tmp, w.nretry);
+    k_delaunay_retry_b<RCAP, RBLK, true><<<rgrid, RBLK, 0, st>>>(t, w.pos, w.cell_start, w.perm, w.nbr, w.deg, w.vol,
+                                                                  w.status, w.tmp, w.nretry);
     count_launches(3);
 }
 

@@ -7,8 +7,13 @@
 // circle): f solves f(j-1) + 4 f(j) + f(j+1) = delta_j0 with periodic ends.
 // |r| < 0.268, so offsets beyond 16 weigh below 2e-10 and are dropped on
 // meshes with n > 33; smaller meshes take every offset. Each pass stages a
-// tile with its halo in shared memory.
+// tile with its halo in shared memory. Every tap is carried as a float pair
+// (hi + lo = the double weight to ~2^-48) and the sum is compensated (Dot2):
+// with single float taps the rounding of the weights perturbs the operator's
+// low-frequency symbol by ~1e-7 in one direction, a bias that a long chain of
+// assignments (a 256-step transport) accumulates step after step.
 #include <math.h>
+#include <string.h>
 
 #include "internal.cuh"
 
@@ -21,20 +26,17 @@ namespace {
 struct Taps {
     int nt;             // number of taps
     int off[DMAXT];     // offsets along the direction (distinct mod n)
-    float w[DMAXT];     // weights f(offset mod n) times the scale
+    float w[DMAXT];     // weights f(offset mod n) times the scale (rounded)
+    float wl[DMAXT];    // the weights' rounding remainders
     int halo;           // largest |offset|
 };
 
-// One pass along x (DIR 0) or y (DIR 1) of every field: dst = taps * src.
+// One pass along x (DIR 0) or y (DIR 1) of one field over the tile at
+// (x0, y0): d = taps * s (s, d the field's n x n arrays).
 template <int DIR>
-__global__ void __launch_bounds__(256) k_circ(int n, int F, const float *__restrict__ src, float *__restrict__ dst,
-                                              Taps t) {
+__device__ __forceinline__ void circ_tile(int n, const float *__restrict__ s, float *__restrict__ d, const Taps &t,
+                                          int x0, int y0) {
     __shared__ float tile[DT + 2 * DK][DT + 1];  // halo <= DK on every mesh
-    const int tiles = (n + DT - 1) / DT;
-    const int f = blockIdx.y;
-    const int x0 = (blockIdx.x % tiles) * DT, y0 = (blockIdx.x / tiles) * DT;
-    const ll nn = (ll)n * n;
-    const float *s = src + (ll)f * nn;
     const int H = t.halo;
     // stage: along the pass direction the tile is DT + 2H long
     for (int i = threadIdx.x; i < (DT + 2 * H) * DT; i += blockDim.x) {
@@ -53,10 +55,39 @@ __global__ void __launch_bounds__(256) k_circ(int n, int F, const float *__restr
         if (DIR == 0) { x = x0 + a; y = y0 + b; }
         else { x = x0 + b; y = y0 + a; }
         if (x >= n || y >= n) continue;
-        float acc = 0.0f;
-        for (int k = 0; k < t.nt; ++k) acc = fmaf(t.w[k], tile[a + H + t.off[k]][b], acc);
-        dst[(ll)f * nn + (ll)y * n + x] = acc;
+        Dot2 acc;
+        float lo = 0.0f;
+        for (int k = 0; k < t.nt; ++k) {
+            const float v = tile[a + H + t.off[k]][b];
+            acc.fma_acc(t.w[k], v);
+            lo = fmaf(t.wl[k], v, lo);
+        }
+        d[(ll)y * n + x] = acc.hi + (acc.lo + lo);
     }
+}
+
+template <int DIR>
+__global__ void __launch_bounds__(256) k_circ(int n, int F, const float *__restrict__ src, float *__restrict__ dst,
+                                              Taps t) {
+    const int tiles = (n + DT - 1) / DT;
+    const ll nn = (ll)n * n;
+    const int f = blockIdx.y;
+    circ_tile<DIR>(n, src + (ll)f * nn, dst + (ll)f * nn, t, (blockIdx.x % tiles) * DT, (blockIdx.x / tiles) * DT);
+}
+
+// Batched: block b is tile b - tile_start[k] of instance k (taps[k] staged in
+// shared memory); fields are [F][NC] packed arrays.
+template <int DIR>
+__global__ void __launch_bounds__(256) k_circ_b(BTab bt, const Taps *__restrict__ taps, const int *__restrict__ tile_start,
+                                                const float *__restrict__ src, float *__restrict__ dst) {
+    __shared__ Taps st;
+    const int k = find_slot(tile_start, bt.ninst, (int)blockIdx.x);
+    for (int i = threadIdx.x; i < (int)(sizeof(Taps) / 4); i += blockDim.x)
+        ((int *)&st)[i] = ((const int *)(taps + k))[i];
+    __syncthreads();
+    const int n = bt.inst[k].n, tiles = (n + DT - 1) / DT, tl = (int)blockIdx.x - __ldg(tile_start + k);
+    const ll off = (ll)blockIdx.y * bt.NC + __ldg(bt.coff + k);
+    circ_tile<DIR>(n, src + off, dst + off, st, (tl % tiles) * DT, (tl / tiles) * DT);
 }
 
 __global__ void __launch_bounds__(256) k_circ1(int n, int F, const float *__restrict__ src, float *__restrict__ dst,
@@ -64,9 +95,14 @@ __global__ void __launch_bounds__(256) k_circ1(int n, int F, const float *__rest
     const ll i = (ll)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (ll)n * F) return;
     const int f = (int)(i / n), x = (int)(i % n);
-    float acc = 0.0f;
-    for (int k = 0; k < t.nt; ++k) acc = fmaf(t.w[k], __ldg(src + (ll)f * n + (((x + t.off[k]) % n) + n) % n), acc);
-    dst[i] = acc;
+    Dot2 acc;
+    float lo = 0.0f;
+    for (int k = 0; k < t.nt; ++k) {
+        const float v = __ldg(src + (ll)f * n + (((x + t.off[k]) % n) + n) % n);
+        acc.fma_acc(t.w[k], v);
+        lo = fmaf(t.wl[k], v, lo);
+    }
+    dst[i] = acc.hi + (acc.lo + lo);
 }
 
 Taps make_taps(int n, double scale) {
@@ -76,16 +112,20 @@ Taps make_taps(int n, double scale) {
     t.nt = 0;
     if (n > 2 * DK + 1) {
         for (int j = -DK; j <= DK; ++j) {
+            const double wd = scale * f(j < 0 ? -j : j);
             t.off[t.nt] = j;
-            t.w[t.nt] = (float)(scale * f(j < 0 ? -j : j));
+            t.w[t.nt] = (float)wd;
+            t.wl[t.nt] = (float)(wd - (double)t.w[t.nt]);
             ++t.nt;
         }
         t.halo = DK;
     } else {
         // every residue once, offsets in (-n/2, n/2]
         for (int j = -((n - 1) / 2); j <= n / 2; ++j) {
+            const double wd = scale * f(((j % n) + n) % n);
             t.off[t.nt] = j;
-            t.w[t.nt] = (float)(scale * f(((j % n) + n) % n));
+            t.w[t.nt] = (float)wd;
+            t.wl[t.nt] = (float)(wd - (double)t.w[t.nt]);
             ++t.nt;
         }
         t.halo = n / 2;
@@ -94,6 +134,24 @@ Taps make_taps(int n, double scale) {
 }
 
 }  // namespace
+
+size_t direct_taps_bytes() { return sizeof(Taps); }
+void make_direct_taps(int n, double L, void *out) {
+    const Taps t = make_taps(n, 6.0 / (L / n));
+    memcpy(out, &t, sizeof(Taps));
+}
+int direct_tile_count(int n) {
+    const int tiles = (n + DT - 1) / DT;
+    return tiles * tiles;
+}
+
+void launch_mass_direct_batched(const BTab &t, const void *taps, const int *tile_start, int ntiles, const float *b,
+                                int F, float *x, float *tmp, cudaStream_t st) {
+    dim3 grid(ntiles, F);
+    k_circ_b<0><<<grid, 256, 0, st>>>(t, (const Taps *)taps, tile_start, b, tmp);
+    k_circ_b<1><<<grid, 256, 0, st>>>(t, (const Taps *)taps, tile_start, tmp, x);
+    count_launches(2);
+}
 
 // x = M^-1 b for F fields (b, x device [F][n^dim]; tmp [F][n^dim] scratch).
 void launch_mass_direct(const Geo &g, const float *b, int F, float *x, float *tmp, cudaStream_t st) {

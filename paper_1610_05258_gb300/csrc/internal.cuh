@@ -10,6 +10,7 @@
 #define PM_MAXF 8      // fields per call
 #define PM_RCAP 12     // rings of cells searched by the triangulation
 #define PM_NET_RSCALE 64.0f  // scale of the residual input and of the output of the warm-start network
+#define PM_NET_GATE 1e-4     // delta-start relative residual above which a field gets the network's correction
 
 typedef long long ll;
 typedef unsigned long long ull;
@@ -35,7 +36,64 @@ struct Geo {
     float h;       // fl32(L/n)
     ll ncell;      // n^dim
     int p1;        // 2D mesh functions: 0 bilinear, 1 P1 on cells split by the (0,0)-(1,1) diagonal
+    ll fstride;    // field stride of the [F][...] node arrays a kernel writes (ncell for one mesh; the
+                   // packed total for the instances of a batch); 0 reads as ncell
 };
+
+__host__ __device__ __forceinline__ ll field_stride(const Geo &g) { return g.fstride ? g.fstride : g.ncell; }
+
+// ---------------------------------------------------------------------------
+// Batches of independent 2D instances packed into one workspace: instance k
+// owns the particle slots [poff[k], poff[k+1]) and the cells/nodes
+// [coff[k], coff[k+1]) of the packed arrays; node arrays are [F][NC] and
+// particle arrays [F][NP] over all instances.
+// ---------------------------------------------------------------------------
+struct BInst {
+    int n;            // nodes per side
+    float invL, h;    // fl32(1/L), fl32(L/n)
+    double L;
+    float vol_scale;  // (L / 2^32)^2 / 6: particle volume per unit of twice the star area
+};
+struct BTab {
+    const BInst *inst;  // [ninst] (device)
+    const ll *poff;     // [ninst + 1] packed particle offsets (device)
+    const ll *coff;     // [ninst + 1] packed cell offsets (device)
+    int ninst;
+    ll NP, NC;
+};
+
+// Largest k in [0, m) with off[k] <= x (off ascending, off[0] = 0).
+__device__ __forceinline__ int find_slot(const ll *__restrict__ off, int m, ll x) {
+    int lo = 0, hi = m - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ int find_slot(const int *__restrict__ off, int m, int x) {
+    int lo = 0, hi = m - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The mesh of instance k as a Geo whose node arrays use the packed stride NC.
+__device__ __forceinline__ Geo batch_geo(const BTab &t, int k) {
+    const BInst I = t.inst[k];
+    Geo g;
+    g.dim = 2;
+    g.n = I.n;
+    g.L = I.L;
+    g.invL = I.invL;
+    g.h = I.h;
+    g.ncell = (ll)I.n * I.n;
+    g.p1 = 0;
+    g.fstride = t.NC;
+    return g;
+}
 
 // Exponent E of the 64-bit fixed point in which the right-hand side of a
 // field with max|A| = amax is accumulated: |b_j| <= amax h^dim < 2^(60 - E).
@@ -113,6 +171,7 @@ struct Work {
     // learned warm start (2D, n a multiple of 128)
     float *feat;           // [F][2][ncell] network input
     float *corr;           // [F][ncell] network output
+    double *hres;          // [PM_MAXF] pinned host: delta-start residual per field (network gating)
     ull *wsum;             // [8] triangulation work counters (counting mode)
     int *nretry;           // particles handed to the triangulation's retry pass
     // mesh -> particle projections (particle-sized, sorted order)
@@ -221,6 +280,13 @@ __device__ __forceinline__ void stencil(const float *__restrict__ xf, int n, ll 
     lo = acc.lo;
 }
 
+// Power of two 2^-ilogb(m) that scales a field of mean absolute value m to
+// order one (1 for m = 0).
+__device__ __forceinline__ float solve_scale(double m) {
+    if (!(m > 0.0)) return 1.0f;
+    return ldexpf(1.0f, min(120, max(-120, -ilogb(m))));
+}
+
 static inline int div_up(ll a, int b) { return (int)((a + b - 1) / b); }
 
 // Checked build (-DPM_CHECKED, a debugging aid): every data-derived index is
@@ -288,6 +354,9 @@ void launch_scatter_sorted(ll np, const int *perm, const float *src, float *dst,
 void launch_export_tris(const Geo &g, Work &w, ll np, int *tri, int *off, ll max_tri, cudaStream_t st);
 void launch_psum(const Geo &g, Work &w, ll np, int F, cudaStream_t st);
 void launch_features(const Geo &g, Work &w, int F, const float *delta, cudaStream_t st);
+// ||b - M delta|| / ||b|| of the delta start per field (from the network's
+// input features) into out[F] (device).
+void launch_start_resid(const Geo &g, Work &w, int F, double *out, cudaStream_t st);
 void launch_apply_correction(const Geo &g, Work &w, int F, float *mesh, cudaStream_t st);
 // Stability diagnostics (Eq. stab): int Ab^2 = Ab^T M Ab of mesh [F][n^dim]
 // and int A^2 = A^T M_p A of the sorted particle values (value of field f at
@@ -296,6 +365,24 @@ void launch_apply_correction(const Geo &g, Work &w, int F, float *mesh, cudaStre
 int energy_blocks();
 void launch_energies(const Geo &g, Work &w, int F, const float *mesh, ll np, const float *pvals, ll fs, ll ss,
                      cudaStream_t st);
+// Batched phases (one launch each over all instances of a BTab; the Work
+// holds the packed arrays, sized for NP particles and NC cells).
+void launch_sort_batched(const BTab &t, Work &w, const float *px, const float *py, const float *vals, int F,
+                         cudaStream_t st);
+void launch_triangulate_batched(const BTab &t, Work &w, cudaStream_t st);
+// tile_start [ninst + 1]: prefix of the instances' right-hand-side tiles.
+int rhs_tile_side();
+void launch_delta_batched(const BTab &t, Work &w, int F, float *mesh_out, cudaStream_t st);
+void launch_rhs_batched(const BTab &t, Work &w, int F, const int *tile_start, int ntiles, cudaStream_t st);
+void launch_rhs_to_float_batched(const BTab &t, Work &w, int F, float *b_out, cudaStream_t st);
+// Direct solve per instance: taps [ninst] (device, opaque records of
+// direct_taps_bytes() each, written by make_direct_taps), tile_start
+// [ninst + 1] prefix of direct_tile_count(n_k).
+size_t direct_taps_bytes();
+void make_direct_taps(int n, double L, void *out);
+int direct_tile_count(int n);
+void launch_mass_direct_batched(const BTab &t, const void *taps, const int *tile_start, int ntiles, const float *b,
+                                int F, float *x, float *tmp, cudaStream_t st);
 void launch_advect_shift(const Geo &g, float *px, float *py, ll np, double dx, double dy, cudaStream_t st);
 void launch_advect_rotate(const Geo &g, float *px, float *py, ll np, double cx, double cy, double c, double s,
                           cudaStream_t st);

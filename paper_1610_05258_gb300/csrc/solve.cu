@@ -134,13 +134,6 @@ __device__ void particle_sums(const double *psum, int nblk, int F, double s1[PM_
     }
 }
 
-// Power of two 2^-ilogb(m) that scales a field of mean absolute value m to
-// order one (1 for m = 0).
-__device__ __forceinline__ float solve_scale(double m) {
-    if (!(m > 0.0)) return 1.0f;
-    return ldexpf(1.0f, min(120, max(-120, -ilogb(m))));
-}
-
 template <int DIM, int P1>
 __global__ void __launch_bounds__(256) k_cg(CG a) {
     const Geo g = a.g;

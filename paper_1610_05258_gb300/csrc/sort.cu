@@ -182,7 +182,97 @@ __global__ void __launch_bounds__(GATHER_BLK) k_gather(ll np, const int *__restr
     }
 }
 
+// ---------------------------------------------------------------------------
+// Batched: every instance's particles in one packed array (instance k at
+// [poff[k], poff[k+1])), cells numbered globally (instance k's cell c at
+// coff[k] + c). Cell ranges of consecutive instances follow each other, so one
+// scan over all cells gives every instance's cell_start, and the sorted slots
+// of instance k are again [poff[k], poff[k+1]).
+// ---------------------------------------------------------------------------
+__global__ void k_key_b(BTab t, const float *__restrict__ px, const float *__restrict__ py, uint2 *__restrict__ fx,
+                        int *__restrict__ key, int *__restrict__ slot, int *__restrict__ count,
+                        int *__restrict__ status) {
+    const ll j = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= t.NP) return;
+    const int k = find_slot(t.poff, t.ninst, j);
+    const BInst I = t.inst[k];
+    float x = px[j], y = py[j];
+    if (!isfinite(x) || !isfinite(y)) {
+        atomicOr(status, ST_NONFINITE);
+        x = 0.0f;
+        y = 0.0f;
+    }
+    const uint32_t X = torus_coord(x, I.invL), Y = torus_coord(y, I.invL);
+    const ll c = __ldg(t.coff + k) + (ll)cell_of(Y, I.n) * I.n + cell_of(X, I.n);
+    PM_CHK(c >= 0 && c < t.NC, 106, return)
+    fx[j] = make_uint2(X, Y);
+    key[j] = (int)c;
+    slot[j] = atomicAdd(&count[c], 1);
+}
+
+// As k_gather, with max|A| per instance and field (maxabs [ninst][PM_MAXF]):
+// a warp whose slots all belong to one instance reduces before its atomic.
+__global__ void __launch_bounds__(GATHER_BLK) k_gather_b(BTab t, const int *__restrict__ tmp,
+                                                         const uint2 *__restrict__ fx, const float *__restrict__ vals,
+                                                         int F, int *__restrict__ perm, uint2 *__restrict__ pos,
+                                                         float *__restrict__ vals_s, unsigned *__restrict__ maxabs,
+                                                         int *__restrict__ status) {
+    const ll np = t.NP;
+    ll s = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = s < np;
+    const int k = find_slot(t.poff, t.ninst, live ? s : np - 1);
+    float mx[PM_MAXF];
+    for (int f = 0; f < PM_MAXF; ++f) mx[f] = 0.0f;
+    bool bad = false;
+    if (live) {
+        const int idx = tmp[s];
+        PM_CHK(idx >= 0 && idx < np, 107, s = np)
+        if (s < np) {
+            perm[s] = idx;
+            pos[s] = __ldg(fx + idx);
+            for (int f = 0; f < F; ++f) {
+                const float a = __ldg(vals + (ll)f * np + idx);
+                if (!isfinite(a)) bad = true;
+                vals_s[(ll)f * np + s] = a;
+                mx[f] = fabsf(a);
+            }
+        }
+    }
+    if (bad) atomicOr(status, ST_NONFINITE);
+    const int k0 = __shfl_sync(0xffffffffu, k, 0);
+    const bool uniform = __all_sync(0xffffffffu, k == k0);
+    for (int f = 0; f < F; ++f) {
+        float m = mx[f];
+        if (uniform) {
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(&maxabs[k0 * PM_MAXF + f], __float_as_uint(m));
+        } else if (m > 0.0f) {
+            atomicMax(&maxabs[k * PM_MAXF + f], __float_as_uint(m));
+        }
+    }
+}
+
 }  // namespace
+
+void launch_sort_batched(const BTab &t, Work &w, const float *px, const float *py, const float *vals, int F,
+                         cudaStream_t st) {
+    const ll NC = t.NC, NP = t.NP;
+    cudaMemsetAsync(w.count, 0, sizeof(int) * NC, st);
+    cudaMemsetAsync(w.maxabs, 0, sizeof(unsigned) * PM_MAXF * t.ninst, st);
+    k_key_b<<<div_up(NP, 256), 256, 0, st>>>(t, px, py, w.fx, w.key, w.slot, w.count, w.status);
+    const int nb = div_up(NC, 4096);
+    k_scan_local<<<nb, 1024, 0, st>>>(w.count, NC, w.cell_start, w.scan_tmp);
+    k_scan_top<<<1, 1024, 0, st>>>(w.scan_tmp, nb, w.cell_start + NC);
+    k_scan_add<<<div_up(NC, 256), 256, 0, st>>>(w.cell_start, NC, w.scan_tmp);
+    k_place<<<div_up(NP, 256), 256, 0, st>>>(NP, w.key, w.slot, w.cell_start, w.tmp);
+    Geo all{};
+    all.dim = 2;
+    all.ncell = NC;  // 2D canonical order inside a cell is by packed index: no geometry needed
+    k_canon<<<div_up(NC, 128), 128, 0, st>>>(all, NP, w.cell_start, w.tmp, w.fx);
+    k_gather_b<<<div_up(NP, GATHER_BLK), GATHER_BLK, 0, st>>>(t, w.tmp, w.fx, vals, F, w.perm, w.pos, w.vals,
+                                                                w.maxabs, w.status);
+    count_launches(8);
+}
 
 void launch_sort(const Geo &g, Work &w, const float *px, const float *py, ll np, const float *vals, int F,
                  cudaStream_t st) {

@@ -94,19 +94,18 @@ __device__ __forceinline__ void delta_tri(const Geo &g, ll np, int p, int ida, i
             float lp = 1.0f - la - lb;
             const ll node = (ll)wrapi((int)(j % n), n) * n + wrapi((int)(i % n), n);
             PM_CHK(node >= 0 && node < g.ncell && ida < np && idb < np, 302, continue)
+            const ll fs = field_stride(g);
             for (int f = 0; f < F; ++f) {
                 const float *v = vals + (ll)f * np;
-                mesh[(ll)f * g.ncell + node] = lp * v[p] + la * v[ida] + lb * v[idb];
+                mesh[(ll)f * fs + node] = lp * v[p] + la * v[ida] + lb * v[idb];
             }
         }
 }
 
-__global__ void __launch_bounds__(128, 8) k_delta2d(Geo g, ll np, const uint2 *__restrict__ pos,
-                                                 const int *__restrict__ nbr, const unsigned char *__restrict__ deg,
-                                                 const float *__restrict__ vals, int F, float *__restrict__ mesh) {
-    ll pl = (ll)blockIdx.x * blockDim.x + threadIdx.x;
-    if (pl >= np) return;
-    const int p = (int)pl, m = deg[p];
+__device__ __forceinline__ void delta_particle(const Geo &g, ll np, int p, const uint2 *__restrict__ pos,
+                                               const int *__restrict__ nbr, const unsigned char *__restrict__ deg,
+                                               const float *__restrict__ vals, int F, float *__restrict__ mesh) {
+    const int m = deg[p];
     if (m < 3) return;
     const uint2 Xp = pos[p];
     int ida;
@@ -122,6 +121,23 @@ __global__ void __launch_bounds__(128, 8) k_delta2d(Geo g, ll np, const uint2 *_
         ax = bx;
         ay = by;
     }
+}
+
+__global__ void __launch_bounds__(128, 8) k_delta2d(Geo g, ll np, const uint2 *__restrict__ pos,
+                                                 const int *__restrict__ nbr, const unsigned char *__restrict__ deg,
+                                                 const float *__restrict__ vals, int F, float *__restrict__ mesh) {
+    const ll pl = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pl < np) delta_particle(g, np, (int)pl, pos, nbr, deg, vals, F, mesh);
+}
+
+// Batched: the particle's instance writes its nodes of the packed [F][NC] mesh.
+__global__ void __launch_bounds__(128, 8) k_delta2d_b(BTab t, const uint2 *__restrict__ pos,
+                                                   const int *__restrict__ nbr, const unsigned char *__restrict__ deg,
+                                                   const float *__restrict__ vals, int F, float *__restrict__ mesh) {
+    const ll pl = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pl >= t.NP) return;
+    const int k = find_slot(t.poff, t.ninst, pl);
+    delta_particle(batch_geo(t, k), t.NP, (int)pl, pos, nbr, deg, vals, F, mesh + __ldg(t.coff + k));
 }
 
 // 1D: node i lies between the last particle at or left of it and the next one.
@@ -471,11 +487,12 @@ __device__ __forceinline__ void add64_split(unsigned *lo, unsigned *hi, ull v) {
 // maxabs then holds max|Ab| per field, and the fixed-point scale keeps 10
 // bits of headroom for particle volumes up to 1024 h^2.
 template <int FF, int MODE, int P1>
-__global__ void __launch_bounds__(256, 4) k_rhs2d(Geo g, ll np, const uint2 *__restrict__ pos,
-                                               const int *__restrict__ cell_start, const int *__restrict__ nbr,
-                                               const unsigned char *__restrict__ deg, const float *__restrict__ vals,
-                                               int F, const unsigned *__restrict__ maxabs, ll *__restrict__ bfix,
-                                               int tiles_x, const float *__restrict__ mesh, ll *__restrict__ cfix) {
+__device__ __forceinline__ void rhs2d_tile(const Geo &g, ll np, const uint2 *__restrict__ pos,
+                                           const int *__restrict__ cell_start, const int *__restrict__ nbr,
+                                           const unsigned char *__restrict__ deg, const float *__restrict__ vals,
+                                           int F, const unsigned *__restrict__ maxabs, ll *__restrict__ bfix,
+                                           int tiles_x, const float *__restrict__ mesh, ll *__restrict__ cfix,
+                                           int tile) {
     // dynamic shared memory: acc_lo, acc_hi [FF][RWIN^2], tab [RTAB][256]
     extern __shared__ unsigned rhs_smem[];
     unsigned(*acc_lo)[RWIN * RWIN] = (unsigned(*)[RWIN * RWIN])rhs_smem;
@@ -485,7 +502,8 @@ __global__ void __launch_bounds__(256, 4) k_rhs2d(Geo g, ll np, const uint2 *__r
     __shared__ int rowbeg[RTS];
     __shared__ int next_chunk;  // next 32-particle chunk of the tile (warps take chunks as they finish)
     const int n = g.n;
-    const int tx0 = (blockIdx.x % tiles_x) * RTS, ty0 = (blockIdx.x / tiles_x) * RTS;
+    const int tx0 = (tile % tiles_x) * RTS, ty0 = (tile / tiles_x) * RTS;
+    const ll fs = field_stride(g);
     const int wx0 = tx0 - RHALO, wy0 = ty0 - RHALO;
     for (int i = threadIdx.x; i < FF * RWIN * RWIN; i += blockDim.x) {
         (&acc_lo[0][0])[i] = 0u;
@@ -621,7 +639,7 @@ __global__ void __launch_bounds__(256, 4) k_rhs2d(Geo g, ll np, const uint2 *__r
 #pragma unroll
                     for (int f = 0; f < FF; ++f) {
                         if (f >= F) break;
-                        const float ab_c = __ldg(mesh + (ll)f * g.ncell + node);
+                        const float ab_c = __ldg(mesh + (ll)f * fs + node);
                         W0[f] = fmaf(ab_c, K0[c], W0[f]);
                         W1[f] = fmaf(ab_c, K1[c], W1[f]);
                         W2[f] = fmaf(ab_c, K2[c], W2[f]);
@@ -672,7 +690,7 @@ __global__ void __launch_bounds__(256, 4) k_rhs2d(Geo g, ll np, const uint2 *__r
                     if (inwin)
                         add64_split(&acc_lo[f][ly * RWIN + lx], &acc_hi[f][ly * RWIN + lx], (ull)iv);
                     else
-                        atomicAdd((ull *)&bfix[(ll)f * g.ncell + node], (ull)iv);
+                        atomicAdd((ull *)&bfix[(ll)f * fs + node], (ull)iv);
                 }
             }
         }
@@ -685,9 +703,34 @@ __global__ void __launch_bounds__(256, 4) k_rhs2d(Geo g, ll np, const uint2 *__r
         const ll node = (ll)wrapi(wy0 + ly, n) * n + wrapi(wx0 + lx, n);
         for (int f = 0; f < F && f < FF; ++f) {
             const ull v = ((ull)acc_hi[f][i] << 32) | (ull)acc_lo[f][i];
-            if (v) atomicAdd((ull *)&bfix[(ll)f * g.ncell + node], v);
+            if (v) atomicAdd((ull *)&bfix[(ll)f * fs + node], v);
         }
     }
+}
+
+template <int FF, int MODE, int P1>
+__global__ void __launch_bounds__(256, 4) k_rhs2d(Geo g, ll np, const uint2 *__restrict__ pos,
+                                               const int *__restrict__ cell_start, const int *__restrict__ nbr,
+                                               const unsigned char *__restrict__ deg, const float *__restrict__ vals,
+                                               int F, const unsigned *__restrict__ maxabs, ll *__restrict__ bfix,
+                                               int tiles_x, const float *__restrict__ mesh, ll *__restrict__ cfix) {
+    rhs2d_tile<FF, MODE, P1>(g, np, pos, cell_start, nbr, deg, vals, F, maxabs, bfix, tiles_x, mesh, cfix,
+                             (int)blockIdx.x);
+}
+
+// Batched: block b is tile b - tile_start[k] of instance k; the instance's
+// cell ranges, max|A| and fixed-point sums are views of the packed arrays.
+template <int FF>
+__global__ void __launch_bounds__(256, 4) k_rhs2d_b(BTab t, const int *__restrict__ tile_start,
+                                                 const uint2 *__restrict__ pos, const int *__restrict__ cell_start,
+                                                 const int *__restrict__ nbr, const unsigned char *__restrict__ deg,
+                                                 const float *__restrict__ vals, int F,
+                                                 const unsigned *__restrict__ maxabs, ll *__restrict__ bfix) {
+    const int k = find_slot(tile_start, t.ninst, (int)blockIdx.x);
+    const Geo g = batch_geo(t, k);
+    const ll co = __ldg(t.coff + k);
+    rhs2d_tile<FF, 0, 0>(g, t.NP, pos, cell_start + co, nbr, deg, vals, F, maxabs + (ll)k * PM_MAXF, bfix + co,
+                         (g.n + RTS - 1) / RTS, nullptr, nullptr, (int)blockIdx.x - __ldg(tile_start + k));
 }
 
 // 1D: interval between sorted particle s and the next one on the circle.
@@ -763,6 +806,17 @@ __global__ void k_appb_box(Geo g, int F, const float *__restrict__ A2, const uns
         }
         bfix[(ll)f * g.ncell + i] = __float2ll_rn(ldexpf(sum * w, fix_exp(maxabs, f, hd)));
     }
+}
+
+// Batched: node j of the packed [F][NC] arrays belongs to instance k.
+__global__ void k_fix_to_float_b(BTab t, int F, const ll *__restrict__ bfix, const unsigned *__restrict__ maxabs,
+                                 float *__restrict__ out) {
+    const ll i = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= t.NC * F) return;
+    const int f = (int)(i / t.NC);
+    const int k = find_slot(t.coff, t.ninst, i - (ll)f * t.NC);
+    const float h = t.inst[k].h;
+    out[i] = ldexpf((float)bfix[i], -fix_exp(maxabs + (ll)k * PM_MAXF, f, h * h));
 }
 
 __global__ void k_fix_to_float(Geo g, int F, const ll *__restrict__ bfix, const unsigned *__restrict__ maxabs,
@@ -854,6 +908,53 @@ __global__ void k_features(Geo g, int F, const float *__restrict__ delta, const 
         feat[((ll)f * 2 + 0) * g.ncell + i] = d[i] * inv;
         feat[((ll)f * 2 + 1) * g.ncell + i] = PM_NET_RSCALE * res * inv / hd;
     }
+}
+
+// Relative residual of the delta start per field, ||b - M delta|| / ||b||,
+// from the network's input channels: channel 1 is PM_NET_RSCALE r / (h^2
+// max|A|); b is read from its fixed point. FP64 block partials [2F][nblk]
+// (sum r^2, sum b^2, both in units of (h^2 max|A|)^2), reduced by
+// k_start_resid_final into out[f].
+__global__ void __launch_bounds__(256) k_start_resid(Geo g, int F, const float *__restrict__ feat,
+                                                      const ll *__restrict__ bfix, const unsigned *__restrict__ maxabs,
+                                                      double *__restrict__ part) {
+    __shared__ double sh[2 * PM_MAXF][8];
+    const float hd = g.h * g.h;
+    double acc[2 * PM_MAXF];
+    for (int k = 0; k < 2 * F; ++k) acc[k] = 0.0;
+    for (ll i = (ll)blockIdx.x * blockDim.x + threadIdx.x; i < g.ncell; i += (ll)gridDim.x * blockDim.x) {
+        for (int f = 0; f < F; ++f) {
+            const float s = __uint_as_float(maxabs[f]);
+            const float inv = s > 0.0f ? 1.0f / (s * hd) : 0.0f;
+            const double r = (double)feat[((ll)f * 2 + 1) * g.ncell + i] * (1.0 / PM_NET_RSCALE);
+            const double b = (double)(ldexpf((float)bfix[(ll)f * g.ncell + i], -fix_exp(maxabs, f, hd)) * inv);
+            acc[2 * f] += r * r;
+            acc[2 * f + 1] += b * b;
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = 0; k < 2 * F; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[k][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * F) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += sh[threadIdx.x][w];
+        part[(ll)threadIdx.x * gridDim.x + blockIdx.x] = v;
+    }
+}
+
+__global__ void k_start_resid_final(int F, int nblk, const double *__restrict__ part, double *__restrict__ out) {
+    const int f = threadIdx.x;
+    if (f >= F) return;
+    double rr = 0.0, bb = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+        rr += part[(ll)(2 * f) * nblk + b];
+        bb += part[(ll)(2 * f + 1) * nblk + b];
+    }
+    out[f] = bb > 0.0 ? sqrt(rr / bb) : 0.0;
 }
 
 // Step length of the network's correction. With r0 = b - M delta (feature
@@ -998,6 +1099,13 @@ void launch_features(const Geo &g, Work &w, int F, const float *delta, cudaStrea
     count_launches(1);
 }
 
+void launch_start_resid(const Geo &g, Work &w, int F, double *out, cudaStream_t st) {
+    double *part = w.red;  // the solver's reduction buffer (the solve has not started yet)
+    k_start_resid<<<ALPHA_BLOCKS, 256, 0, st>>>(g, F, w.feat, w.bfix, w.maxabs, part);
+    k_start_resid_final<<<1, 32, 0, st>>>(F, ALPHA_BLOCKS, part, out);
+    count_launches(2);
+}
+
 void launch_apply_correction(const Geo &g, Work &w, int F, float *mesh, cudaStream_t st) {
     // scratch: the solver's reduction buffer (the solve has not started yet)
     double *part = w.red, *alpha = w.red + 2LL * PM_MAXF * ALPHA_BLOCKS;
@@ -1057,6 +1165,7 @@ static size_t rhs2d_smem() {
 // device (called when a context is created, outside any stream capture).
 template <int FF>
 static void rhs_attr() {
+    cudaFuncSetAttribute(k_rhs2d_b<FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs2d_smem<FF>());
     cudaFuncSetAttribute(k_rhs2d<FF, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs2d_smem<FF>());
     cudaFuncSetAttribute(k_rhs2d<FF, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs2d_smem<FF>());
     cudaFuncSetAttribute(k_rhs2d<FF, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs2d_smem<FF>());
@@ -1105,6 +1214,34 @@ void launch_rhs(const Geo &g, Work &w, ll np, int F, cudaStream_t st) {
             launch_rhs2d<PM_MAXF>(g, w, np, F, nt, tx, st);
     } else
         k_rhs1d<<<div_up(np, 128), 128, 0, st>>>(g, np, w.pos, w.vals, F, w.maxabs, w.bfix);
+    count_launches(1);
+}
+
+int rhs_tile_side() { return RTS; }
+
+void launch_delta_batched(const BTab &t, Work &w, int F, float *mesh_out, cudaStream_t st) {
+    if (t.NP <= 0) return;
+    k_delta2d_b<<<div_up(t.NP, 128), 128, 0, st>>>(t, w.pos, w.nbr, w.deg, w.vals, F, mesh_out);
+    count_launches(1);
+}
+
+void launch_rhs_batched(const BTab &t, Work &w, int F, const int *tile_start, int ntiles, cudaStream_t st) {
+    cudaMemsetAsync(w.bfix, 0, sizeof(ll) * t.NC * F, st);
+    if (t.NP <= 0 || ntiles <= 0) return;
+    if (F <= 2)
+        k_rhs2d_b<2><<<ntiles, 256, rhs2d_smem<2>(), st>>>(t, tile_start, w.pos, w.cell_start, w.nbr, w.deg, w.vals,
+                                                            F, w.maxabs, w.bfix);
+    else if (F <= 4)
+        k_rhs2d_b<4><<<ntiles, 256, rhs2d_smem<4>(), st>>>(t, tile_start, w.pos, w.cell_start, w.nbr, w.deg, w.vals,
+                                                            F, w.maxabs, w.bfix);
+    else
+        k_rhs2d_b<PM_MAXF><<<ntiles, 256, rhs2d_smem<PM_MAXF>(), st>>>(t, tile_start, w.pos, w.cell_start, w.nbr,
+                                                                        w.deg, w.vals, F, w.maxabs, w.bfix);
+    count_launches(1);
+}
+
+void launch_rhs_to_float_batched(const BTab &t, Work &w, int F, float *b_out, cudaStream_t st) {
+    k_fix_to_float_b<<<div_up(t.NC * F, 256), 256, 0, st>>>(t, F, w.bfix, w.maxabs, b_out);
     count_launches(1);
 }
 

@@ -65,6 +65,7 @@ def test_reference_arm_rank_handling(monkeypatch):
 
     class A:
         world, rank, gpus, steps, warmup = 2, 1, 2, 1, 0
+        workload, ref_procs = "mixture", 1
 
     buf = io.StringIO()
     with redirect_stdout(buf):
@@ -72,7 +73,8 @@ def test_reference_arm_rank_handling(monkeypatch):
     assert buf.getvalue() == ""
 
     calls = []
-    monkeypatch.setattr(bench, "oracle_sample", lambda: calls.append(1) or _tiny())
+    monkeypatch.setattr(bench, "_sample", lambda w, seed: calls.append(1) or {"inst": _tiny(), "what": "tiny"})
+    monkeypatch.setattr(bench, "_CACHE", {})
 
     class B(A):
         rank = 0

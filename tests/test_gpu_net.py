@@ -158,3 +158,6 @@ def test_trained_network_gains_over_delta_start(built):
         assert learned[f].iters < plain[f].iters
     for f in range(F):
         assert learned[f].rel_resid <= 1e-6 and learned[f].cons_err <= 1e-6
+        if plain[f].init_rel_resid < 1e-4:
+            # gated: a field whose delta start is already this close keeps it
+            assert learned[f].init_rel_resid == plain[f].init_rel_resid, (f, learned[f], plain[f])
