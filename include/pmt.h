@@ -342,8 +342,9 @@ pm_status pm_net_features(pm_ctx *ctx, const float *px, const float *py, long lo
  * periodic problems of uneven mesh and particle sizes advanced together).
  *
  * All instances share one packed workspace and every phase of a step (pack,
- * sort, stars, right-hand side, direct solve, per-instance solve) is one
- * launch over all instances (about 18 kernels per step in total), captured
+ * sort, stars, right-hand side, start, per-instance solve on a thread-block
+ * cluster) is one launch over all instances (about 18 kernels per step in
+ * total), captured
  * once into a CUDA graph and replayed while the arguments stay the same.
  * ------------------------------------------------------------------------- */
 typedef struct pm_batch pm_batch;
@@ -351,17 +352,23 @@ typedef struct pm_batch pm_batch;
  * and up to max_np[k] particles (all host arrays; sum of max_np below 2^28).
  * Allocates the packed workspace now. stream is the caller's stream the
  * batch synchronises with. tune: 0 = choose, on the first call, by timing
- * one step for each setting (threads of the per-instance solve block 256,
- * 512 or 1024, instances packed as given or largest first), cached per
- * device and size class for the process; 256, 512 or 1024 = that block size,
- * instances as given. PM_EINVAL on any other value or an invalid instance. */
+ * one step for each setting (the solve's threads per CTA and CTAs per
+ * instance, instances packed as given or largest first), cached per device
+ * and size class for the process; 256, 512 or 1024 = that many threads, one
+ * CTA per instance, instances as given. PM_EINVAL on any other value or an
+ * invalid instance. */
 pm_status pm_batch_create(pm_batch **out, int ninst, const int *n, const double *L, const long long *max_np,
                           int max_fields, int tune, void *stream);
 void pm_batch_destroy(pm_batch *b);
 const char *pm_batch_last_error(const pm_batch *b);
-/* The chosen solve block threads (negative when the instances are packed
- * largest first) and the step time measured when choosing (0 if not tuned). */
-pm_status pm_batch_tuning(const pm_batch *b, int *threads, double *step_ms);
+/* The solve's setting: threads per CTA, CTAs per instance (a thread-block
+ * cluster of 1, 4 or 8 that reduces through distributed shared memory),
+ * instances packed largest first (1) or as given (0), and the step time
+ * measured when the autotuner chose it (0 if not tuned). Outputs may be NULL. */
+pm_status pm_batch_tuning(const pm_batch *b, int *threads, int *cluster, int *largest_first, double *step_ms);
+/* Fix the solve's setting (threads 256, 512 or 1024; cluster 1, 4 or 8;
+ * packing order) instead of the autotuner's; PM_EINVAL otherwise. */
+pm_status pm_batch_set_tuning(pm_batch *b, int threads, int cluster, int largest_first);
 /* Start of the batch's solves: PM_WS_DIRECT (default: the exact inverse of
  * each instance's mass matrix), PM_WS_DELTA (the delta assignment) or
  * PM_WS_ZERO; PM_EINVAL otherwise. */

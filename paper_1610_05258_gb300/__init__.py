@@ -125,7 +125,8 @@ def load_library(path: str | None = None):
         "pm_batch_create": [ctypes.POINTER(vp), i, vp, vp, vp, i, i, vp],
         "pm_batch_destroy": [vp],
         "pm_batch_last_error": [vp],
-        "pm_batch_tuning": [vp, ctypes.POINTER(i), ctypes.POINTER(d)],
+        "pm_batch_tuning": [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d)],
+        "pm_batch_set_tuning": [vp, i, i, i],
         "pm_batch_assign_mass": [vp, vp, vp, vp, vp, i, vp, d, i, vp],
         "pm_batch_set_start": [vp, i],
         "pm_net_num_params": [],
@@ -460,10 +461,16 @@ class Batch:
             self.h = None
 
     def tuning(self):
-        """(solve block threads, packed largest first, step ms measured when tuning)."""
-        s, ms = ctypes.c_int(0), ctypes.c_double(0.0)
-        self.lib.pm_batch_tuning(self.h, ctypes.byref(s), ctypes.byref(ms))
-        return abs(s.value), s.value < 0, ms.value
+        """(solve threads per CTA, CTAs per instance, packed largest first, step
+        ms measured when tuning)."""
+        th, cl, lf, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+        self.lib.pm_batch_tuning(self.h, ctypes.byref(th), ctypes.byref(cl), ctypes.byref(lf), ctypes.byref(ms))
+        return th.value, cl.value, bool(lf.value), ms.value
+
+    def set_tuning(self, threads, cluster=1, largest_first=False):
+        s = self.lib.pm_batch_set_tuning(self.h, threads, cluster, int(largest_first))
+        if s != 0:
+            raise PMError(s, self.lib.pm_batch_last_error(self.h).decode())
 
     def set_start(self, warm_start="direct"):
         ws = {"direct": PM_WS_DIRECT, "delta": PM_WS_DELTA, "zero": PM_WS_ZERO, "user": PM_WS_USER,

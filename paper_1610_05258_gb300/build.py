@@ -12,12 +12,23 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 CHECKED = os.environ.get("PM_CHECKED") == "1"  # debugging build with index checks
-OUT = os.path.join(HERE, "_build_checked" if CHECKED else "_build")
-LIB = os.path.join(OUT, "libpmt.so")
+# Accumulation variants for the precision study (tests only): "plain" FP32
+# sums without compensation, "fp64" sums in double; "" is the library.
+VARIANTS = {"": [], "plain": ["-DPM_PLAIN_SUMS"], "fp64": ["-DPM_FP64_SUMS"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 if CHECKED:
     FLAGS.append("-DPM_CHECKED")
+
+
+def out_dir(variant: str = "") -> str:
+    if CHECKED:
+        return os.path.join(HERE, "_build_checked")
+    return os.path.join(HERE, "_build" + ("_" + variant if variant else ""))
+
+
+OUT = out_dir()
+LIB = os.path.join(OUT, "libpmt.so")
 
 
 def _nvcc():
@@ -34,22 +45,25 @@ def _stale(obj, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, variant: str = "") -> str:
+    out = out_dir(variant)
+    lib = os.path.join(out, "libpmt.so")
+    flags = FLAGS + VARIANTS[variant]
+    os.makedirs(out, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(ROOT, "include", "pmt.h")]
     nvcc = _nvcc()
     jobs = []
     objs = []
     for s in srcs:
-        o = os.path.join(OUT, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(out, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or _stale(o, [s, *headers]):
             jobs.append((s, o))
 
     def run(job):
         s, o = job
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", s, "-o", o]
+        cmd = [nvcc, *ARCH, *flags, "-c", s, "-o", o]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -61,13 +75,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for msg in ex.map(run, jobs):
             if verbose and msg:
                 sys.stderr.write(msg)
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".{os.getpid()}.tmp"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".{os.getpid()}.tmp"
         r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -16,16 +16,17 @@
 //              or the delta assignment per particle, or zero)
 //   solve      mean mode, true residual, CG if it is not yet
 //              below rtol, conservation and stability report,
-//              result written to the caller's array             (one block per instance)
+//              result written to the caller's array             (one cluster per instance)
 //
 // about 18 launches per step whatever the number of instances, captured once
 // into a CUDA graph and replayed while the arguments stay the same. Tables
 // resolve a particle, cell or tile to its instance (binary search over the
 // offsets). The autotuner times one step for each candidate setting the first
 // time a batch of a given size class runs on a device and keeps the fastest:
-// the threads of the per-instance solve block and the packing order of the
-// instances (as given, or largest first so that the longest solve blocks
-// start first).
+// the threads per CTA and the CTAs per instance (a thread-block cluster that
+// reduces through distributed shared memory) of the solve, and the packing
+// order of the instances (as given, or largest first so that the longest
+// solves start first).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -35,22 +36,53 @@
 #include <tuple>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
-// Block-wide sum of one double per thread (all threads receive it); fixed
-// order: warp shuffle tree, then the warps' sums in index order.
-template <int NT>
-__device__ __forceinline__ double block_sum(double v, double *sh) {
+// Cluster-wide sum of one double per thread (every thread of the cluster
+// receives it): warp shuffle tree, the warps' sums in index order, then the
+// CTAs' sums read from each CTA's shared memory (DSMEM) in rank order, so the
+// result is the same on every CTA and every run. slot[2] alternates between
+// calls: a CTA writes slot[ph] only after every CTA has passed the barrier of
+// the previous call, which follows its reads of slot[ph] two calls back.
+template <int NT, int CS>
+__device__ __forceinline__ double cluster_sum(double v, double *sh, double *slot, int &ph) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __syncthreads();
     if (lane == 0) sh[wid] = v;
     __syncthreads();
-    double s = 0.0;
-    for (int k = 0; k < NT / 32; ++k) s += sh[k];
-    return s;
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < NT / 32; ++k) s += sh[k];
+        slot[ph] = s;
+    }
+    double tot = 0.0;
+    if (CS == 1) {
+        __syncthreads();
+        tot = slot[ph];
+    } else {
+        cg::cluster_group cl = cg::this_cluster();
+        cl.sync();
+        for (int r = 0; r < CS; ++r) tot += *cl.map_shared_rank(&slot[ph], r);
+    }
+    ph ^= 1;
+    return tot;
+}
+
+// Barrier over the instance's threads (the CTA, or its cluster), ordering
+// their global-memory writes before the reads that follow.
+template <int CS>
+__device__ __forceinline__ void instance_sync() {
+    if (CS == 1)
+        __syncthreads();
+    else
+        cg::this_cluster().sync();
 }
 
 __global__ void k_pack(BTab t, const float *const *__restrict__ px, const float *const *__restrict__ py,
@@ -84,15 +116,20 @@ struct SolveArgs {
     const unsigned char *deg;
 };
 
-// One block per instance: the same steps as the grid-wide CG kernel on one
+// One cluster of CS CTAs per instance: the same steps as the grid-wide CG kernel on one
 // mesh (power-of-two field scale, exact mean mode from sum b, true residual
 // with the compensated stencil, CG iterations only while it is above rtol),
 // then the conservation sums and the result in the caller's array.
-template <int NT>
+template <int NT, int CS>
 __global__ void __launch_bounds__(NT) k_batch_solve(SolveArgs a) {
     __shared__ double sh[NT / 32];
+    __shared__ double slot[2];
+    int ph = 0;
     const BTab &t = a.t;
-    const int k = a.order[blockIdx.x];
+    // instance = cluster index; this CTA's threads take every CS-th chunk of NT
+    const int k = a.order[blockIdx.x / CS];
+    const int rank = CS == 1 ? 0 : (int)(blockIdx.x % CS);
+    const ll t0 = (ll)rank * NT + threadIdx.x, TS = (ll)NT * CS;
     const BInst I = t.inst[k];
     const int n = I.n;
     const ll nn = (ll)n * n, co = t.coff[k], p0 = t.poff[k], p1 = t.poff[k + 1];
@@ -106,31 +143,31 @@ __global__ void __launch_bounds__(NT) k_batch_solve(SolveArgs a) {
         float *xf = a.x + fo, *rf = a.r + fo, *pf = a.p + fo, *qf = a.q + fo;
         // sums of b, |b| and the start
         Dot2 sb, sa, sx;
-        for (ll i = threadIdx.x; i < nn; i += NT) {
+        for (ll i = t0; i < nn; i += TS) {
             const float bv = bf[i];
             sb.add(bv);
             sa.add(fabsf(bv));
             sx.add(xf[i]);
         }
-        const double sumb = block_sum<NT>((double)sb.hi + (double)sb.lo, sh);
-        const double suma = block_sum<NT>((double)sa.hi + (double)sa.lo, sh);
-        const double sumx = block_sum<NT>((double)sx.hi + (double)sx.lo, sh);
+        const double sumb = cluster_sum<NT, CS>((double)sb.hi + (double)sb.lo, sh, slot, ph);
+        const double suma = cluster_sum<NT, CS>((double)sa.hi + (double)sa.lo, sh, slot, ph);
+        const double sumx = cluster_sum<NT, CS>((double)sx.hi + (double)sx.lo, sh, slot, ph);
         const float S = solve_scale(suma / (double)nn);
         const float shv = (float)((double)S * (sumb / ((double)nn * hd) - sumx / (double)nn));
         // scaled start with the exact mean mode, scaled b (into q) and |S b|^2
         Dot2 s2;
-        for (ll i = threadIdx.x; i < nn; i += NT) {
+        for (ll i = t0; i < nn; i += TS) {
             xf[i] = xf[i] * S + shv;
             const float bv = bf[i] * S;
             qf[i] = bv;
             s2.fma_acc(bv, bv);
         }
-        const double bb = block_sum<NT>((double)s2.hi + (double)s2.lo, sh);
-        __syncthreads();
+        const double bb = cluster_sum<NT, CS>((double)s2.hi + (double)s2.lo, sh, slot, ph);
+        instance_sync<CS>();
         // r = S b - M x, p = r (q keeps S b until the first iteration)
         auto residual = [&](bool set_p) {
             Dot2 s;
-            for (ll i = threadIdx.x; i < nn; i += NT) {
+            for (ll i = t0; i < nn; i += TS) {
                 float hi, lo;
                 stencil<2, 0>(xf, n, i, hi, lo);
                 const float rv = fmaf(-c, hi, qf[i]) - c * lo;
@@ -138,7 +175,7 @@ __global__ void __launch_bounds__(NT) k_batch_solve(SolveArgs a) {
                 if (set_p) pf[i] = rv;
                 s.fma_acc(rv, rv);
             }
-            return block_sum<NT>((double)s.hi + (double)s.lo, sh);
+            return cluster_sum<NT, CS>((double)s.hi + (double)s.lo, sh, slot, ph);
         };
         double rr = residual(true);
         const double init = bb > 0.0 ? sqrt(rr / bb) : 0.0;
@@ -149,68 +186,68 @@ __global__ void __launch_bounds__(NT) k_batch_solve(SolveArgs a) {
             // exact power of two)
             for (it = 0; it < a.max_iter && rr > tol2 * bb; ++it) {
                 Dot2 pq;
-                for (ll i = threadIdx.x; i < nn; i += NT) {
+                for (ll i = t0; i < nn; i += TS) {
                     float hi, lo;
                     stencil<2, 0>(pf, n, i, hi, lo);
                     const float qv = c * hi + c * lo;
                     qf[i] = qv;
                     pq.fma_acc(pf[i], qv);
                 }
-                const double dpq = block_sum<NT>((double)pq.hi + (double)pq.lo, sh);
+                const double dpq = cluster_sum<NT, CS>((double)pq.hi + (double)pq.lo, sh, slot, ph);
                 if (!(dpq > 0.0)) break;
                 const float al = (float)(rr / dpq);
                 Dot2 s;
-                for (ll i = threadIdx.x; i < nn; i += NT) {
+                for (ll i = t0; i < nn; i += TS) {
                     xf[i] = fmaf(al, pf[i], xf[i]);
                     const float rv = fmaf(-al, qf[i], rf[i]);
                     rf[i] = rv;
                     s.fma_acc(rv, rv);
                 }
-                const double rn = block_sum<NT>((double)s.hi + (double)s.lo, sh);
+                const double rn = cluster_sum<NT, CS>((double)s.hi + (double)s.lo, sh, slot, ph);
                 const float be = (float)(rn / rr);
                 rr = rn;
-                for (ll i = threadIdx.x; i < nn; i += NT) pf[i] = fmaf(be, pf[i], rf[i]);
-                __syncthreads();
+                for (ll i = t0; i < nn; i += TS) pf[i] = fmaf(be, pf[i], rf[i]);
+                instance_sync<CS>();
             }
             // true residual against S b (rebuilt in q)
-            for (ll i = threadIdx.x; i < nn; i += NT) qf[i] = bf[i] * S;
-            __syncthreads();
+            for (ll i = t0; i < nn; i += TS) qf[i] = bf[i] * S;
+            instance_sync<CS>();
             rr = residual(false);
         }
         // result, conservation and stability
         const float inv = 1.0f / S;  // a power of two: exact
         float *o = a.out[k] + (ll)f * nn;
         Dot2 sxx, em;
-        for (ll i = threadIdx.x; i < nn; i += NT) {
+        for (ll i = t0; i < nn; i += TS) {
             const float xv = xf[i] * inv;
             o[i] = xv;
             sxx.add(xv);
         }
-        const double sum_mesh = block_sum<NT>((double)sxx.hi + (double)sxx.lo, sh) * hd;
-        __syncthreads();
+        const double sum_mesh = cluster_sum<NT, CS>((double)sxx.hi + (double)sxx.lo, sh, slot, ph) * hd;
+        instance_sync<CS>();
         if (a.report) {
-            for (ll i = threadIdx.x; i < nn; i += NT) {
+            for (ll i = t0; i < nn; i += TS) {
                 float hi, lo;
                 stencil<2, 0>(o, n, i, hi, lo);
                 em.fma_acc(o[i], hi);
                 em.fma_acc(o[i], lo);
             }
         }
-        const double emesh = block_sum<NT>((double)em.hi + (double)em.lo, sh) * ((double)I.L / n) * ((double)I.L / n) / 36.0;
+        const double emesh = cluster_sum<NT, CS>((double)em.hi + (double)em.lo, sh, slot, ph) * ((double)I.L / n) * ((double)I.L / n) / 36.0;
         Dot2 pa, pb;
         const float *vf = a.vals + (ll)f * t.NP;
-        for (ll s = p0 + threadIdx.x; s < p1; s += NT) {
+        for (ll s = p0 + t0; s < p1; s += TS) {
             const float v = a.vol[s], y = vf[s];
             pa.fma_acc(v, y);
             pb.fma_acc(v, fabsf(y));
         }
-        const double sp = block_sum<NT>((double)pa.hi + (double)pa.lo, sh);
-        const double spa = block_sum<NT>((double)pb.hi + (double)pb.lo, sh);
+        const double sp = cluster_sum<NT, CS>((double)pa.hi + (double)pa.lo, sh, slot, ph);
+        const double spa = cluster_sum<NT, CS>((double)pb.hi + (double)pb.lo, sh, slot, ph);
         // int A^2 over the instance's owned triangles (A^T M_p A)
         double ep = 0.0;
         if (a.report) {
             Dot2 e;
-            for (ll s = p0 + threadIdx.x; s < p1; s += NT) {
+            for (ll s = p0 + t0; s < p1; s += TS) {
                 const int m = a.deg[s];
                 if (m < 3) continue;
                 const uint2 Xp = a.pos[s];
@@ -233,9 +270,9 @@ __global__ void __launch_bounds__(NT) k_batch_solve(SolveArgs a) {
                     ca = cb;
                 }
             }
-            ep = block_sum<NT>((double)e.hi + (double)e.lo, sh) * I.L * I.L / 12.0;
+            ep = cluster_sum<NT, CS>((double)e.hi + (double)e.lo, sh, slot, ph) * I.L * I.L / 12.0;
         }
-        if (threadIdx.x == 0) {
+        if (t0 == 0) {
             double *r = a.scal + ((ll)k * PM_MAXF + f) * 16;
             const double res = bb > 0.0 ? sqrt(rr / bb) : 0.0;
             r[0] = it;
@@ -248,9 +285,9 @@ __global__ void __launch_bounds__(NT) k_batch_solve(SolveArgs a) {
             r[7] = ep;
             if (res > a.rtol) bad = true;
         }
-        __syncthreads();
+        instance_sync<CS>();
     }
-    if (threadIdx.x == 0 && bad) atomicOr(a.status, ST_NOTCONV);
+    if (t0 == 0 && bad) atomicOr(a.status, ST_NOTCONV);
 }
 
 }  // namespace
@@ -280,6 +317,7 @@ struct pm_batch {
     int ntiles_rhs = 0, ntiles_dir = 0;
     // tuning
     int threads = 0;     // solve block threads (256, 512, 1024); 0 = autotune
+    int cluster = 1;     // CTAs per instance in the solve (a thread-block cluster of 1, 4 or 8)
     int largest_first = 0;
     int start = PM_WS_DIRECT;  // start of the solves
     double tuned_ms = 0.0;
@@ -295,7 +333,10 @@ struct pm_batch {
 namespace {
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune;  // (device, size class) -> setting
+struct Tune {
+    int threads = 0, cluster = 1, largest_first = 0;
+};
+std::map<std::tuple<int, int, int, int, int>, Tune> g_tune;  // (device, size class) -> setting
 
 pm_status bfail(pm_batch *b, pm_status s, const std::string &m) {
     b->err = m;
@@ -397,6 +438,43 @@ pm_status set_pointers(pm_batch *b, const float *const *px, const float *const *
     return ok ? PM_OK : bfail(b, PM_ECUDA, "batch pointer upload");
 }
 
+using SolveKernel = void (*)(SolveArgs);
+
+SolveKernel solve_kernel(int threads, int cs) {
+    if (threads == 1024)
+        return cs == 8 ? k_batch_solve<1024, 8> : (cs == 4 ? k_batch_solve<1024, 4> : k_batch_solve<1024, 1>);
+    if (threads == 256)
+        return cs == 8 ? k_batch_solve<256, 8> : (cs == 4 ? k_batch_solve<256, 4> : k_batch_solve<256, 1>);
+    return cs == 8 ? k_batch_solve<512, 8> : (cs == 4 ? k_batch_solve<512, 4> : k_batch_solve<512, 1>);
+}
+
+cudaLaunchConfig_t solve_config(int K, int threads, int cs, cudaStream_t st, cudaLaunchAttribute *attr) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(K * cs);
+    cfg.blockDim = dim3(threads);
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+// Whether a (threads, cluster) setting of the solve can run on this device.
+bool solve_fits(int threads, int cs) {
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = solve_config(1, threads, cs, nullptr, attr);
+    int n = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, solve_kernel(threads, cs), &cfg);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return n > 0;
+}
+
 // Queue one step on the batch's main stream.
 int enqueue_step(pm_batch *b, int F, double rtol, int max_iter, int report) {
     const BTab &t = b->tab;
@@ -436,13 +514,11 @@ int enqueue_step(pm_batch *b, int F, double rtol, int max_iter, int report) {
     a.nbr = w.nbr;
     a.deg = w.deg;
     const int K = b->ninst;
-    if (b->threads == 1024)
-        k_batch_solve<1024><<<K, 1024, 0, st>>>(a);
-    else if (b->threads == 256)
-        k_batch_solve<256><<<K, 256, 0, st>>>(a);
-    else
-        k_batch_solve<512><<<K, 512, 0, st>>>(a);
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = solve_config(K, b->threads, b->cluster, st, attr);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, solve_kernel(b->threads, b->cluster), a);
     count_launches(1);
+    if (e != cudaSuccess) return (int)e;
     return (int)cudaGetLastError();
 }
 
@@ -547,10 +623,28 @@ pm_status pm_batch_set_start(pm_batch *b, int warm_start) {
     return PM_OK;
 }
 
-pm_status pm_batch_tuning(const pm_batch *b, int *threads, double *step_ms) {
+pm_status pm_batch_tuning(const pm_batch *b, int *threads, int *cluster, int *largest_first, double *step_ms) {
     if (!b) return PM_EINVAL;
-    if (threads) *threads = b->threads * (b->largest_first ? -1 : 1);
+    if (threads) *threads = b->threads;
+    if (cluster) *cluster = b->cluster;
+    if (largest_first) *largest_first = b->largest_first;
     if (step_ms) *step_ms = b->tuned_ms;
+    return PM_OK;
+}
+
+pm_status pm_batch_set_tuning(pm_batch *b, int threads, int cluster, int largest_first) {
+    if (!b) return PM_EINVAL;
+    if ((threads != 256 && threads != 512 && threads != 1024) || (cluster != 1 && cluster != 4 && cluster != 8))
+        return bfail(b, PM_EINVAL, "threads must be 256, 512 or 1024 and cluster 1, 4 or 8");
+    if (!solve_fits(threads, cluster)) return bfail(b, PM_EINVAL, "this cluster does not fit the device");
+    b->threads = threads;
+    b->cluster = cluster;
+    b->fixed = true;
+    if ((largest_first != 0) != (b->largest_first != 0)) {
+        pm_status s = set_layout(b, b->np.data(), largest_first != 0);
+        if (s) return s;
+    }
+    b->key.clear();  // recapture
     return PM_OK;
 }
 
@@ -569,27 +663,31 @@ pm_status pm_batch_assign_mass(pm_batch *b, const float *const *px, const float 
     cudaEventRecord(b->fork, b->user);
     cudaStreamWaitEvent(b->main, b->fork, 0);
     bool same_np = b->np.size() == (size_t)K && std::equal(b->np.begin(), b->np.end(), np);
-    // autotune once per (device, size class): solve block threads x packing order
+    // autotune once per (device, size class): the solve's threads per CTA and
+    // CTAs per instance (cluster) x the packing order
     if (!b->fixed && b->threads == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         ll NPt = 0;
         for (int k = 0; k < K; ++k) NPt += np[k];
         const auto cls = std::make_tuple(dev, K, (int)std::log2((double)NPt + 1.0), (int)std::log2((double)b->NC + 1.0), F);
-        std::pair<int, int> best{0, 0};
+        Tune best;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             auto it = g_tune.find(cls);
             if (it != g_tune.end()) best = it->second;
         }
-        if (!best.first) {
+        if (!best.threads) {
             double best_ms = 1e30;
-            for (int lf : {0, 1}) {
+            const int cand[5][2] = {{1024, 1}, {512, 4}, {1024, 4}, {512, 8}, {1024, 8}};
+            for (int lf : {1, 0}) {
                 pm_status s = set_layout(b, np, lf);
                 if (s) return s;
                 if ((s = set_pointers(b, px, py, vals, mesh_out))) return s;
-                for (int th : {256, 512, 1024}) {
-                    b->threads = th;
+                for (const auto &c : cand) {
+                    if (!solve_fits(c[0], c[1])) continue;
+                    b->threads = c[0];
+                    b->cluster = c[1];
                     int e = enqueue_step(b, F, rtol, max_iter, 0);  // warm
                     cudaEventRecord(b->t0, b->main);
                     e |= enqueue_step(b, F, rtol, max_iter, 0);
@@ -599,7 +697,9 @@ pm_status pm_batch_assign_mass(pm_batch *b, const float *const *px, const float 
                     cudaEventElapsedTime(&ms, b->t0, b->t1);
                     if (ms < best_ms) {
                         best_ms = ms;
-                        best = {th, lf};
+                        best.threads = c[0];
+                        best.cluster = c[1];
+                        best.largest_first = lf;
                     }
                 }
             }
@@ -607,9 +707,10 @@ pm_status pm_batch_assign_mass(pm_batch *b, const float *const *px, const float 
             std::lock_guard<std::mutex> lk(g_tune_mu);
             g_tune[cls] = best;
         }
-        b->threads = best.first;
-        if (best.second != b->largest_first || !same_np) {
-            pm_status s = set_layout(b, np, best.second);
+        b->threads = best.threads;
+        b->cluster = best.cluster;
+        if (best.largest_first != b->largest_first || !same_np) {
+            pm_status s = set_layout(b, np, best.largest_first);
             if (s) return s;
         }
     } else if (!same_np) {
@@ -620,6 +721,8 @@ pm_status pm_batch_assign_mass(pm_batch *b, const float *const *px, const float 
     std::vector<const void *> key;
     key.push_back((const void *)(ll)F);
     key.push_back((const void *)(ll)b->threads);
+    key.push_back((const void *)(ll)b->cluster);
+    key.push_back((const void *)(ll)b->largest_first);
     key.push_back((const void *)(ll)b->start);
     for (int k = 0; k < K; ++k) {
         key.push_back(px[k]);

@@ -198,6 +198,38 @@ __device__ __forceinline__ uint32_t cell_frac(uint32_t X, int n) { return (uint3
 __device__ __forceinline__ float frac_f(uint32_t X, int n) { return (float)cell_frac(X, n) * 2.3283064365386963e-10f; }
 __device__ __forceinline__ int wrapi(int i, int n) { int r = i % n; return r < 0 ? r + n : r; }
 
+// Accumulators. The library's arithmetic is the compensated one (PM_SUMS
+// unset): FP32 values with error-free transformations. Two other builds exist
+// only for the precision study of the tests (the build script's variants):
+// PM_PLAIN_SUMS accumulates in plain FP32, PM_FP64_SUMS in FP64.
+#if defined(PM_PLAIN_SUMS)
+struct KSum {
+    float s;
+    __device__ __forceinline__ KSum() : s(0.f) {}
+    __device__ __forceinline__ void add(float x) { s += x; }
+    __device__ __forceinline__ float get() const { return s; }
+};
+struct Dot2 {
+    float hi, lo;
+    __device__ __forceinline__ Dot2() : hi(0.f), lo(0.f) {}
+    __device__ __forceinline__ void fma_acc(float a, float b) { hi = fmaf(a, b, hi); }
+    __device__ __forceinline__ void add(float a) { hi += a; }
+};
+#elif defined(PM_FP64_SUMS)
+struct KSum {
+    double s;
+    __device__ __forceinline__ KSum() : s(0.0) {}
+    __device__ __forceinline__ void add(float x) { s += (double)x; }
+    __device__ __forceinline__ float get() const { return (float)s; }
+};
+struct Dot2 {
+    double hi;
+    float lo;
+    __device__ __forceinline__ Dot2() : hi(0.0), lo(0.f) {}
+    __device__ __forceinline__ void fma_acc(float a, float b) { hi = fma((double)a, (double)b, hi); }
+    __device__ __forceinline__ void add(float a) { hi += (double)a; }
+};
+#else
 // Compensated (Kahan-Babuska/Neumaier) accumulator in FP32.
 struct KSum {
     float s, c;
@@ -238,6 +270,8 @@ struct Dot2 {
         lo += e;
     }
 };
+
+#endif
 
 // Compensated M x at node i of field array xf; returns (hi, lo) of the
 // unscaled stencil sum; the caller multiplies by c = h/6, h^2/36 (bilinear)

@@ -51,12 +51,34 @@ def test_batch_matches_oracle_and_single_context(case, tune):
             assert info[k][f].energy_mesh == pytest.approx(sinfo[f].energy_mesh, rel=1e-5)
             assert info[k][f].energy_particles == pytest.approx(sinfo[f].energy_particles, rel=1e-5)
             assert info[k][f].sum_particles == pytest.approx(sinfo[f].sum_particles, rel=1e-6, abs=1e-12)
-    threads, largest_first, ms = b.tuning()
-    assert threads in (256, 512, 1024)
+    threads, cluster, largest_first, ms = b.tuning()
+    assert threads in (256, 512, 1024) and cluster in (1, 4, 8)
     if tune:
-        assert threads == tune and not largest_first and ms == 0.0
+        assert threads == tune and cluster == 1 and not largest_first and ms == 0.0
     else:
         assert ms > 0.0
+
+
+@pytest.mark.parametrize("threads,cluster,largest_first", [(1024, 8, True), (512, 4, False), (256, 8, False)])
+def test_batch_solve_on_clusters(case, threads, cluster, largest_first):
+    """The per-instance solve on a thread-block cluster (reductions through
+    distributed shared memory) gives the same fields, from the exact-inverse
+    start and from the zero start (CG iterations across the cluster)."""
+    from paper_1610_05258_gb300 import Batch
+    insts, want = case
+    b = Batch([i.n for i in insts], [i.L for i in insts], [i.np for i in insts], max_fields=2)
+    b.set_tuning(threads, cluster, largest_first)
+    assert b.tuning()[:3] == (threads, cluster, largest_first)
+    for start in ("direct", "zero"):
+        b.set_start(start)
+        outs, info, _ = _run(b, insts)
+        for k in range(len(insts)):
+            assert rel_l2(outs[k].double().cpu().numpy(), want[k]) <= 1e-5, (start, k)
+            for f in range(2):
+                assert info[k][f].rel_resid <= 1e-6 and info[k][f].cons_err <= 1e-6
+                assert info[k][f].energy_mesh <= info[k][f].energy_particles * (1 + 1e-6)
+        if start == "zero":
+            assert min(x.iters for row in info for x in row) > 0
 
 
 def test_batch_graph_replay_and_launch_count(case):
