@@ -447,9 +447,11 @@ pm_status pm_profile_read(pm_ctx *ctx, double *ms, long long *calls, int reset);
  * after each clip, summed over all particles and calls since the last reset,
  * each particle counted once, in the pass that completes its cell.
  * counts[5] = cells the main pass gave up to the retry passes (capacity 9),
- * counts[6] = cells the first retry pass gave up to the last (capacity 12).
+ * counts[6] = cells the first retry pass gave up to the last (capacity 12),
+ * counts[7] = in-circle vertex tests the float filter could not decide and
+ * left to the exact 128-bit predicate.
  * Waits for the context's stream. Host array of `ncounts` entries (entries
- * past 6 are written as 0). PM_EINVAL on a NULL ctx or array. */
+ * past 7 are written as 0). PM_EINVAL on a NULL ctx or array. */
 pm_status pm_work_read(pm_ctx *ctx, long long *counts, int ncounts, int reset);
 const char *pm_phase_name(int phase);
 /* Number of kernels this library has launched in the process so far. */

@@ -38,7 +38,8 @@ EXPORTS = [
     "pm_net_num_params", "pm_net_create", "pm_net_destroy", "pm_net_set_stream", "pm_net_state", "pm_net_load",
     "pm_net_forward", "pm_net_train_step", "pm_net_grad", "pm_net_features",
 ]
-WORK_COUNTERS = ["candidates", "tested", "vertex_tests", "clips", "cell_size_sum", "retried", "retried_last"]
+WORK_COUNTERS = ["candidates", "tested", "vertex_tests", "clips", "cell_size_sum", "retried", "retried_last",
+                 "exact_tests"]
 PHASES = ["sort", "triangulate", "delta", "flip", "rhs", "solve", "g2p", "advect", "other", "net"]
 
 

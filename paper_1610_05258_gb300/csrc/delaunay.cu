@@ -135,7 +135,7 @@ __device__ __forceinline__ float set_vertex(PolyS<NB> P, int k, float ax, float 
 // Work of the cells a pass completes (a pass that gives a cell up to a larger
 // capacity drops what it counted for it), and the cells given up.
 struct WorkCount {
-    unsigned cand = 0, tested = 0, vtests = 0, clips = 0, msum = 0, over = 0;
+    unsigned cand = 0, tested = 0, vtests = 0, clips = 0, msum = 0, over = 0, exact = 0;
 };
 
 // Clip the cell of p by the bisector of candidate s (relative position
@@ -174,6 +174,7 @@ __device__ __forceinline__ int clip_by(PolyS<NB> P, int &m, float &R2, int sx, i
         rkeep = in ? rkeep : fmaxf(rkeep, c.w);
     }
     if (undecided) {
+        if (COUNT) wc.exact += __popc(undecided);
         const int ps = perm[sidx];
         if (pp == -2) pp = perm[p];
         for (unsigned u = undecided; u; u &= u - 1) {
@@ -389,17 +390,18 @@ __device__ __forceinline__ int star_of(PolyS<NB> P, int p, const Geo &g, ll np, 
     return 0;
 }
 
-// Work counters 0..4 into wsum[0..4], the give-ups into wsum[over_slot].
+// Work counters 0..4 into wsum[0..4], the give-ups into wsum[over_slot], the
+// vertex tests the float filter left to the exact predicate into wsum[7].
 template <bool COUNT>
 __device__ __forceinline__ void add_counts(const WorkCount &wc, ull *__restrict__ wsum, int over_slot) {
     if (!COUNT) return;
     // warp sums, one atomic per warp and counter
-    unsigned v[6] = {wc.cand, wc.tested, wc.vtests, wc.clips, wc.msum, wc.over};
+    unsigned v[7] = {wc.cand, wc.tested, wc.vtests, wc.clips, wc.msum, wc.over, wc.exact};
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
+    for (int i = 0; i < 7; ++i) {
         unsigned x = v[i];
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if ((threadIdx.x & 31) == 0 && x) atomicAdd(wsum + (i < 5 ? i : over_slot), (ull)x);
+        if ((threadIdx.x & 31) == 0 && x) atomicAdd(wsum + (i < 5 ? i : (i == 5 ? over_slot : 7)), (ull)x);
     }
 }
 
