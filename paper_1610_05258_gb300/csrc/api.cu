@@ -211,7 +211,8 @@ pm_status pm_ctx_create_mesh(pm_ctx **out, int dim, int n, double L, long long m
               alloc(c, &w.bar, 2) && alloc(c, &w.status, 1) && alloc(c, &w.empty, 1) && alloc(c, &w.ntri, 1) &&
               alloc(c, &w.wsum, 8) && alloc(c, &w.nretry, 1) && alloc(c, &w.meshmax, PM_MAXF) &&
               alloc(c, &w.pc, F * np) && alloc(c, &w.px, pcg_width((int)F) * np) &&
-              alloc(c, &w.pq, pcg_width((int)F) * np) && alloc(c, &w.prp, 2LL * pcg_width((int)F) * np);
+              alloc(c, &w.pq, pcg_width((int)F) * np) && alloc(c, &w.prp, 2LL * pcg_width((int)F) * np) &&
+              alloc(c, &w.pp2, pcg_width((int)F) * np);
     w.cfix = (ll *)w.prp;
     w.red_blocks = 4096;
     if (ok && dim == 2) ok = alloc(c, &w.nbr, (ll)PM_MAXDEG * np) && alloc(c, &w.pcoef, (ll)PM_MAXDEG * np);
@@ -244,7 +245,7 @@ void pm_ctx_destroy(pm_ctx *c) {
     void *ptrs[] = {w.fx,  w.key, w.slot, w.count, w.cell_start, w.scan_tmp, w.tmp,  w.perm,  w.pos,
                     w.vals, w.maxabs, w.nbr, w.deg,  w.vol,  w.part,  w.bfix, w.psum, w.epart, w.r, w.p,
                     w.q,   w.b,   w.red,  w.scal,  w.bar,  w.status, w.empty, w.ntri, w.feat, w.corr,
-                    w.wsum, w.nretry, w.meshmax, w.pc, w.px, w.pq, w.prp, w.pcoef, w.mesh_il};
+                    w.wsum, w.nretry, w.meshmax, w.pc, w.px, w.pq, w.prp, w.pp2, w.pcoef, w.mesh_il};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (w.hstatus) cudaFreeHost(w.hstatus);
@@ -528,7 +529,7 @@ pm_status pm_interpolate_mass(pm_ctx *c, const float *mesh, int F, const float *
     }
     if (e) return cuda_fail(c, (cudaError_t)e, "pm_interpolate_mass solve launch");
     if ((s = check_launch(c, "pm_interpolate_mass"))) return s;
-    if (info) return report(c, F, info, mesh, np, c->w.px, 1, pcg_width(c->w.F_max));
+    if (info) return report(c, F, info, mesh, np, c->w.pq, 1, pcg_width(F));
     return PM_OK;
 }
 

@@ -177,8 +177,10 @@ struct Work {
     // mesh -> particle projections (particle-sized, sorted order)
     unsigned *meshmax;     // [PM_MAXF] max |Ab| bit patterns
     float *pc;             // [F][np] right-hand side c
-    float *px, *pq;        // [np][W] solution, M_p p (W = pcg_width(F_max), fields interleaved)
-    float *prp;            // [2][np][W] residual and search direction (r, then p)
+    float *px, *pq;        // [np][W] iterate, M_p p; the solution ends in pq (W = pcg_width(F_max),
+                           // fields interleaved; the solve of F fields uses stride pcg_width(F))
+    float *prp;            // [2][np][W] D^-1 r and the even iterations' search direction
+    float *pp2;            // [np][W] the odd iterations' search direction
     ll *cfix;              // = (ll *)prp: fixed-point c before conversion
     float *pcoef;          // [PM_MAXDEG][np] particle mass matrix rows (2D)
     float *mesh_il;        // [ncell][g2p_width(F_max)] mesh fields interleaved per node (G2P)
@@ -371,7 +373,8 @@ void launch_g2p_integral(const Geo &g, Work &w, ll np, int F, const float *mesh,
 void launch_div_vol(ll np, int F, const float *vol, float *c, cudaStream_t st);
 void launch_scale(ll m, float s, float *x, cudaStream_t st);
 // Full-mass mesh -> particle solve M_p x = c (c sorted, [F][np]); writes the
-// solution to out in caller order [F][np]. 0 or a CUDA error.
+// solution to out in caller order [F][np], and leaves it in w.pq, sorted and
+// interleaved with stride pcg_width(F). 0 or a CUDA error.
 int launch_pcg(const Geo &g, Work &w, ll np, int F, const float *c, float *out, double rtol, int max_iter,
                cudaStream_t st);
 // Interleaved width of the particle solve's vectors for F fields (2, 4 or PM_MAXF).

@@ -136,6 +136,9 @@ __device__ void particle_sums(const double *psum, int nblk, int F, double s1[PM_
 
 template <int DIM, int P1>
 __global__ void __launch_bounds__(256) k_cg(CG a) {
+    // Reduction slot groups alternate (3 (k & 1) for the k-th reduction), so a
+    // block that runs ahead never overwrites partials another block is summing.
+    int rk = 0, rg = 0;
     const Geo g = a.g;
     const int F = a.F, n = g.n;
     const ll nn = g.ncell;
@@ -162,14 +165,15 @@ __global__ void __launch_bounds__(256) k_cg(CG a) {
         w[f] = (double)sa.hi + (double)sa.lo;
         alpha[f] = (double)sx.hi + (double)sx.lo;
     }
-    block_partial(v, F, a.red, 0);
-    block_partial(w, F, a.red, 1);
-    block_partial(alpha, F, a.red, 2);
+    rg = 3 * (rk++ & 1);
+    block_partial(v, F, a.red, rg);
+    block_partial(w, F, a.red, rg + 1);
+    block_partial(alpha, F, a.red, rg + 2);
     if (!grid_sync(a.bar, a.status)) return;
     double sumb[PM_MAXF], sumx[PM_MAXF], suma[PM_MAXF];
-    grid_total(a.red, F, 0, sumb);
-    grid_total(a.red, F, 1, suma);
-    grid_total(a.red, F, 2, sumx);
+    grid_total(a.red, F, rg, sumb);
+    grid_total(a.red, F, rg + 1, suma);
+    grid_total(a.red, F, rg + 2, sumx);
     // The system is solved for S b with S a power of two that brings the mean
     // |b| to order one (exact scaling: FP32 inner products of any field stay
     // in range); x is scaled by S on entry and by 1/S on exit. Then the exact
@@ -189,9 +193,10 @@ __global__ void __launch_bounds__(256) k_cg(CG a) {
         }
         w[f] = (double)s2.hi + (double)s2.lo;
     }
-    block_partial(w, F, a.red, 3);
+    rg = 3 * (rk++ & 1);
+    block_partial(w, F, a.red, rg);
     if (!grid_sync(a.bar, a.status)) return;
-    grid_total(a.red, F, 3, bb);
+    grid_total(a.red, F, rg, bb);
     // --- r = b - M x, p = r
     for (int f = 0; f < F; ++f) {
         Dot2 s;
@@ -206,9 +211,10 @@ __global__ void __launch_bounds__(256) k_cg(CG a) {
         }
         v[f] = (double)s.hi + (double)s.lo;
     }
-    block_partial(v, F, a.red, 0);
+    rg = 3 * (rk++ & 1);
+    block_partial(v, F, a.red, rg);
     if (!grid_sync(a.bar, a.status)) return;
-    grid_total(a.red, F, 0, rr);
+    grid_total(a.red, F, rg, rr);
     const double tol2 = a.rtol * a.rtol;
     for (int f = 0; f < F; ++f) {
         act[f] = rr[f] > tol2 * bb[f] && bb[f] > 0.0;
@@ -233,10 +239,11 @@ __global__ void __launch_bounds__(256) k_cg(CG a) {
                 }
                 v[f] = (double)s.hi + (double)s.lo;
             }
-            block_partial(v, F, a.red, 0);
+            rg = 3 * (rk++ & 1);
+            block_partial(v, F, a.red, rg);
             if (!grid_sync(a.bar, a.status)) return;
             double tr[PM_MAXF];
-            grid_total(a.red, F, 0, tr);
+            grid_total(a.red, F, rg, tr);
             bool again = false;
             for (int f = 0; f < F; ++f)
                 if (bb[f] > 0.0 && tr[f] > tol2 * bb[f]) { act[f] = true; again = true; }
@@ -257,9 +264,10 @@ __global__ void __launch_bounds__(256) k_cg(CG a) {
                 }
                 v[f] = (double)s.hi + (double)s.lo;
             }
-            block_partial(v, F, a.red, 0);
+            rg = 3 * (rk++ & 1);
+            block_partial(v, F, a.red, rg);
             if (!grid_sync(a.bar, a.status)) return;
-            grid_total(a.red, F, 0, w);
+            grid_total(a.red, F, rg, w);
             for (int f = 0; f < F; ++f)
                 if (act[f]) rr[f] = w[f];
         }
@@ -278,9 +286,10 @@ __global__ void __launch_bounds__(256) k_cg(CG a) {
             }
             v[f] = (double)s.hi + (double)s.lo;
         }
-        block_partial(v, F, a.red, 0);
+        rg = 3 * (rk++ & 1);
+        block_partial(v, F, a.red, rg);
         if (!grid_sync(a.bar, a.status)) return;
-        grid_total(a.red, F, 0, w);
+        grid_total(a.red, F, rg, w);
         // x += alpha p, r -= alpha q, (r, r)
         for (int f = 0; f < F; ++f) {
             v[f] = 0.0;
@@ -297,9 +306,10 @@ __global__ void __launch_bounds__(256) k_cg(CG a) {
             }
             v[f] = (double)s.hi + (double)s.lo;
         }
-        block_partial(v, F, a.red, 0);
+        rg = 3 * (rk++ & 1);
+        block_partial(v, F, a.red, rg);
         if (!grid_sync(a.bar, a.status)) return;
-        grid_total(a.red, F, 0, w);
+        grid_total(a.red, F, rg, w);
         for (int f = 0; f < F; ++f) {
             if (!act[f]) continue;
             beta[f] = w[f] / rr[f];
@@ -332,12 +342,13 @@ __global__ void __launch_bounds__(256) k_cg(CG a) {
         v[f] = (double)s.hi + (double)s.lo;
         w[f] = (double)sx.hi + (double)sx.lo;
     }
-    block_partial(v, F, a.red, 0);
-    block_partial(w, F, a.red, 1);
+    rg = 3 * (rk++ & 1);
+    block_partial(v, F, a.red, rg);
+    block_partial(w, F, a.red, rg + 1);
     if (!grid_sync(a.bar, a.status)) return;
     double tr[PM_MAXF], sx[PM_MAXF];
-    grid_total(a.red, F, 0, tr);
-    grid_total(a.red, F, 1, sx);
+    grid_total(a.red, F, rg, tr);
+    grid_total(a.red, F, rg + 1, sx);
     double ps1[PM_MAXF], ps2[PM_MAXF];
     if (blockIdx.x == 0 && a.psum) particle_sums(a.psum, a.nblk_psum, F, ps1, ps2);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -384,6 +395,9 @@ __global__ void __launch_bounds__(256) k_cg(CG a) {
 // ---------------------------------------------------------------------------
 template <int DIM, int P1>
 __global__ void __launch_bounds__(256) k_cheb(CG a) {
+    // Reduction slot groups alternate (3 (k & 1) for the k-th reduction), so a
+    // block that runs ahead never overwrites partials another block is summing.
+    int rk = 0, rg = 0;
     const Geo g = a.g;
     const int F = a.F, n = g.n;
     const ll nn = g.ncell;
@@ -412,14 +426,15 @@ __global__ void __launch_bounds__(256) k_cheb(CG a) {
         w[f] = (double)sa.hi + (double)sa.lo;
         u[f] = (double)sx.hi + (double)sx.lo;
     }
-    block_partial(v, F, a.red, 0);
-    block_partial(w, F, a.red, 1);
-    block_partial(u, F, a.red, 2);
+    rg = 3 * (rk++ & 1);
+    block_partial(v, F, a.red, rg);
+    block_partial(w, F, a.red, rg + 1);
+    block_partial(u, F, a.red, rg + 2);
     if (!grid_sync(a.bar, a.status)) return;
     double sumb[PM_MAXF], sumx[PM_MAXF], suma[PM_MAXF];
-    grid_total(a.red, F, 0, sumb);
-    grid_total(a.red, F, 1, suma);
-    grid_total(a.red, F, 2, sumx);
+    grid_total(a.red, F, rg, sumb);
+    grid_total(a.red, F, rg + 1, suma);
+    grid_total(a.red, F, rg + 2, sumx);
     // solve for S b (S a power of two, as in k_cg), exact mean mode, |S b|^2
     float S[PM_MAXF];
     for (int f = 0; f < F; ++f) {
@@ -436,9 +451,10 @@ __global__ void __launch_bounds__(256) k_cheb(CG a) {
         }
         w[f] = (double)s2.hi + (double)s2.lo;
     }
-    block_partial(w, F, a.red, 3);
+    rg = 3 * (rk++ & 1);
+    block_partial(w, F, a.red, rg);
     if (!grid_sync(a.bar, a.status)) return;
-    grid_total(a.red, F, 3, bb);
+    grid_total(a.red, F, rg, bb);
     const double tol2 = a.rtol * a.rtol;
     int steps_done = 0, steps_f[PM_MAXF];
     for (int f = 0; f < PM_MAXF; ++f) steps_f[f] = 0;
@@ -459,12 +475,13 @@ __global__ void __launch_bounds__(256) k_cheb(CG a) {
             v[f] = (double)s.hi + (double)s.lo;
             u[f] = (double)sx.hi + (double)sx.lo;
         }
-        block_partial(v, F, a.red, 0);
-        block_partial(u, F, a.red, 1);
+        rg = 3 * (rk++ & 1);
+        block_partial(v, F, a.red, rg);
+        block_partial(u, F, a.red, rg + 1);
         if (!grid_sync(a.bar, a.status)) return;
-        grid_total(a.red, F, 0, rr);
+        grid_total(a.red, F, rg, rr);
         double sx[PM_MAXF];
-        grid_total(a.red, F, 1, sx);
+        grid_total(a.red, F, rg + 1, sx);
         if (pass == 0 && blockIdx.x == 0 && threadIdx.x == 0)
             for (int f = 0; f < F; ++f) a.scal[f * 16 + S_INIT] = bb[f] > 0.0 ? sqrt(rr[f] / bb[f]) : 0.0;
         // steps of each field for the bound 2 q^k ||r_0|| <= rtol ||b||; the
@@ -592,6 +609,9 @@ __device__ __forceinline__ void stencil4(const float *__restrict__ xf, int n, ll
 
 template <int P1>
 __global__ void __launch_bounds__(256) k_cg2v(CG a) {
+    // Reduction slot groups alternate (3 (k & 1) for the k-th reduction), so a
+    // block that runs ahead never overwrites partials another block is summing.
+    int rk = 0, rg = 0;
     const Geo g = a.g;
     const int F = a.F, n = g.n;
     const ll nn = g.ncell, nq = nn / 4;
@@ -640,14 +660,15 @@ __global__ void __launch_bounds__(256) k_cg2v(CG a) {
         w[f] = (double)sa.hi + (double)sa.lo;
         alpha[f] = (double)sx.hi + (double)sx.lo;
     }
-    block_partial(v, F, a.red, 0);
-    block_partial(w, F, a.red, 1);
-    block_partial(alpha, F, a.red, 2);
+    rg = 3 * (rk++ & 1);
+    block_partial(v, F, a.red, rg);
+    block_partial(w, F, a.red, rg + 1);
+    block_partial(alpha, F, a.red, rg + 2);
     if (!grid_sync(a.bar, a.status)) return;
     double sumb[PM_MAXF], sumx[PM_MAXF], suma[PM_MAXF];
-    grid_total(a.red, F, 0, sumb);
-    grid_total(a.red, F, 1, suma);
-    grid_total(a.red, F, 2, sumx);
+    grid_total(a.red, F, rg, sumb);
+    grid_total(a.red, F, rg + 1, suma);
+    grid_total(a.red, F, rg + 2, sumx);
     // solve for S b (S a power of two, as in k_cg), exact mean mode, |S b|^2
     float S[PM_MAXF];
     for (int f = 0; f < F; ++f) {
@@ -670,9 +691,10 @@ __global__ void __launch_bounds__(256) k_cg2v(CG a) {
         }
         w[f] = (double)s2.hi + (double)s2.lo;
     }
-    block_partial(w, F, a.red, 3);
+    rg = 3 * (rk++ & 1);
+    block_partial(w, F, a.red, rg);
     if (!grid_sync(a.bar, a.status)) return;
-    grid_total(a.red, F, 3, bb);
+    grid_total(a.red, F, rg, bb);
     // --- r = b - M x, p = r
     for (int f = 0; f < F; ++f) {
         Dot2 s;
@@ -693,9 +715,10 @@ __global__ void __launch_bounds__(256) k_cg2v(CG a) {
         }
         v[f] = (double)s.hi + (double)s.lo;
     }
-    block_partial(v, F, a.red, 0);
+    rg = 3 * (rk++ & 1);
+    block_partial(v, F, a.red, rg);
     if (!grid_sync(a.bar, a.status)) return;
-    grid_total(a.red, F, 0, rr);
+    grid_total(a.red, F, rg, rr);
     const double tol2 = a.rtol * a.rtol;
     for (int f = 0; f < F; ++f) {
         act[f] = rr[f] > tol2 * bb[f] && bb[f] > 0.0;
@@ -732,10 +755,11 @@ __global__ void __launch_bounds__(256) k_cg2v(CG a) {
         if (!any) {
             // recursive residuals converged: check the true residual once
             for (int f = 0; f < F; ++f) v[f] = true_resid(f, false);
-            block_partial(v, F, a.red, 0);
+            rg = 3 * (rk++ & 1);
+            block_partial(v, F, a.red, rg);
             if (!grid_sync(a.bar, a.status)) return;
             double tr[PM_MAXF];
-            grid_total(a.red, F, 0, tr);
+            grid_total(a.red, F, rg, tr);
             bool again = false;
             for (int f = 0; f < F; ++f)
                 if (bb[f] > 0.0 && tr[f] > tol2 * bb[f]) { act[f] = true; again = true; }
@@ -743,9 +767,10 @@ __global__ void __launch_bounds__(256) k_cg2v(CG a) {
             ++restarts;
             // restart the drifted fields from their true residual
             for (int f = 0; f < F; ++f) v[f] = act[f] ? true_resid(f, true) : 0.0;
-            block_partial(v, F, a.red, 0);
+            rg = 3 * (rk++ & 1);
+            block_partial(v, F, a.red, rg);
             if (!grid_sync(a.bar, a.status)) return;
-            grid_total(a.red, F, 0, w);
+            grid_total(a.red, F, rg, w);
             for (int f = 0; f < F; ++f)
                 if (act[f]) rr[f] = w[f];
         }
@@ -768,9 +793,10 @@ __global__ void __launch_bounds__(256) k_cg2v(CG a) {
             }
             v[f] = (double)s.hi + (double)s.lo;
         }
-        block_partial(v, F, a.red, 0);
+        rg = 3 * (rk++ & 1);
+        block_partial(v, F, a.red, rg);
         if (!grid_sync(a.bar, a.status)) return;
-        grid_total(a.red, F, 0, w);
+        grid_total(a.red, F, rg, w);
         // x += alpha p, r -= alpha q, (r, r)
         for (int f = 0; f < F; ++f) {
             v[f] = 0.0;
@@ -792,9 +818,10 @@ __global__ void __launch_bounds__(256) k_cg2v(CG a) {
             }
             v[f] = (double)s.hi + (double)s.lo;
         }
-        block_partial(v, F, a.red, 0);
+        rg = 3 * (rk++ & 1);
+        block_partial(v, F, a.red, rg);
         if (!grid_sync(a.bar, a.status)) return;
-        grid_total(a.red, F, 0, w);
+        grid_total(a.red, F, rg, w);
         for (int f = 0; f < F; ++f) {
             if (!act[f]) continue;
             beta[f] = w[f] / rr[f];
@@ -836,12 +863,13 @@ __global__ void __launch_bounds__(256) k_cg2v(CG a) {
         v[f] = (double)s.hi + (double)s.lo;
         w[f] = (double)sx.hi + (double)sx.lo;
     }
-    block_partial(v, F, a.red, 0);
-    block_partial(w, F, a.red, 1);
+    rg = 3 * (rk++ & 1);
+    block_partial(v, F, a.red, rg);
+    block_partial(w, F, a.red, rg + 1);
     if (!grid_sync(a.bar, a.status)) return;
     double tr[PM_MAXF], sx[PM_MAXF];
-    grid_total(a.red, F, 0, tr);
-    grid_total(a.red, F, 1, sx);
+    grid_total(a.red, F, rg, tr);
+    grid_total(a.red, F, rg + 1, sx);
     double ps1[PM_MAXF], ps2[PM_MAXF];
     if (blockIdx.x == 0 && a.psum) particle_sums(a.psum, a.nblk_psum, F, ps1, ps2);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -892,12 +920,22 @@ __global__ void k_mass_apply(Geo g, const float *__restrict__ x, int F, float *_
 // stars (2D: diagonal v/2 and, for neighbour q_k, the coefficient
 // (|T_k| + |T_k+1|)/12 of the two star triangles sharing the edge; 1D: gaps g
 // give g/6 (x_left + 2 x_p) and g/6 (2 x_p + x_right)). Conjugate gradients
-// with the Jacobi preconditioner (diagonal v/2 in 2D, 2v/3 in 1D), from the
-// lumped start c/v, in one persistent cooperative kernel with the same
-// fixed-order FP64 reductions as the mesh solve. The vectors are interleaved
-// per particle, [np][FF] with FF = 2, 4 or 8 >= F, so that one row of M_p
-// gathers each neighbour's fields with one wide load; fields past F stay 0,
-// and a converged field is frozen by zero step lengths.
+// with the Jacobi preconditioner D (diagonal v/2 in 2D, 2v/3 in 1D), from the
+// lumped start c/v, in one persistent cooperative kernel with fixed-order
+// FP64 reductions. The vectors are interleaved per particle, [np][FF] with
+// FF = 2, 4 or 8 >= F, so that one row of M_p gathers each neighbour's fields
+// with one wide load; fields past F stay 0, and a converged field is frozen
+// by zero step lengths.
+//
+// Two passes and two grid barriers per iteration. The kernel keeps the
+// preconditioned residual z = D^-1 r instead of r (r = D z where the norms
+// need it). The pass that applies M_p forms the new search direction
+// p = z + beta p_prev at the row and at each neighbour it gathers (the same
+// FMA at every use, so every copy has the same bits), writes p into the
+// other of two direction buffers, and applies the previous iteration's
+// x += alpha p_prev at its own row. The second pass updates z. The last
+// x += alpha p is folded into the closing residual pass, which writes the
+// solution to q.
 // ---------------------------------------------------------------------------
 struct PCG {
     Geo g;
@@ -907,8 +945,9 @@ struct PCG {
     const uint2 *pos;
     const int *nbr;
     const unsigned char *deg;
-    const float *coef;  // [PM_MAXDEG][np] off-diagonal row coefficients (2D)
-    float *x, *r, *p, *q;  // [np][FF]
+    const float *coef;      // [PM_MAXDEG][np] off-diagonal row coefficients (2D)
+    float *x, *z, *q;       // [np][FF]: iterate, D^-1 r, M_p p (the solution at exit)
+    float *p[2];            // [np][FF]: search directions of even and odd iterations
     double *red, *scal;
     unsigned *bar;
     int *status;
@@ -953,9 +992,15 @@ __device__ __forceinline__ void stv(float *p, const VF<FF> &o) {
     }
 }
 
-// Row s of M_p applied to the interleaved vector xb (all FF fields).
-template <int DIM, int FF>
-__device__ __forceinline__ VF<FF> pmass_row(const PCG &a, const float *__restrict__ xb, ll s) {
+// Row s of M_p applied to the vector whose value at particle i is val(i),
+// all FF fields at once; xs = val(s), already at hand. In 2D the star is
+// walked two entries at a time, with the next pair's entries loaded while the
+// current pair's neighbours are gathered; the first pair is loaded together
+// with the degree (every row has PM_MAXDEG allocated slots, so these loads
+// stay in bounds; entries past the degree are never used). The sums keep the
+// order diagonal, slot 0, 1, ...
+template <int DIM, int FF, class Val>
+__device__ __forceinline__ VF<FF> pmass_row(const PCG &a, ll s, const VF<FF> &xs, Val val) {
     const ll np = a.np;
     KSum acc[FF];
     if (DIM == 1) {
@@ -963,7 +1008,7 @@ __device__ __forceinline__ VF<FF> pmass_row(const PCG &a, const float *__restric
         const ll sl = s == 0 ? np - 1 : s - 1, sr = s + 1 == np ? 0 : s + 1;
         const float u = a.unit * (1.0f / 6.0f);
         const float gl = (float)(uint32_t)(X - a.pos[sl].x) * u, gr = (float)(uint32_t)(a.pos[sr].x - X) * u;
-        const VF<FF> xl = ldv<FF>(xb + sl * FF), xs = ldv<FF>(xb + s * FF), xr = ldv<FF>(xb + sr * FF);
+        const VF<FF> xl = val(sl), xr = val(sr);
 #pragma unroll
         for (int f = 0; f < FF; ++f) {
             acc[f].add(gl * xl.v[f]);
@@ -971,18 +1016,43 @@ __device__ __forceinline__ VF<FF> pmass_row(const PCG &a, const float *__restric
             acc[f].add(gr * xr.v[f]);
         }
     } else {
+        int e0 = a.nbr[s], e1 = a.nbr[np + s];
+        float w0 = a.coef[s], w1 = a.coef[np + s];
         const int m = a.deg[s];
         const float d = 0.5f * a.vol[s];
-        const VF<FF> xs = ldv<FF>(xb + s * FF);
 #pragma unroll
         for (int f = 0; f < FF; ++f) acc[f].add(d * xs.v[f]);
-        for (int k = 0; k < m; ++k) {
-            const int id = a.nbr[(ll)k * np + s] & 0x0fffffff;
-            PM_CHK(id >= 0 && id < np, 402, break)
-            const float w = a.coef[(ll)k * np + s];
-            const VF<FF> xn = ldv<FF>(xb + (ll)id * FF);
+        for (int k = 0; k < m; k += 2) {
+            int n0 = 0, n1 = 0;
+            float u0 = 0.0f, u1 = 0.0f;
+            if (k + 2 < m) {
+                n0 = a.nbr[(ll)(k + 2) * np + s];
+                u0 = a.coef[(ll)(k + 2) * np + s];
+            }
+            if (k + 3 < m) {
+                n1 = a.nbr[(ll)(k + 3) * np + s];
+                u1 = a.coef[(ll)(k + 3) * np + s];
+            }
+            int i0 = e0 & 0x0fffffff;
+            PM_CHK(i0 < np, 402, i0 = (int)s)
+            const VF<FF> x0 = val(i0);
+            if (k + 1 < m) {
+                int i1 = e1 & 0x0fffffff;
+                PM_CHK(i1 < np, 402, i1 = (int)s)
+                const VF<FF> x1 = val(i1);
 #pragma unroll
-            for (int f = 0; f < FF; ++f) acc[f].add(w * xn.v[f]);
+                for (int f = 0; f < FF; ++f) {
+                    acc[f].add(w0 * x0.v[f]);
+                    acc[f].add(w1 * x1.v[f]);
+                }
+            } else {
+#pragma unroll
+                for (int f = 0; f < FF; ++f) acc[f].add(w0 * x0.v[f]);
+            }
+            e0 = n0;
+            e1 = n1;
+            w0 = u0;
+            w1 = u1;
         }
     }
     VF<FF> o;
@@ -1022,17 +1092,71 @@ __global__ void k_star_coef(ll np, const uint2 *__restrict__ pos, const int *__r
     coef[(ll)(m - 1) * np + s] = wprev + wfirst;           // edge (p, q_m-1): triangles m-1 and 0
 }
 
+
+// Block reduction of FF per-thread doubles (fields f < F) into
+// red[slot*F + f][block]; the same tree and order as block_partial.
+template <int FF>
+__device__ __forceinline__ void block_partial_v(const double (&v)[FF], int F, double *red, int slot) {
+    __shared__ double sh[FF][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int f = 0; f < FF; ++f) {
+        if (f >= F) break;
+        double s = v[f];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) sh[f][wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < F) {
+        double s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[threadIdx.x][w];
+        PM_CHK((ll)(slot * F + threadIdx.x + 1) * gridDim.x <= 6LL * PM_MAXF * 1024, 401, s = 0)
+        red[(ll)(slot * F + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// grid_total into a shared array: out[f] = sum over blocks of the partials
+// of (slot, f), the same order on every block. Ends with a block barrier.
+__device__ __forceinline__ void grid_total_sh(const double *red, int F, int slot, double *out) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (wid < F) {
+        const double *src = red + (ll)(slot * F + wid) * gridDim.x;
+        double s = 0;
+        for (unsigned i = lane; i < gridDim.x; i += 32) s += src[i];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) out[wid] = s;
+    }
+    __syncthreads();
+}
+
+// Per-field solver scalars, identical on every block (each block computes
+// them from the same totals); shared so that the row loops stay small.
+struct PcgState {
+    double cc[PM_MAXF], rz[PM_MAXF], sumc[PM_MAXF], sumabs[PM_MAXF], t0[PM_MAXF], t1[PM_MAXF];
+    float al[PM_MAXF], be[PM_MAXF];
+    int act[PM_MAXF], its[PM_MAXF];
+};
+
+// Compensated partials of the FF fields as doubles (fields past F give 0).
+template <int FF>
+__device__ __forceinline__ void dot_out(const Dot2 (&s)[FF], int F, double (&v)[FF]) {
+#pragma unroll
+    for (int f = 0; f < FF; ++f) v[f] = f < F ? (double)s[f].hi + (double)s[f].lo : 0.0;
+}
+
+// Reductions use slot groups {0,1,2}, {3,4}, then alternate {0} and {1,2}
+// inside the loop and {5,0} at the end: no two consecutive reductions share a
+// slot, so a block that runs ahead to the next reduction never overwrites a
+// partial that a slower block is still summing.
 template <int DIM, int FF>
-__global__ void __launch_bounds__(256) k_pcg(PCG a) {
+__global__ void __launch_bounds__(256, FF == 8 ? 2 : 4) k_pcg(PCG a) {
+    __shared__ PcgState S;
     const int F = a.F;
     const ll np = a.np;
     const ll tid = (ll)blockIdx.x * blockDim.x + threadIdx.x, nth = (ll)gridDim.x * blockDim.x;
     const float dfac = DIM == 2 ? 0.5f : 2.0f / 3.0f;  // Jacobi diagonal = dfac v
-    double v[PM_MAXF], w[PM_MAXF], cc[PM_MAXF], rz[PM_MAXF], ab[PM_MAXF];
-    bool act[PM_MAXF];
-    int it_f[PM_MAXF];
-    for (int f = 0; f < PM_MAXF; ++f) v[f] = w[f] = ab[f] = 0.0;
-    // --- lumped start x = c / v; norms and sums of c
+    // --- lumped start x = c / v; (c, c), sum c, sum |c|
     {
         Dot2 s2[FF], s1[FF], sa[FF];
         for (ll s = tid; s < np; s += nth) {
@@ -1048,176 +1172,201 @@ __global__ void __launch_bounds__(256) k_pcg(PCG a) {
             }
             stv<FF>(a.x + s * FF, xv);
         }
-#pragma unroll
-        for (int f = 0; f < FF; ++f)
-            if (f < F) {
-                v[f] = (double)s2[f].hi + (double)s2[f].lo;
-                w[f] = (double)s1[f].hi + (double)s1[f].lo;
-                ab[f] = (double)sa[f].hi + (double)sa[f].lo;
-            }
+        double v[FF];
+        dot_out<FF>(s2, F, v);
+        block_partial_v<FF>(v, F, a.red, 0);
+        dot_out<FF>(s1, F, v);
+        block_partial_v<FF>(v, F, a.red, 1);
+        dot_out<FF>(sa, F, v);
+        block_partial_v<FF>(v, F, a.red, 2);
     }
-    block_partial(v, F, a.red, 0);
-    block_partial(w, F, a.red, 1);
-    block_partial(ab, F, a.red, 2);
     if (!grid_sync(a.bar, a.status)) return;
-    double sumc[PM_MAXF], sumabs[PM_MAXF];
-    grid_total(a.red, F, 0, cc);
-    grid_total(a.red, F, 1, sumc);
-    grid_total(a.red, F, 2, sumabs);
-    // --- r = c - M x, z = r / d, p = z; (r, r), (r, z)
+    grid_total_sh(a.red, F, 0, S.cc);
+    grid_total_sh(a.red, F, 1, S.sumc);
+    grid_total_sh(a.red, F, 2, S.sumabs);
+    // --- r = c - M x, z = r / d; (r, r), (r, z)
     {
         Dot2 s2[FF], sz[FF];
         for (ll s = tid; s < np; s += nth) {
-            const VF<FF> mx = pmass_row<DIM, FF>(a, a.x, s);
+            const VF<FF> xs = ldv<FF>(a.x + s * FF);
+            const VF<FF> mx = pmass_row<DIM, FF>(a, s, xs, [&](ll i) { return ldv<FF>(a.x + i * FF); });
             const float d = dfac * a.vol[s];
-            VF<FF> rv, zv;
+            VF<FF> zv;
 #pragma unroll
             for (int f = 0; f < FF; ++f) {
-                rv.v[f] = (f < F ? a.c[(ll)f * np + s] : 0.0f) - mx.v[f];
-                zv.v[f] = d > 0.0f ? rv.v[f] / d : 0.0f;
-                s2[f].fma_acc(rv.v[f], rv.v[f]);
-                sz[f].fma_acc(rv.v[f], zv.v[f]);
+                const float rv = (f < F ? a.c[(ll)f * np + s] : 0.0f) - mx.v[f];
+                zv.v[f] = d > 0.0f ? rv / d : 0.0f;
+                s2[f].fma_acc(rv, rv);
+                sz[f].fma_acc(rv, zv.v[f]);
             }
-            stv<FF>(a.r + s * FF, rv);
-            stv<FF>(a.p + s * FF, zv);
+            stv<FF>(a.z + s * FF, zv);
         }
-#pragma unroll
-        for (int f = 0; f < FF; ++f)
-            if (f < F) {
-                v[f] = (double)s2[f].hi + (double)s2[f].lo;
-                w[f] = (double)sz[f].hi + (double)sz[f].lo;
-            }
+        double v[FF];
+        dot_out<FF>(s2, F, v);
+        block_partial_v<FF>(v, F, a.red, 3);
+        dot_out<FF>(sz, F, v);
+        block_partial_v<FF>(v, F, a.red, 4);
     }
-    block_partial(v, F, a.red, 0);
-    block_partial(w, F, a.red, 1);
     if (!grid_sync(a.bar, a.status)) return;
-    double rr[PM_MAXF];
-    grid_total(a.red, F, 0, rr);
-    grid_total(a.red, F, 1, rz);
+    grid_total_sh(a.red, F, 3, S.t0);
+    grid_total_sh(a.red, F, 4, S.rz);
     // The iteration stops on its recurrence for (r, r), which in FP32 drifts
     // from the true residual by a few roundings (observed: under 1 %); it
     // stops at 0.9 rtol so that the true residual, recomputed at exit, meets
     // rtol.
     const double tol2 = 0.81 * a.rtol * a.rtol;
-    for (int f = 0; f < F; ++f) {
-        act[f] = cc[f] > 0.0 && rr[f] > tol2 * cc[f];
-        it_f[f] = 0;
-        if (blockIdx.x == 0 && threadIdx.x == 0)
-            a.scal[f * 16 + S_INIT] = cc[f] > 0.0 ? sqrt(rr[f] / cc[f]) : 0.0;
-    }
+    if (threadIdx.x == 0)
+        for (int f = 0; f < F; ++f) {
+            S.act[f] = S.cc[f] > 0.0 && S.t0[f] > tol2 * S.cc[f];
+            S.its[f] = 0;
+            S.al[f] = 0.0f;
+            S.be[f] = 0.0f;
+            if (blockIdx.x == 0) a.scal[f * 16 + S_INIT] = S.cc[f] > 0.0 ? sqrt(S.t0[f] / S.cc[f]) : 0.0;
+        }
+    __syncthreads();
+    int last = -1;  // the last iteration run: its alpha p is still to be added to x
     for (int it = 0; it < a.max_iter; ++it) {
         bool any = false;
-        for (int f = 0; f < F; ++f) any |= act[f];
+        for (int f = 0; f < F; ++f) any |= S.act[f] != 0;
         if (!any) break;
-        // q = M p, (p, q)
-        {
-            Dot2 sq[FF];
-            for (ll i = tid; i < np; i += nth) {
-                const VF<FF> qv = pmass_row<DIM, FF>(a, a.p, i);
-                const VF<FF> pv = ldv<FF>(a.p + i * FF);
-                stv<FF>(a.q + i * FF, qv);
+        // p = z + beta p_prev (at the row and at each neighbour), q = M p,
+        // (p, q); x += alpha_prev p_prev at the row
+        const float *pin = a.p[(it + 1) & 1];
+        float *pout = a.p[it & 1];
+        float be[FF], ap[FF];
 #pragma unroll
-                for (int f = 0; f < FF; ++f) sq[f].fma_acc(pv.v[f], qv.v[f]);
-            }
-#pragma unroll
-            for (int f = 0; f < FF; ++f)
-                if (f < F) v[f] = (double)sq[f].hi + (double)sq[f].lo;
+        for (int f = 0; f < FF; ++f) {
+            be[f] = f < F ? S.be[f] : 0.0f;
+            ap[f] = f < F ? S.al[f] : 0.0f;
         }
-        block_partial(v, F, a.red, 0);
-        if (!grid_sync(a.bar, a.status)) return;
-        grid_total(a.red, F, 0, w);
-        // x += alpha p, r -= alpha q; (r, r), (r, z) with z = r / d. A
-        // converged field gets alpha = 0 (frozen).
-        float al[FF];
-#pragma unroll
-        for (int f = 0; f < FF; ++f) al[f] = (f < F && act[f]) ? (float)(rz[f] / w[f]) : 0.0f;
+        const bool first = it == 0;
         {
+            auto pval = [&](ll i) {
+                VF<FF> zv = ldv<FF>(a.z + i * FF);
+                if (!first) {
+                    const VF<FF> pv = ldv<FF>(pin + i * FF);
+#pragma unroll
+                    for (int f = 0; f < FF; ++f) zv.v[f] = fmaf(be[f], pv.v[f], zv.v[f]);
+                }
+                return zv;
+            };
+            Dot2 sq[FF];
+            for (ll s = tid; s < np; s += nth) {
+                VF<FF> ps = ldv<FF>(a.z + s * FF);
+                if (!first) {
+                    const VF<FF> pv = ldv<FF>(pin + s * FF);
+                    VF<FF> xv = ldv<FF>(a.x + s * FF);
+#pragma unroll
+                    for (int f = 0; f < FF; ++f) {
+                        ps.v[f] = fmaf(be[f], pv.v[f], ps.v[f]);
+                        xv.v[f] = fmaf(ap[f], pv.v[f], xv.v[f]);
+                    }
+                    stv<FF>(a.x + s * FF, xv);
+                }
+                const VF<FF> qv = pmass_row<DIM, FF>(a, s, ps, pval);
+                stv<FF>(pout + s * FF, ps);
+                stv<FF>(a.q + s * FF, qv);
+#pragma unroll
+                for (int f = 0; f < FF; ++f) sq[f].fma_acc(ps.v[f], qv.v[f]);
+            }
+            double v[FF];
+            dot_out<FF>(sq, F, v);
+            block_partial_v<FF>(v, F, a.red, 0);
+        }
+        if (!grid_sync(a.bar, a.status)) return;
+        grid_total_sh(a.red, F, 0, S.t0);
+        if (threadIdx.x == 0)
+            for (int f = 0; f < F; ++f) S.al[f] = S.act[f] ? (float)(S.rz[f] / S.t0[f]) : 0.0f;
+        __syncthreads();
+        last = it;
+        // z -= alpha q / d; (r, r) and (r, z) with r = d z
+        {
+            float al[FF];
+#pragma unroll
+            for (int f = 0; f < FF; ++f) al[f] = f < F ? S.al[f] : 0.0f;
             Dot2 s2[FF], sz[FF];
-            for (ll i = tid; i < np; i += nth) {
-                VF<FF> xv = ldv<FF>(a.x + i * FF), pv = ldv<FF>(a.p + i * FF);
-                VF<FF> qv = ldv<FF>(a.q + i * FF), rv = ldv<FF>(a.r + i * FF);
-                const float d = dfac * a.vol[i];
+            for (ll s = tid; s < np; s += nth) {
+                VF<FF> zv = ldv<FF>(a.z + s * FF);
+                const VF<FF> qv = ldv<FF>(a.q + s * FF);
+                const float d = dfac * a.vol[s];
 #pragma unroll
                 for (int f = 0; f < FF; ++f) {
-                    xv.v[f] = fmaf(al[f], pv.v[f], xv.v[f]);
-                    rv.v[f] = fmaf(-al[f], qv.v[f], rv.v[f]);
-                    const float zv = d > 0.0f ? rv.v[f] / d : 0.0f;
-                    s2[f].fma_acc(rv.v[f], rv.v[f]);
-                    sz[f].fma_acc(rv.v[f], zv);
+                    zv.v[f] = d > 0.0f ? fmaf(-al[f], qv.v[f] / d, zv.v[f]) : 0.0f;
+                    const float rv = d * zv.v[f];
+                    s2[f].fma_acc(rv, rv);
+                    sz[f].fma_acc(rv, zv.v[f]);
                 }
-                stv<FF>(a.x + i * FF, xv);
-                stv<FF>(a.r + i * FF, rv);
+                stv<FF>(a.z + s * FF, zv);
             }
-#pragma unroll
-            for (int f = 0; f < FF; ++f)
-                if (f < F) {
-                    v[f] = (double)s2[f].hi + (double)s2[f].lo;
-                    w[f] = (double)sz[f].hi + (double)sz[f].lo;
-                }
-        }
-        block_partial(v, F, a.red, 0);
-        block_partial(w, F, a.red, 1);
-        if (!grid_sync(a.bar, a.status)) return;
-        grid_total(a.red, F, 0, rr);
-        double rz_new[PM_MAXF];
-        grid_total(a.red, F, 1, rz_new);
-        float be[FF];
-#pragma unroll
-        for (int f = 0; f < FF; ++f) be[f] = 0.0f;
-        for (int f = 0; f < F; ++f) {
-            if (!act[f]) continue;
-            be[f] = (float)(rz_new[f] / rz[f]);
-            rz[f] = rz_new[f];
-            ++it_f[f];
-            if (rr[f] <= tol2 * cc[f]) act[f] = false;
-        }
-        // p = z + beta p
-        for (ll i = tid; i < np; i += nth) {
-            VF<FF> pv = ldv<FF>(a.p + i * FF);
-            const VF<FF> rv = ldv<FF>(a.r + i * FF);
-            const float d = dfac * a.vol[i];
-#pragma unroll
-            for (int f = 0; f < FF; ++f) pv.v[f] = fmaf(be[f], pv.v[f], d > 0.0f ? rv.v[f] / d : 0.0f);
-            stv<FF>(a.p + i * FF, pv);
+            double v[FF];
+            dot_out<FF>(s2, F, v);
+            block_partial_v<FF>(v, F, a.red, 1);
+            dot_out<FF>(sz, F, v);
+            block_partial_v<FF>(v, F, a.red, 2);
         }
         if (!grid_sync(a.bar, a.status)) return;
+        grid_total_sh(a.red, F, 1, S.t0);
+        grid_total_sh(a.red, F, 2, S.t1);
+        if (threadIdx.x == 0)
+            for (int f = 0; f < F; ++f) {
+                S.be[f] = 0.0f;
+                if (!S.act[f]) continue;
+                S.be[f] = (float)(S.t1[f] / S.rz[f]);
+                S.rz[f] = S.t1[f];
+                ++S.its[f];
+                if (S.t0[f] <= tol2 * S.cc[f]) S.act[f] = 0;
+            }
+        __syncthreads();
     }
-    // --- report: true residual, sum v x (= sum c for the exact solution)
+    // --- report: x += alpha p of the last iteration (at the row and at each
+    // neighbour), true residual c - M x, sum v x (= sum c for the exact
+    // solution); the solution goes to q
     {
+        float ap[FF];
+#pragma unroll
+        for (int f = 0; f < FF; ++f) ap[f] = (f < F && last >= 0) ? S.al[f] : 0.0f;
+        const float *pl = a.p[(last >= 0 ? last : 0) & 1];
+        const bool pend = last >= 0;
+        auto xval = [&](ll i) {
+            VF<FF> xv = ldv<FF>(a.x + i * FF);
+            if (pend) {
+                const VF<FF> pv = ldv<FF>(pl + i * FF);
+#pragma unroll
+                for (int f = 0; f < FF; ++f) xv.v[f] = fmaf(ap[f], pv.v[f], xv.v[f]);
+            }
+            return xv;
+        };
         Dot2 s2[FF], sv[FF];
         for (ll s = tid; s < np; s += nth) {
-            const VF<FF> mx = pmass_row<DIM, FF>(a, a.x, s);
-            const VF<FF> xv = ldv<FF>(a.x + s * FF);
+            const VF<FF> xs = xval(s);
+            const VF<FF> mx = pmass_row<DIM, FF>(a, s, xs, xval);
             const float vv = a.vol[s];
 #pragma unroll
             for (int f = 0; f < FF; ++f) {
                 const float rv = (f < F ? a.c[(ll)f * np + s] : 0.0f) - mx.v[f];
                 s2[f].fma_acc(rv, rv);
-                sv[f].fma_acc(vv, xv.v[f]);
+                sv[f].fma_acc(vv, xs.v[f]);
             }
+            stv<FF>(a.q + s * FF, xs);
         }
-#pragma unroll
-        for (int f = 0; f < FF; ++f)
-            if (f < F) {
-                v[f] = (double)s2[f].hi + (double)s2[f].lo;
-                w[f] = (double)sv[f].hi + (double)sv[f].lo;
-            }
+        double v[FF];
+        dot_out<FF>(s2, F, v);
+        block_partial_v<FF>(v, F, a.red, 5);
+        dot_out<FF>(sv, F, v);
+        block_partial_v<FF>(v, F, a.red, 0);
     }
-    block_partial(v, F, a.red, 0);
-    block_partial(w, F, a.red, 1);
     if (!grid_sync(a.bar, a.status)) return;
-    double tr[PM_MAXF], svx[PM_MAXF];
-    grid_total(a.red, F, 0, tr);
-    grid_total(a.red, F, 1, svx);
+    grid_total_sh(a.red, F, 5, S.t0);
+    grid_total_sh(a.red, F, 0, S.t1);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         bool bad = false;
         for (int f = 0; f < F; ++f) {
-            const double res = cc[f] > 0.0 ? sqrt(tr[f] / cc[f]) : 0.0;
-            a.scal[f * 16 + S_ITERS] = it_f[f];
+            const double res = S.cc[f] > 0.0 ? sqrt(S.t0[f] / S.cc[f]) : 0.0;
+            a.scal[f * 16 + S_ITERS] = S.its[f];
             a.scal[f * 16 + S_RESID] = res;
-            a.scal[f * 16 + S_SUMMESH] = sumc[f];   // int Ab = sum_mu c_mu
-            a.scal[f * 16 + S_SUMPART] = svx[f];    // sum_mu v_mu Abb_mu
-            a.scal[f * 16 + S_SUMABS] = sumabs[f];  // sum_mu |c_mu|: scale of the conservation error
+            a.scal[f * 16 + S_SUMMESH] = S.sumc[f];   // int Ab = sum_mu c_mu
+            a.scal[f * 16 + S_SUMPART] = S.t1[f];     // sum_mu v_mu Abb_mu
+            a.scal[f * 16 + S_SUMABS] = S.sumabs[f];  // sum_mu |c_mu|: scale of the conservation error
             if (res > a.rtol) bad = true;
         }
         if (bad) atomicOr(a.status, ST_NOTCONV);
@@ -1371,8 +1520,9 @@ int launch_pcg(const Geo &g, Work &w, ll np, int F, const float *c, float *out, 
     a.deg = w.deg;
     a.coef = w.pcoef;
     a.x = w.px;
-    a.r = w.prp;
-    a.p = w.prp + (ll)pcg_width(w.F_max) * w.np_max;
+    a.z = w.prp;
+    a.p[0] = w.prp + (ll)pcg_width(w.F_max) * w.np_max;
+    a.p[1] = w.pp2;
     a.q = w.pq;
     a.red = w.red;
     a.scal = w.scal;
@@ -1398,7 +1548,7 @@ int launch_pcg(const Geo &g, Work &w, ll np, int F, const float *c, float *out, 
     count_launches(1);
     if (e != cudaSuccess) return (int)e;
     if (np > 0) {
-        k_unsort_aos<<<div_up(np, 256), 256, 0, st>>>(np, F, FF, w.perm, w.px, out);
+        k_unsort_aos<<<div_up(np, 256), 256, 0, st>>>(np, F, FF, w.perm, w.pq, out);
         count_launches(1);
     }
     return 0;

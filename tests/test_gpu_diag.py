@@ -73,12 +73,14 @@ def test_mass_assignment_energies(built, dim, kind):
         assert info[f].energy_mesh == pytest.approx(em_or[f], rel=TOL)
 
 
-@pytest.mark.parametrize("dim", [1, 2])
-def test_full_mass_interpolation_energies(built, dim):
+@pytest.mark.parametrize("dim,fmax", [(1, 2), (2, 2), (2, 5)])
+def test_full_mass_interpolation_energies(built, dim, fmax):
+    """fmax = 5: a context sized for more fields than the call projects (the
+    solve's interleaved width follows the call's field count, 2, not 8)."""
     from paper_1610_05258_gb300 import Context
     n, L, px_h, py_h, _ = _case(dim, 92)
     mesh = W.mesh_field(dim, n, L, F=2, seed=5).astype(np.float32)
-    c = Context(dim, n, L, px_h.size, 2)
+    c = Context(dim, n, L, px_h.size, fmax)
     px, py, dm = to_dev(torch, px_h, py_h, mesh)
     out, info = c.interpolate_mass(dm, px, py)
     got = out.double().cpu().numpy()
