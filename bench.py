@@ -628,28 +628,34 @@ def run_chain(args, pm, torch, dist, local):
     mass = res["mass"]
 
     # ---- end to end: the step's inputs (positions and the mesh fields) from
-    # pinned host memory, its result (the mesh fields) back, every step
+    # pinned host memory, its results (the new mesh fields and the moved
+    # positions) back into host memory, every step. The next step starts from
+    # those host copies, so this chain passes through the same states as the
+    # device-resident one (same start, same number of steps).
     e2e = None
     if not args.no_e2e:
         hpx = px0.cpu().pin_memory()
         hpy = py0.cpu().pin_memory() if py0 is not None else None
-        hmesh = t(mesh0).cpu().pin_memory()
-        hout = torch.empty_like(hmesh).pin_memory()
+        hmesh = [t(mesh0).cpu().pin_memory(), torch.empty(F, nodes).pin_memory()]
         dpx = torch.empty_like(px0)
         dpy = torch.empty_like(py0) if py0 is not None else None
         dmesh, dout = torch.empty_like(mesh[0]), torch.empty_like(mesh[0])
-        bi = (hpx.numel() + (hpy.numel() if hpy is not None else 0) + hmesh.numel()) * 4
-        bo = hout.numel() * 4
+        bi = (hpx.numel() + (hpy.numel() if hpy is not None else 0) + hmesh[0].numel()) * 4
+        bo = bi
 
         def e2e_step():
             dpx.copy_(hpx, non_blocking=True)
             if dpy is not None:
                 dpy.copy_(hpy, non_blocking=True)
-            dmesh.copy_(hmesh, non_blocking=True)
+            dmesh.copy_(hmesh[0], non_blocking=True)
             ctx.interpolate(dmesh, dpx, dpy, out=vel)
             advect(dmesh, dpx, dpy, vel)
             ctx.assign_mass(dpx, dpy, vel, out=dout, info=False)
-            hout.copy_(dout, non_blocking=True)
+            hmesh[1].copy_(dout, non_blocking=True)
+            hpx.copy_(dpx, non_blocking=True)
+            if dpy is not None:
+                hpy.copy_(dpy, non_blocking=True)
+            hmesh.reverse()
 
         for _ in range(args.warmup):
             e2e_step()

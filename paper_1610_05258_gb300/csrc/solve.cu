@@ -1373,13 +1373,15 @@ __global__ void __launch_bounds__(256, FF == 8 ? 2 : 4) k_pcg(PCG a) {
     }
 }
 
-// Interleaved solution [np][FF] -> caller order [F][np].
-__global__ void k_unsort_aos(ll np, int F, int FF, const int *__restrict__ perm, const float *__restrict__ x,
+// Interleaved solution [np][FF] -> caller order [F][np], one field per grid
+// row: the rows run one after another, so the scattered writes of a row stay
+// within one field's array, which the L2 holds and merges before writing back.
+__global__ void k_unsort_aos(ll np, int FF, const int *__restrict__ perm, const float *__restrict__ x,
                              float *__restrict__ out) {
     const ll s = (ll)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= np) return;
-    const int k = perm[s];
-    for (int f = 0; f < F; ++f) out[(ll)f * np + k] = x[s * FF + f];
+    const int f = blockIdx.y;
+    out[(ll)f * np + perm[s]] = x[s * FF + f];
 }
 
 // Resident blocks of a persistent kernel: SMs x min(occupancy, cap), looked
@@ -1548,7 +1550,7 @@ int launch_pcg(const Geo &g, Work &w, ll np, int F, const float *c, float *out, 
     count_launches(1);
     if (e != cudaSuccess) return (int)e;
     if (np > 0) {
-        k_unsort_aos<<<div_up(np, 256), 256, 0, st>>>(np, F, FF, w.perm, w.pq, out);
+        k_unsort_aos<<<dim3((unsigned)div_up(np, 256), F), 256, 0, st>>>(np, FF, w.perm, w.pq, out);
         count_launches(1);
     }
     return 0;
