@@ -450,8 +450,12 @@ __device__ __forceinline__ bool owned_tri(int p, int m, int k, uint2 Xp, float u
     rel_of(nbr[(ll)(k == 0 ? m - 1 : k - 1) * np + p], Xp, pos, T.a, ax, ay);
     rel_of(nbr[(ll)k * np + p], Xp, pos, T.b, bx, by);
     if (T.a <= p || T.b <= p) return false;
-    T.vx[0] = up; T.vx[1] = up + (float)ax * sc; T.vx[2] = up + (float)bx * sc;
-    T.vy[0] = wp; T.vy[1] = wp + (float)ay * sc; T.vy[2] = wp + (float)by * sc;
+    // One explicit rounding (FMA) per coordinate: the piece counting and the
+    // piece integration call this separately and must get the same bits, also
+    // when a vertex lies exactly on a cell line (the bounding box below);
+    // left to the compiler, the two inlined copies may round differently.
+    T.vx[0] = up; T.vx[1] = __fmaf_rn((float)ax, sc, up); T.vx[2] = __fmaf_rn((float)bx, sc, up);
+    T.vy[0] = wp; T.vy[1] = __fmaf_rn((float)ay, sc, wp); T.vy[2] = __fmaf_rn((float)by, sc, wp);
     T.i0 = (int)floorf(fminf(T.vx[0], fminf(T.vx[1], T.vx[2])));
     T.i1 = (int)floorf(fmaxf(T.vx[0], fmaxf(T.vx[1], T.vx[2])));
     T.j0 = (int)floorf(fminf(T.vy[0], fminf(T.vy[1], T.vy[2])));

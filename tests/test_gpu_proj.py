@@ -114,3 +114,33 @@ def test_projection_errors(built):
     assert e.value.status == 3
     out, info = c.interpolate_mass(m, px, py)  # usable afterwards
     assert info[0].rel_resid <= 1e-6
+
+
+@pytest.mark.parametrize("dim,F", [(2, 1), (2, 3), (2, 4), (2, 6), (2, 8), (1, 4), (1, 7)])
+def test_interpolate_mass_field_counts(built, dim, F):
+    """Every interleave width of the particle solve (2, 4 and 8 fields per
+    particle record, fields past F padded), in a context sized for 8 fields:
+    parity, residual and conservation per field; a field of zeros stays
+    zero."""
+    from paper_1610_05258_gb300 import Context
+    inst = W.uniform_instance(29, 4, F=1, seed=300 + F) if dim == 2 else W.tophat_1d(157, 389, seed=300 + F)
+    mesh = W.mesh_field(dim, inst.n, inst.L, F=F, seed=40 + F, kind="noise").astype(np.float32)
+    if F > 2:
+        mesh[1] = 0.0
+    c = Context(dim, inst.n, inst.L, inst.np, 8)
+    dm, px = to_dev(torch, mesh, inst.px)
+    py = to_dev(torch, inst.py)[0] if dim == 2 else None
+    got, info = c.interpolate_mass(dm, px, py, rtol=1e-6)
+    got = got.cpu().numpy()
+    want = oracle.interpolate_mass(dim, inst.n, inst.L, mesh, inst.px, inst.py)
+    for f in range(F):
+        if not mesh[f].any():
+            assert not got[f].any(), f
+            continue
+        assert rel_l2(got[f], want[f]) <= TOL, (f, rel_l2(got[f], want[f]))
+        assert info[f].rel_resid <= 1e-6 and info[f].cons_err <= 1e-6
+    back = c.interpolate(dm, px, py).cpu().numpy()
+    want_d = oracle.interpolate(dim, inst.n, inst.L, mesh, inst.px, inst.py)
+    for f in range(F):
+        if mesh[f].any():
+            assert rel_l2(back[f], want_d[f]) <= TOL, f
