@@ -196,6 +196,24 @@ pm_status pm_assign_pic(pm_ctx *ctx, const float *px, const float *py, long long
 pm_status pm_assign_mass(pm_ctx *ctx, const float *px, const float *py, long long np, const float *vals, int F,
                          float *mesh_out, const pm_solve_opts *opts, pm_solve_info *info);
 
+/* pm_assign_mass with the particles and the result in HOST memory (same
+ * method, same arithmetic, the same result bit for bit). px, py [np] and
+ * vals [F][np] are read from host memory, mesh_out [F][n^dim] is written to
+ * host memory. The positions are uploaded first, on the context's stream;
+ * the values on a second stream of the context, while the sort and the
+ * particle functions (which do not need them) run; the value gather waits for
+ * them. Page-locked host buffers (cudaHostAlloc / cudaHostRegister) let the
+ * uploads overlap the kernels; pageable ones work but copy synchronously.
+ * The context holds device copies of the inputs and output at its maximum
+ * sizes, allocated by its first host-buffer call (PM_ENOMEM if that fails);
+ * later calls allocate nothing. Asynchronous like pm_assign_mass: mesh_out is
+ * valid once the context's stream has completed (pm_sync), or on return when
+ * info is given. The warm start PM_WS_USER (a device x0) is rejected with
+ * PM_EINVAL; everything else as pm_assign_mass. No counterpart in the paper:
+ * host-side data handling around Sec. 2.4. */
+pm_status pm_assign_mass_host(pm_ctx *ctx, const float *px, const float *py, long long np, const float *vals, int F,
+                              float *mesh_out, const pm_solve_opts *opts, pm_solve_info *info);
+
 /* Lumped assignment (Table 1, "lumped" row; Sec. 2.4 remarks, Eq. lumped
  * with v_i = sum_j m_ij = h^dim):  mesh_out[f][i] = int A_f psi_i / h^dim,
  * the exact right-hand side of the mass assignment divided by the node

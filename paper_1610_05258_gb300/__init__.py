@@ -31,7 +31,7 @@ _STATUS = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ENOTCONV", 4: "PM_
 
 EXPORTS = [
     "pm_ctx_create", "pm_ctx_create_mesh", "pm_ctx_destroy", "pm_ctx_set_stream", "pm_sync", "pm_last_error", "pm_ctx_workspace_bytes",
-    "pm_interpolate", "pm_interpolate_lumped", "pm_interpolate_mass", "pm_assign_lumped", "pm_assign_delta", "pm_assign_flip", "pm_assign_mass", "pm_mass_rhs", "pm_mass_rhs_mode", "pm_mass_apply",
+    "pm_interpolate", "pm_interpolate_lumped", "pm_interpolate_mass", "pm_assign_lumped", "pm_assign_delta", "pm_assign_flip", "pm_assign_mass", "pm_assign_mass_host", "pm_mass_rhs", "pm_mass_rhs_mode", "pm_mass_apply",
     "pm_mass_solve", "pm_particle_volumes", "pm_triangulate", "pm_sort", "pm_advect_shift", "pm_advect_rotate",
     "pm_advect_rk2", "pm_profile", "pm_profile_read", "pm_work_read", "pm_phase_name", "pm_kernel_launches",
     "pm_batch_create", "pm_batch_destroy", "pm_batch_last_error", "pm_batch_tuning", "pm_batch_assign_mass",
@@ -108,6 +108,7 @@ def load_library(path: str | None = None):
         "pm_assign_flip": [vp, vp, vp, ll, vp, i, vp, vp, ctypes.POINTER(ll)],
         "pm_assign_pic": [vp, vp, vp, ll, vp, i, vp],
         "pm_assign_mass": [vp, vp, vp, ll, vp, i, vp, ctypes.POINTER(_Opts), vp],
+        "pm_assign_mass_host": [vp, vp, vp, ll, vp, i, vp, ctypes.POINTER(_Opts), vp],
         "pm_mass_rhs": [vp, vp, vp, ll, vp, i, vp],
         "pm_mass_rhs_mode": [vp, vp, vp, ll, vp, i, i, vp],
         "pm_mass_apply": [vp, vp, i, vp],
@@ -320,6 +321,33 @@ class Context:
             return out
         return out, [_info(x)
                      for x in inf]
+
+    def assign_mass_host(self, px, py, vals, out=None, warm_start="delta", rtol=1e-6, max_iter=200, info=True,
+                         net=None, rhs="exact", solver="cg"):
+        """Mass assignment from CPU tensors into a CPU tensor (pm_assign_mass_host):
+        pinned tensors let the uploads overlap the kernels. Without info the
+        result is valid after the context's stream completes (sync())."""
+        def host(t):
+            if t is None:
+                return None
+            if t.is_cuda or t.dtype != self.torch.float32 or not t.is_contiguous():
+                raise TypeError("expected a contiguous float32 CPU tensor")
+            return t
+        px, py, vals = host(px), host(py), host(vals)
+        F = vals.numel() // max(1, px.numel())
+        out = out if out is not None else self.torch.empty(F, self.nodes, dtype=self.torch.float32).pin_memory()
+        host(out)
+        if net is not None:
+            warm_start = "net"
+        o = self._opts(warm_start, rtol, max_iter, None, net, rhs, solver)
+        inf = (_Info * F)() if info else None
+        self._stream()
+        s = self.lib.pm_assign_mass_host(self.h, _ptr(px), _ptr(py), px.numel(), _ptr(vals), F, _ptr(out),
+                                         ctypes.byref(o), inf)
+        self._check(s)
+        if not info:
+            return out
+        return out, [_info(x) for x in inf]
 
     def net_features(self, px, py, vals):
         """(delta [F, n^2], features [F, 2, n^2], max|A_f| list) for the network."""

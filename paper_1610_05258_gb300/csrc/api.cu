@@ -32,6 +32,11 @@ struct pm_ctx {
     size_t nev = 0;
     double acc_ms[PM_NPHASE] = {0};
     ll acc_calls[PM_NPHASE] = {0};
+    // host-buffer mass assignment: device copies of the inputs and output,
+    // the stream that uploads the values and its events (made on first use)
+    float *hx = nullptr, *hy = nullptr, *hv = nullptr, *hout = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_vals = nullptr;
 };
 
 namespace {
@@ -250,6 +255,11 @@ void pm_ctx_destroy(pm_ctx *c) {
         if (p) cudaFree(p);
     if (w.hstatus) cudaFreeHost(w.hstatus);
     if (w.hres) cudaFreeHost(w.hres);
+    for (float *p : {c->hx, c->hy, c->hv, c->hout})
+        if (p) cudaFree(p);
+    if (c->ev_start) cudaEventDestroy(c->ev_start);
+    if (c->ev_vals) cudaEventDestroy(c->ev_vals);
+    if (c->side) cudaStreamDestroy(c->side);
     for (auto &e : c->ev) {
         cudaEventDestroy(e.a);
         cudaEventDestroy(e.b);
@@ -383,10 +393,21 @@ static pm_status report(pm_ctx *c, int F, pm_solve_info *info, const float *mesh
 
 // Everything of a mass assignment before the solve: sort, particle
 // functions, particle sums, right-hand side and the warm start.
+// vals_ready (may be NULL): the values are still arriving, and become
+// readable on the context's stream once that event completes. The sort and
+// the particle functions run without them, and their gather waits for it.
 static pm_status mass_front(pm_ctx *c, const float *px, const float *py, ll np, const float *vals, int F,
-                            float *mesh_out, const pm_solve_opts &o, bool &start) {
+                            float *mesh_out, const pm_solve_opts &o, bool &start, cudaEvent_t vals_ready = nullptr) {
     pm_status s;
-    if ((s = prepare(c, px, py, np, vals, F, true))) return s;
+    if (vals_ready) {
+        if ((s = prepare(c, px, py, np, nullptr, 0, true))) return s;
+        Phase ph(c, PM_PH_SORT);
+        cudaStreamWaitEvent(c->st, vals_ready, 0);
+        launch_gather_vals(c->w, np, vals, F, c->st);
+        if ((s = check_launch(c, "value gather"))) return s;
+    } else if ((s = prepare(c, px, py, np, vals, F, true))) {
+        return s;
+    }
     {
         Phase ph(c, PM_PH_RHS);
         launch_psum(c->g, c->w, np, F, c->st);
@@ -461,12 +482,11 @@ static pm_status mass_solve_launch(pm_ctx *c, int F, float *mesh_out, bool start
     return check_launch(c, "solve");
 }
 
-pm_status pm_assign_mass(pm_ctx *c, const float *px, const float *py, long long np, const float *vals, int F,
-                         float *mesh_out, const pm_solve_opts *opts, pm_solve_info *info) {
+static pm_status mass_args(pm_ctx *c, const float *px, const float *py, ll np, const float *vals, int F,
+                           float *mesh_out, const pm_solve_opts *opts, pm_solve_opts &o) {
     pm_status s = check_particles(c, px, py, np, F, vals, c && c->g.dim == 2 ? 3 : 2);
     if (s) return s;
     if (F < 1 || !mesh_out) return fail(c, PM_EINVAL, "null output or no field");
-    pm_solve_opts o;
     default_opts(opts, o);
     if (o.warm_start < PM_WS_DELTA || o.warm_start > PM_WS_DIRECT) return fail(c, PM_EINVAL, "unknown warm start");
     if (o.rhs_mode != PM_RHS_EXACT && o.rhs_mode != PM_RHS_APPB) return fail(c, PM_EINVAL, "unknown rhs_mode");
@@ -475,10 +495,66 @@ pm_status pm_assign_mass(pm_ctx *c, const float *px, const float *py, long long 
         return fail(c, PM_EINVAL, "PM_RHS_APPB and PM_WS_DIRECT need the bilinear mesh");
     if (o.warm_start == PM_WS_USER && !o.x0) return fail(c, PM_EINVAL, "PM_WS_USER without x0");
     if (o.warm_start == PM_WS_NET && (!o.net || !c->w.feat)) return fail(c, PM_EINVAL, "PM_WS_NET needs a network and a 2D bilinear mesh with n % 128 == 0");
+    return PM_OK;
+}
+
+pm_status pm_assign_mass(pm_ctx *c, const float *px, const float *py, long long np, const float *vals, int F,
+                         float *mesh_out, const pm_solve_opts *opts, pm_solve_info *info) {
+    pm_solve_opts o;
+    pm_status s = mass_args(c, px, py, np, vals, F, mesh_out, opts, o);
+    if (s) return s;
     bool start = true;
     if ((s = mass_front(c, px, py, np, vals, F, mesh_out, o, start))) return s;
     if ((s = mass_solve_launch(c, F, mesh_out, start, o))) return s;
     if (info) return report(c, F, info, mesh_out, np, c->w.vals, np, 1);
+    return PM_OK;
+}
+
+// Device copies for the host-buffer call: inputs at the context's maximum
+// sizes, one mesh-sized output, the upload stream and its events.
+static pm_status host_staging(pm_ctx *c) {
+    if (c->hx) return PM_OK;
+    Work &w = c->w;
+    const ll np = w.np_max, F = w.F_max;
+    bool ok = alloc(c, &c->hx, np) && (c->g.dim == 1 || alloc(c, &c->hy, np)) && alloc(c, &c->hv, F * np) &&
+              alloc(c, &c->hout, F * c->g.ncell);
+    ok = ok && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->ev_vals, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return fail(c, PM_ENOMEM, "host-buffer staging: allocation failed");
+    }
+    return PM_OK;
+}
+
+pm_status pm_assign_mass_host(pm_ctx *c, const float *px, const float *py, long long np, const float *vals, int F,
+                              float *mesh_out, const pm_solve_opts *opts, pm_solve_info *info) {
+    pm_solve_opts o;
+    pm_status s = mass_args(c, px, py, np, vals, F, mesh_out, opts, o);
+    if (s) return s;
+    if (o.warm_start == PM_WS_USER) return fail(c, PM_EINVAL, "PM_WS_USER takes a device x0: use pm_assign_mass");
+    if ((s = host_staging(c))) return s;
+    const size_t pb = sizeof(float) * (size_t)np;
+    // Positions first, on the context's stream. The values follow on the side
+    // stream once the positions are up (copies share the copy engine, so
+    // queued first they would hold the positions back) and everything queued
+    // before on the context's stream is done (an earlier call may still be
+    // reading them); the sort and the particle functions run meanwhile.
+    cudaMemcpyAsync(c->hx, px, pb, cudaMemcpyHostToDevice, c->st);
+    if (c->g.dim == 2) cudaMemcpyAsync(c->hy, py, pb, cudaMemcpyHostToDevice, c->st);
+    cudaEventRecord(c->ev_start, c->st);
+    cudaStreamWaitEvent(c->side, c->ev_start, 0);
+    cudaMemcpyAsync(c->hv, vals, pb * F, cudaMemcpyHostToDevice, c->side);
+    cudaEventRecord(c->ev_vals, c->side);
+    if ((s = check_launch(c, "host-buffer uploads"))) return s;
+    bool start = true;
+    if ((s = mass_front(c, c->hx, c->g.dim == 2 ? c->hy : nullptr, np, c->hv, F, c->hout, o, start, c->ev_vals)))
+        return s;
+    if ((s = mass_solve_launch(c, F, c->hout, start, o))) return s;
+    cudaMemcpyAsync(mesh_out, c->hout, sizeof(float) * F * (size_t)c->g.ncell, cudaMemcpyDeviceToHost, c->st);
+    if ((s = check_launch(c, "host-buffer download"))) return s;
+    if (info) return report(c, F, info, c->hout, np, c->w.vals, np, 1);
     return PM_OK;
 }
 

@@ -354,6 +354,9 @@ void count_launches(int k);
 // Launchers (one per translation unit, all asynchronous on `st`).
 void launch_sort(const Geo &g, Work &w, const float *px, const float *py, ll np, const float *vals, int F,
                  cudaStream_t st);
+// The field rows of the sort's gather alone, for a sort launched with vals =
+// NULL (positions and cell order only): sorted values and max|A| per field.
+void launch_gather_vals(Work &w, ll np, const float *vals, int F, cudaStream_t st);
 // G2P; il is workspace for the mesh fields interleaved per node
 // ([n^dim][g2p_width(F)] floats, unused for F = 1).
 int g2p_width(int F);

@@ -147,23 +147,27 @@ __global__ void k_canon(Geo g, ll np, const int *__restrict__ cell_start, int *_
 // particles is 67 MB), instead of spreading over all arrays at once. Each
 // field's row tracks max |A| of that field.
 #define GATHER_BLK 256
+// row0 = 1 gathers the fields only (grid rows 0..F-1 take rows 1..F), after a
+// sort that gathered the positions alone.
 __global__ void __launch_bounds__(GATHER_BLK) k_gather(ll np, const int *__restrict__ tmp, const uint2 *__restrict__ fx,
                          const float *__restrict__ vals, int *__restrict__ perm, uint2 *__restrict__ pos,
-                         float *__restrict__ vals_s, unsigned *__restrict__ maxabs, int *__restrict__ status) {
+                         float *__restrict__ vals_s, unsigned *__restrict__ maxabs, int *__restrict__ status,
+                         int row0) {
     const ll s = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = (int)blockIdx.y + row0;
     int idx = -1;
     if (s < np) {
         idx = tmp[s];
         PM_CHK(idx >= 0 && idx < np, 105, idx = -1)
     }
-    if (blockIdx.y == 0) {
+    if (row == 0) {
         if (idx >= 0) {
             perm[s] = idx;
             pos[s] = __ldg(fx + idx);
         }
         return;
     }
-    const int f = blockIdx.y - 1;
+    const int f = row - 1;
     float mx = 0.0f;
     bool bad = false;
     if (idx >= 0) {
@@ -292,7 +296,16 @@ void launch_sort(const Geo &g, Work &w, const float *px, const float *py, ll np,
     if (np > 0) {
         k_canon<<<div_up(g.ncell, 128), 128, 0, st>>>(g, np, w.cell_start, w.tmp, w.fx);
         const dim3 grid((unsigned)div_up(np, GATHER_BLK), 1 + (vals ? F : 0));
-        k_gather<<<grid, GATHER_BLK, 0, st>>>(np, w.tmp, w.fx, vals, w.perm, w.pos, w.vals, w.maxabs, w.status);
+        k_gather<<<grid, GATHER_BLK, 0, st>>>(np, w.tmp, w.fx, vals, w.perm, w.pos, w.vals, w.maxabs, w.status, 0);
     }
     count_launches(np > 0 ? 7 : 3);
+}
+
+void launch_gather_vals(Work &w, ll np, const float *vals, int F, cudaStream_t st) {
+    if (np <= 0 || F <= 0) return;
+    const dim3 grid((unsigned)div_up(np, GATHER_BLK), F);
+    // caller indices from w.perm (row 0 copied them there; w.tmp may have been
+    // reused since, e.g. as the triangulation's retry list)
+    k_gather<<<grid, GATHER_BLK, 0, st>>>(np, w.perm, w.fx, vals, w.perm, w.pos, w.vals, w.maxabs, w.status, 1);
+    count_launches(1);
 }
