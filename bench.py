@@ -323,9 +323,9 @@ DELAUNAY_OP_WEIGHTS = {"candidates": 10, "tested": 5, "vertex_tests": 5, "clips"
 ALU_LANES = 152 * 128
 # DRAM traffic of one k_delaunay launch per particle: dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture on the 1024^2 mixture (4,194,304
-# particles: 100.62 MB read + 100.76 MB written), scaled to a launch by its
+# particles: 100.11 MB read + 106.89 MB written), scaled to a launch by its
 # particle count (the kernel's traffic grows in proportion to it).
-DELAUNAY_DRAM_BYTES_PER_PARTICLE = (100.624128e6 + 100.764928e6) / 4194304
+DELAUNAY_DRAM_BYTES_PER_PARTICLE = (100.109568e6 + 106.889216e6) / 4194304
 
 
 def alu_roofline(kernel, counts, ms, sm_mhz, n_particles):

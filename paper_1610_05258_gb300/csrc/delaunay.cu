@@ -163,15 +163,33 @@ __device__ __forceinline__ int clip_by(PolyS<NB> P, int &m, float &R2, int sx, i
     unsigned mask = 0, undecided = 0;
     float rkeep = 0.0f;
     const int t = P.t;
+    if (CAP <= 12) {
+        // CAP predicated iterations on every lane: no loop exit that depends
+        // on the lane's own cell size (lanes of a warp hold cells of
+        // different sizes). Entries past m are stale but in bounds, and are
+        // masked out.
+#pragma unroll
+        for (int k = 0; k < CAP; ++k) {
+            const bool live = k < m;
+            const float4 c = P.v[k][t];
+            const float hk = c.x * fsx + c.y * fsy - hs;
+            const float mg = c.z * ns + mr;
+            const bool in = live && hk > mg, out = hk < -mg;  // NaN: neither
+            mask |= (in ? 1u : 0u) << k;
+            undecided |= (live && !in && !out ? 1u : 0u) << k;
+            rkeep = (in || !live) ? rkeep : fmaxf(rkeep, c.w);
+        }
+    } else {
 #pragma unroll 4
-    for (int k = 0; k < m; ++k) {
-        const float4 c = P.v[k][t];
-        const float hk = c.x * fsx + c.y * fsy - hs;
-        const float mg = c.z * ns + mr;
-        const bool in = hk > mg, out = hk < -mg;  // both false also when hk or mg is NaN
-        mask |= (in ? 1u : 0u) << k;
-        undecided |= (!in && !out ? 1u : 0u) << k;
-        rkeep = in ? rkeep : fmaxf(rkeep, c.w);
+        for (int k = 0; k < m; ++k) {
+            const float4 c = P.v[k][t];
+            const float hk = c.x * fsx + c.y * fsy - hs;
+            const float mg = c.z * ns + mr;
+            const bool in = hk > mg, out = hk < -mg;  // both false also when hk or mg is NaN
+            mask |= (in ? 1u : 0u) << k;
+            undecided |= (!in && !out ? 1u : 0u) << k;
+            rkeep = in ? rkeep : fmaxf(rkeep, c.w);
+        }
     }
     if (undecided) {
         if (COUNT) wc.exact += __popc(undecided);
