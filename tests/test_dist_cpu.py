@@ -102,5 +102,5 @@ def test_alu_roofline_arithmetic():
     assert r["achieved"] == pytest.approx(80e9 / 1e-2 / 1e12)
     assert r["peak"] == pytest.approx(152 * 128 * 2000e6 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
-    assert r["traffic"] == pytest.approx(100.624128e6 + 100.764928e6)
+    assert r["traffic"] == pytest.approx(100.109568e6 + 106.889216e6)  # the 1024^2 capture's DRAM bytes
     assert bench.alu_roofline("k", counts, 10.0, 2000.0, 2 * 4194304)["traffic"] == pytest.approx(2 * r["traffic"])
