@@ -490,12 +490,15 @@ def run_mixture(args, pm, torch, dist, local):
     proj = {}
     for name, fn in (("full_mass", lambda: ctx.interpolate_mass(mesh_fields, px, py, out=back, info=False)),
                      ("lumped", lambda: ctx.interpolate_lumped(mesh_fields, px, py, out=back)),
-                     ("delta", lambda: ctx.interpolate(mesh_fields, px, py, out=back))):
+                     ("delta", lambda: ctx.interpolate(mesh_fields, px, py, out=back)),
+                     # the same particles, already sorted by the calls above: results in sorted order
+                     ("delta_sorted", lambda: ctx.interpolate_sorted(mesh_fields, N, out=back))):
         t, _, phases = timed_arm(ctx, torch, stream, flush, args, dist, dev, fn, pm)
         proj[name] = {"ms_per_step": t, "value": args.world * N * F / (t * 1e-3),
                       "phase_ms_per_step": {k: round(v, 4) for k, v in phases.items()}}
     proj["full_mass"]["solve"] = solve_report(pinfo)
     g2p_ms = proj["delta"]["ms_per_step"]
+    g2p_sorted_ms = proj["delta_sorted"]["ms_per_step"]
     # one untimed pass of the counting build of the triangulation
     ctx.profile(True, count_work=True)
     ctx.assign_mass(px, py, vals, out=out, info=False)
@@ -510,6 +513,9 @@ def run_mixture(args, pm, torch, dist, local):
     roof["hbm_minimal_io"] = {"bytes_per_step": minimal, "achieved_gbs": minimal / (plain["ms"] * 1e-3) / 1e9,
                               "peak_gbs": hbm, "frac": minimal / (plain["ms"] * 1e-3) / 1e9 / hbm}
     rooflines = [hbm_roofline("k_interleave + k_g2p (mesh -> particle, Eq. delta2)", g2p_bytes(N, n * n, F), g2p_ms,
+                              "8 B position + 4F B values per particle, 4F B per node"),
+                 hbm_roofline("k_interleave + k_g2p_sorted (Eq. delta2 at the sorted particles, sorted results)",
+                              g2p_bytes(N, n * n, F), g2p_sorted_ms,
                               "8 B position + 4F B values per particle, 4F B per node")]
 
     cpu = cpu_baseline("mixture", 10.0, pm, torch, dev) if (args.rank == 0 and not args.no_cpu) else None
@@ -546,7 +552,9 @@ def run_mixture(args, pm, torch, dist, local):
                  "what": "the same step with P1 mesh functions on cells split by the (0,0)-(1,1) diagonal "
                          "(7-point mass stencil) instead of bilinear ones"},
         mesh_to_particle={"what": "the step's mesh fields projected back onto the same particles; each entry is "
-                                  "one call per step (full mass includes the sort and triangulation)", **proj},
+                                  "one call per step (full mass includes the sort and triangulation; delta_sorted "
+                                  "interpolates at the particles the previous calls sorted, results in sorted order)",
+                          **proj},
         roofline=roof, rooflines=rooflines, cpu_baseline=cpu, e2e=e2e, gpu_launches=plain["launches"], clocks=ck)
     finish(args, dist, line)
 

@@ -158,6 +158,22 @@ long long pm_ctx_workspace_bytes(const pm_ctx *ctx);
 pm_status pm_interpolate(pm_ctx *ctx, const float *mesh, int F, const float *px, const float *py, long long np,
                          float *out);
 
+/* Delta interpolation (Eq. delta2, as pm_interpolate) at the particles of the
+ * context's most recent sort, with the results in that sorted order: out
+ * [F][np], slot s holding the value at caller particle perm[s] (the
+ * permutation pm_sort returns: cell-major, then caller index). The same bits
+ * as pm_interpolate gives for that particle. The particles are those of the
+ * last call that sorted: pm_sort, pm_particle_volumes, pm_triangulate and
+ * every assignment, right-hand side and mesh -> particle projection other
+ * than pm_interpolate, on this context; their positions are not read again.
+ * np must equal that call's particle count (PM_EINVAL otherwise, and when no
+ * call has sorted yet). In sorted order a warp's particles share a few cells,
+ * so their corner reads mostly hit in L1: use it where the caller's particles
+ * stay put between the assignment and the interpolation and sorted results
+ * serve (or are reordered once with the permutation). Asynchronous. No
+ * counterpart in the paper: a data-layout variant of Eq. delta2. */
+pm_status pm_interpolate_sorted(pm_ctx *ctx, const float *mesh, int F, long long np, float *out);
+
 /* delta assignment, Sec. 2.2 Eq. delta:  mesh_out[f][i] = A_f(r_i) =
  * sum_mu vals[f][mu] psi_mu(r_i).  Needs np >= 2 (1D) / np >= 3 (2D).
  * Asynchronous. */

@@ -31,7 +31,7 @@ _STATUS = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ENOTCONV", 4: "PM_
 
 EXPORTS = [
     "pm_ctx_create", "pm_ctx_create_mesh", "pm_ctx_destroy", "pm_ctx_set_stream", "pm_sync", "pm_last_error", "pm_ctx_workspace_bytes",
-    "pm_interpolate", "pm_interpolate_lumped", "pm_interpolate_mass", "pm_assign_lumped", "pm_assign_delta", "pm_assign_flip", "pm_assign_mass", "pm_assign_mass_host", "pm_mass_rhs", "pm_mass_rhs_mode", "pm_mass_apply",
+    "pm_interpolate", "pm_interpolate_sorted", "pm_interpolate_lumped", "pm_interpolate_mass", "pm_assign_lumped", "pm_assign_delta", "pm_assign_flip", "pm_assign_mass", "pm_assign_mass_host", "pm_mass_rhs", "pm_mass_rhs_mode", "pm_mass_apply",
     "pm_mass_solve", "pm_particle_volumes", "pm_triangulate", "pm_sort", "pm_advect_shift", "pm_advect_rotate",
     "pm_advect_rk2", "pm_profile", "pm_profile_read", "pm_work_read", "pm_phase_name", "pm_kernel_launches",
     "pm_batch_create", "pm_batch_destroy", "pm_batch_last_error", "pm_batch_tuning", "pm_batch_assign_mass",
@@ -109,6 +109,7 @@ def load_library(path: str | None = None):
         "pm_assign_pic": [vp, vp, vp, ll, vp, i, vp],
         "pm_assign_mass": [vp, vp, vp, ll, vp, i, vp, ctypes.POINTER(_Opts), vp],
         "pm_assign_mass_host": [vp, vp, vp, ll, vp, i, vp, ctypes.POINTER(_Opts), vp],
+        "pm_interpolate_sorted": [vp, vp, i, ll, vp],
         "pm_mass_rhs": [vp, vp, vp, ll, vp, i, vp],
         "pm_mass_rhs_mode": [vp, vp, vp, ll, vp, i, i, vp],
         "pm_mass_apply": [vp, vp, i, vp],
@@ -243,6 +244,16 @@ class Context:
         out = out if out is not None else self._empty(F, px.numel())
         self._stream()
         self._check(self.lib.pm_interpolate_lumped(self.h, _ptr(mesh), F, _ptr(px), _ptr(py), px.numel(), _ptr(out)))
+        return out
+
+    def interpolate_sorted(self, mesh, np_, out=None):
+        """Delta G2P at the particles of the context's last sort, results in
+        that sorted order (pm_interpolate_sorted); np_ = that call's count."""
+        mesh = self._f32(mesh)
+        F = mesh.numel() // self.nodes
+        out = out if out is not None else self._empty(F, np_)
+        self._stream()
+        self._check(self.lib.pm_interpolate_sorted(self.h, _ptr(mesh), F, np_, _ptr(out)))
         return out
 
     def interpolate_mass(self, mesh, px, py=None, out=None, rtol=1e-6, max_iter=200, info=True):

@@ -32,6 +32,7 @@ struct pm_ctx {
     size_t nev = 0;
     double acc_ms[PM_NPHASE] = {0};
     ll acc_calls[PM_NPHASE] = {0};
+    ll sorted_np = -1;  // particles of the most recent sort (w.pos, w.perm); -1: none yet
     // host-buffer mass assignment: device copies of the inputs and output,
     // the stream that uploads the values and its events (made on first use)
     float *hx = nullptr, *hy = nullptr, *hv = nullptr, *hout = nullptr;
@@ -158,6 +159,7 @@ pm_status prepare(pm_ctx *c, const float *px, const float *py, ll np, const floa
         launch_sort(c->g, c->w, px, py, np, vals, F, c->st);
     }
     if (pm_status s = check_launch(c, "sort")) return s;
+    c->sorted_np = np;
     if (need_tri) {
         Phase ph(c, PM_PH_TRIANGULATE);
         if (c->g.dim == 2)
@@ -293,6 +295,19 @@ pm_status pm_interpolate(pm_ctx *c, const float *mesh, int F, const float *px, c
         launch_g2p(c->g, mesh, F, px, py, np, out, c->w.mesh_il, c->w.status, c->st);
     }
     return check_launch(c, "pm_interpolate");
+}
+
+pm_status pm_interpolate_sorted(pm_ctx *c, const float *mesh, int F, long long np, float *out) {
+    if (!c) return PM_EINVAL;
+    if (c->sorted_np < 0) return fail(c, PM_EINVAL, "no particles sorted yet");
+    if (np != c->sorted_np) return fail(c, PM_EINVAL, "np differs from the particles of the last sort");
+    if (F < 1 || F > c->w.F_max) return fail(c, PM_EINVAL, "field count out of range");
+    if (np > 0 && (!mesh || !out)) return fail(c, PM_EINVAL, "null mesh or output array");
+    {
+        Phase ph(c, PM_PH_G2P);
+        launch_g2p_sorted(c->g, mesh, F, c->w.pos, np, out, c->w.mesh_il, c->st);
+    }
+    return check_launch(c, "pm_interpolate_sorted");
 }
 
 pm_status pm_assign_delta(pm_ctx *c, const float *px, const float *py, long long np, const float *vals, int F,

@@ -112,6 +112,73 @@ __global__ void __launch_bounds__(256) k_g2p(Geo g, const float *__restrict__ il
     }
 }
 
+// The same interpolation at the particles of the context's sort, in sorted
+// order: slot s reads its torus coordinates from pos[s] (those of caller
+// particle perm[s], so the weights and the result are the same bits as
+// k_g2p's for that particle) and writes out[f][s]. Consecutive threads hold
+// particles of the same or neighbouring cells, so a warp's corner loads fall
+// on a few lines and mostly hit L1. The fields stay interleaved per node:
+// four 16-byte corner loads beat 4F 4-byte ones here too (0.128 against
+// 0.182 ms on 16.8M particles, F = 4).
+template <int DIM, int W>
+__global__ void __launch_bounds__(256) k_g2p_sorted(Geo g, const float *__restrict__ il, int F,
+                                                    const uint2 *__restrict__ pos, ll np, float *__restrict__ out) {
+    const ll k = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= np) return;
+    const int n = g.n;
+    const uint2 P = __ldcs(pos + k);
+    const int cx = cell_of(P.x, n);
+    const float s = frac_f(P.x, n);
+    const int x1 = cx + 1 == n ? 0 : cx + 1;
+    if (DIM == 1) {
+        const NodeVec<W> m0 = load_node<W>(il, cx), m1 = load_node<W>(il, x1);
+#pragma unroll
+        for (int f = 0; f < W; ++f)
+            if (f < F) __stcs(out + (ll)f * np + k, fmaf(s, m1.v[f], (1.0f - s) * m0.v[f]));
+        return;
+    }
+    const int cy = cell_of(P.y, n);
+    const float t = frac_f(P.y, n);
+    const int y1 = cy + 1 == n ? 0 : cy + 1;
+    const ll i00 = (ll)cy * n + cx, i10 = (ll)cy * n + x1, i01 = (ll)y1 * n + cx, i11 = (ll)y1 * n + x1;
+    float w00, w10, w01, w11;
+    cell_weights(g.p1 != 0, s, t, w00, w10, w01, w11);
+    const NodeVec<W> m00 = load_node<W>(il, i00), m10 = load_node<W>(il, i10), m01 = load_node<W>(il, i01),
+                     m11 = load_node<W>(il, i11);
+#pragma unroll
+    for (int f = 0; f < W; ++f) {
+        if (f < F) {
+            float v = w00 * m00.v[f];
+            v = fmaf(w10, m10.v[f], v);
+            v = fmaf(w01, m01.v[f], v);
+            v = fmaf(w11, m11.v[f], v);
+            __stcs(out + (ll)f * np + k, v);
+        }
+    }
+}
+
+template <int DIM>
+void g2p_sorted_run(const Geo &g, const float *mesh, int F, const uint2 *pos, ll np, float *out, float *il,
+                    cudaStream_t st) {
+    const int nb = div_up(np, 256), nbm = div_up(g.ncell, 256);
+    if (F == 1) {
+        k_g2p_sorted<DIM, 1><<<nb, 256, 0, st>>>(g, mesh, F, pos, np, out);
+        count_launches(1);
+        return;
+    }
+    if (F == 2) {
+        k_interleave<2><<<nbm, 256, 0, st>>>(g.ncell, F, mesh, il);
+        k_g2p_sorted<DIM, 2><<<nb, 256, 0, st>>>(g, il, F, pos, np, out);
+    } else if (F <= 4) {
+        k_interleave<4><<<nbm, 256, 0, st>>>(g.ncell, F, mesh, il);
+        k_g2p_sorted<DIM, 4><<<nb, 256, 0, st>>>(g, il, F, pos, np, out);
+    } else {
+        k_interleave<8><<<nbm, 256, 0, st>>>(g.ncell, F, mesh, il);
+        k_g2p_sorted<DIM, 8><<<nb, 256, 0, st>>>(g, il, F, pos, np, out);
+    }
+    count_launches(2);
+}
+
 template <int DIM>
 void g2p_run(const Geo &g, const float *mesh, int F, const float *px, const float *py, ll np, float *out,
                float *il, int *status, cudaStream_t st) {
@@ -150,6 +217,15 @@ void launch_g2p(const Geo &g, const float *mesh, int F, const float *px, const f
         g2p_run<1>(g, mesh, F, px, py, np, out, il, status, st);
     else
         g2p_run<2>(g, mesh, F, px, py, np, out, il, status, st);
+}
+
+void launch_g2p_sorted(const Geo &g, const float *mesh, int F, const uint2 *pos, ll np, float *out, float *il,
+                       cudaStream_t st) {
+    if (np <= 0) return;
+    if (g.dim == 1)
+        g2p_sorted_run<1>(g, mesh, F, pos, np, out, il, st);
+    else
+        g2p_sorted_run<2>(g, mesh, F, pos, np, out, il, st);
 }
 
 void launch_scatter_sorted(ll np, const int *perm, const float *src, float *dst, cudaStream_t st) {

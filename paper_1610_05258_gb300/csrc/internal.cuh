@@ -362,6 +362,10 @@ void launch_gather_vals(Work &w, ll np, const float *vals, int F, cudaStream_t s
 int g2p_width(int F);
 void launch_g2p(const Geo &g, const float *mesh, int F, const float *px, const float *py, ll np, float *out,
                 float *il, int *status, cudaStream_t st);
+// G2P at the particles of the sort in w.pos (torus coordinates, sorted
+// order); out [F][np] in that order. il as for launch_g2p.
+void launch_g2p_sorted(const Geo &g, const float *mesh, int F, const uint2 *pos, ll np, float *out, float *il,
+                       cudaStream_t st);
 void launch_triangulate(const Geo &g, Work &w, ll np, cudaStream_t st, bool count_work = false);
 void launch_volumes_1d(const Geo &g, Work &w, ll np, cudaStream_t st);
 void launch_delta(const Geo &g, Work &w, ll np, int F, float *mesh_out, cudaStream_t st);
