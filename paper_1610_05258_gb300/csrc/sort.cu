@@ -305,7 +305,8 @@ void launch_gather_vals(Work &w, ll np, const float *vals, int F, cudaStream_t s
     if (np <= 0 || F <= 0) return;
     const dim3 grid((unsigned)div_up(np, GATHER_BLK), F);
     // caller indices from w.perm (row 0 copied them there; w.tmp may have been
-    // reused since, e.g. as the triangulation's retry list)
-    k_gather<<<grid, GATHER_BLK, 0, st>>>(np, w.perm, w.fx, vals, w.perm, w.pos, w.vals, w.maxabs, w.status, 1);
+    // reused since, e.g. as the triangulation's retry list); the position
+    // row's outputs are not touched by these rows, so none are passed
+    k_gather<<<grid, GATHER_BLK, 0, st>>>(np, w.perm, nullptr, vals, nullptr, nullptr, w.vals, w.maxabs, w.status, 1);
     count_launches(1);
 }
