@@ -73,3 +73,20 @@ def test_host_call_oracle_parity_and_rejects_device_start(built):
         assert x.rel_resid <= 1e-6 and x.cons_err <= 1e-6
     with pytest.raises(PMError):
         c.assign_mass_host(_host(inst.px, True), _host(inst.py, True), _host(inst.vals, True), warm_start="user")
+
+
+@pytest.mark.parametrize("mesh_kind,rhs,warm", [("p1", "exact", "delta"), ("q1", "appb", "delta"),
+                                                 ("q1", "exact", "direct"), ("q1", "exact", "zero")])
+def test_host_call_other_modes(built, mesh_kind, rhs, warm):
+    """The deferred value gather feeds every right-hand side and start: the
+    host call equals the device call bit for bit on the P1 mesh, with the
+    App. B right-hand side, and from the direct and zero starts."""
+    from paper_1610_05258_gb300 import Context
+    inst = W.uniform_instance(48, 4, F=2, seed=610)
+    c = Context(2, inst.n, inst.L, inst.np, 2, mesh=mesh_kind)
+    dpx, dpy, dv = to_dev(torch, inst.px, inst.py, inst.vals)
+    want = c.assign_mass(dpx, dpy, dv, rhs=rhs, warm_start=warm, info=False).cpu()
+    got = c.assign_mass_host(_host(inst.px, True), _host(inst.py, True), _host(inst.vals, True), rhs=rhs,
+                             warm_start=warm, info=False)
+    c.sync()
+    assert torch.equal(got, want)
