@@ -222,7 +222,8 @@ pm_status pm_ctx_create_mesh(pm_ctx **out, int dim, int n, double L, long long m
               alloc(c, &w.pp2, pcg_width((int)F) * np);
     w.cfix = (ll *)w.prp;
     w.red_blocks = 4096;
-    if (ok && dim == 2) ok = alloc(c, &w.nbr, (ll)PM_MAXDEG * np) && alloc(c, &w.pcoef, (ll)PM_MAXDEG * np);
+    if (ok && dim == 2)
+        ok = alloc(c, &w.nbr, (ll)PM_MAXDEG * np) && alloc(c, &w.pcoef, (ll)PM_MAXDEG * np) && alloc(c, &w.r2, F * nc);
     if (ok && F > 1) ok = alloc(c, &w.mesh_il, (ll)g2p_width((int)F) * nc);
     if (ok && dim == 2 && n % 128 == 0 && !g.p1)  // the network start: bilinear meshes
         ok = alloc(c, &w.feat, 2 * F * nc) && alloc(c, &w.corr, F * nc);
@@ -252,7 +253,7 @@ void pm_ctx_destroy(pm_ctx *c) {
     void *ptrs[] = {w.fx,  w.key, w.slot, w.count, w.cell_start, w.scan_tmp, w.tmp,  w.perm,  w.pos,
                     w.vals, w.maxabs, w.nbr, w.deg,  w.vol,  w.part,  w.bfix, w.psum, w.epart, w.r, w.p,
                     w.q,   w.b,   w.red,  w.scal,  w.bar,  w.status, w.empty, w.ntri, w.feat, w.corr,
-                    w.wsum, w.nretry, w.meshmax, w.pc, w.px, w.pq, w.prp, w.pp2, w.pcoef, w.mesh_il};
+                    w.wsum, w.nretry, w.meshmax, w.pc, w.px, w.pq, w.prp, w.pp2, w.pcoef, w.mesh_il, w.r2};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (w.hstatus) cudaFreeHost(w.hstatus);

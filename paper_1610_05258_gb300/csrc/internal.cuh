@@ -181,6 +181,7 @@ struct Work {
                            // fields interleaved; the solve of F fields uses stride pcg_width(F))
     float *prp;            // [2][np][W] D^-1 r and the even iterations' search direction
     float *pp2;            // [np][W] the odd iterations' search direction
+    float *r2;             // [F][ncell] second residual buffer of the blocked Chebyshev passes (2D)
     ll *cfix;              // = (ll *)prp: fixed-point c before conversion
     float *pcoef;          // [PM_MAXDEG][np] particle mass matrix rows (2D)
     float *mesh_il;        // [ncell][g2p_width(F_max)] mesh fields interleaved per node (G2P)

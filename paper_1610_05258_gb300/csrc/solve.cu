@@ -35,6 +35,7 @@ struct CG {
     const ll *bfix;         // fixed-point right-hand side (or null)
     const unsigned *maxabs; // fixed-point scale source
     float *x, *r, *p, *q, *b;
+    float *r2;              // second residual buffer of the blocked Chebyshev passes (2D)
     double *red;            // [6 * PM_MAXF][grid]
     double *scal;           // [F][16]
     unsigned *bar;          // [2] barrier count, generation
@@ -393,6 +394,42 @@ __global__ void __launch_bounds__(256) k_cg(CG a) {
 // exactly first, as for CG, and every update d_k has zero mean, so the result
 // is conservative to rounding.
 // ---------------------------------------------------------------------------
+// Temporal blocking of the Chebyshev steps (2D): a tile of CT x CT nodes
+// with a halo of CH nodes runs up to CH steps in shared memory, the valid
+// region shrinking by one node per step, then writes its interior back.
+#define CT 32
+#define CH 4
+#define CR (CT + 2 * CH)
+
+// stencil<2, P1> on a CR x CR shared-memory region: the same terms in the
+// same order, so the same bits as on the global array.
+template <int P1>
+__device__ __forceinline__ void stencil_s(const float *__restrict__ d, int i, float &hi, float &lo) {
+    Dot2 acc;
+    const float *r0 = d + i - CR, *r1 = d + i, *r2 = d + i + CR;
+    if (P1) {
+        acc.add(6.0f * r1[0]);
+        acc.add(r1[-1]);
+        acc.add(r1[1]);
+        acc.add(r0[0]);
+        acc.add(r2[0]);
+        acc.add(r0[-1]);
+        acc.add(r2[1]);
+    } else {
+        acc.add(16.0f * r1[0]);
+        acc.add(4.0f * r1[-1]);
+        acc.add(4.0f * r1[1]);
+        acc.add(4.0f * r0[0]);
+        acc.add(4.0f * r2[0]);
+        acc.add(r0[-1]);
+        acc.add(r0[1]);
+        acc.add(r2[-1]);
+        acc.add(r2[1]);
+    }
+    hi = acc.hi;
+    lo = acc.lo;
+}
+
 template <int DIM, int P1>
 __global__ void __launch_bounds__(256) k_cheb(CG a) {
     // Reduction slot groups alternate (3 (k & 1) for the k-th reduction), so a
@@ -521,6 +558,87 @@ __global__ void __launch_bounds__(256) k_cheb(CG a) {
         if (!grid_sync(a.bar, a.status)) return;
         double rho = 1.0 / sigma;
         float *dc = a.p, *dn = a.q;
+        if (DIM == 2) {
+            // passes of up to CH steps; d and r alternate between two buffers
+            // (other tiles read them as halo), x is only updated at its own
+            // nodes. Every node gets the plain loop's arithmetic in the same
+            // order, so the iterate is the same bits.
+            __shared__ float sd[2][CR * CR], sr[CR * CR], sx[CT * CT];
+            float *rc = a.r, *rn = a.r2;
+            const int tside = (n + CT - 1) / CT, ntiles = tside * tside;
+            for (int kb = 0; kb < K; kb += CH) {
+                const int steps = min(CH, K - kb);
+                float c1s[CH], c2s[CH];
+#pragma unroll
+                for (int j = 0; j < CH; ++j) {
+                    c1s[j] = c2s[j] = 0.0f;
+                    if (j < steps) {
+                        const double rho1 = 1.0 / (2.0 * sigma - rho);
+                        c1s[j] = (float)(rho1 * rho);
+                        c2s[j] = (float)(2.0 * rho1 / delta);
+                        rho = rho1;
+                    }
+                }
+                for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+                    const int tx0 = (tile % tside) * CT, ty0 = (tile / tside) * CT;
+                    for (int f = 0; f < F; ++f) {
+                        const int sf = min(steps, Kf[f] - kb);  // this field's steps in the pass
+                        if (sf <= 0) continue;
+                        const ll fo = (ll)f * nn;
+                        for (int i = threadIdx.x; i < CR * CR; i += blockDim.x) {
+                            const int gx = wrapi(tx0 - CH + i % CR, n), gy = wrapi(ty0 - CH + i / CR, n);
+                            sd[0][i] = dc[fo + (ll)gy * n + gx];
+                            sr[i] = rc[fo + (ll)gy * n + gx];
+                        }
+                        for (int i = threadIdx.x; i < CT * CT; i += blockDim.x) {
+                            const int gx = tx0 + i % CT, gy = ty0 + i / CT;
+                            sx[i] = gx < n && gy < n ? a.x[fo + (ll)gy * n + gx] : 0.0f;
+                        }
+                        __syncthreads();
+                        int cur = 0;
+                        for (int j = 0; j < sf; ++j) {
+                            const int lo_ = j + 1, hi_ = CR - 1 - j;  // output region of this step
+                            const float *din = sd[cur];
+                            float *dout = sd[cur ^ 1];
+                            for (int i = threadIdx.x; i < CR * CR; i += blockDim.x) {
+                                const int lx = i % CR, ly = i / CR;
+                                if (lx < lo_ || lx >= hi_ || ly < lo_ || ly >= hi_) continue;
+                                float hi, lo;
+                                stencil_s<P1>(din, i, hi, lo);
+                                const float dv = din[i];
+                                const int ix = lx - CH, iy = ly - CH;
+                                if (ix >= 0 && ix < CT && iy >= 0 && iy < CT) sx[iy * CT + ix] += dv;
+                                const float rv = sr[i] - fmaf(c, hi, c * lo);
+                                sr[i] = rv;
+                                dout[i] = fmaf(c1s[j], dv, c2s[j] * rv);
+                            }
+                            __syncthreads();
+                            cur ^= 1;
+                        }
+                        for (int i = threadIdx.x; i < CT * CT; i += blockDim.x) {
+                            const int ix = i % CT, iy = i / CT, gx = tx0 + ix, gy = ty0 + iy;
+                            if (gx >= n || gy >= n) continue;
+                            const int li = (iy + CH) * CR + ix + CH;
+                            const ll o = fo + (ll)gy * n + gx;
+                            a.x[o] = sx[i];
+                            rn[o] = sr[li];
+                            dn[o] = sd[cur][li];
+                        }
+                        __syncthreads();
+                    }
+                }
+                float *t = dc;
+                dc = dn;
+                dn = t;
+                t = rc;
+                rc = rn;
+                rn = t;
+                if (!grid_sync(a.bar, a.status)) return;
+            }
+            steps_done += K;
+            for (int f = 0; f < F; ++f) steps_f[f] += Kf[f];
+            continue;
+        }
         for (int k = 0; k < K; ++k) {
             const double rho1 = 1.0 / (2.0 * sigma - rho);
             const float c1 = (float)(rho1 * rho), c2 = (float)(2.0 * rho1 / delta);
@@ -1485,6 +1603,7 @@ int launch_cheb(const Geo &g, Work &w, int F, const float *b_float, bool b_from_
     a.p = w.p;
     a.q = w.q;
     a.b = w.b;
+    a.r2 = w.r2;
     a.red = w.red;
     a.scal = w.scal;
     a.bar = w.bar;
@@ -1496,6 +1615,7 @@ int launch_cheb(const Geo &g, Work &w, int F, const float *b_float, bool b_from_
     a.nblk_psum = w.nblk_psum;
     const bool p1 = g.dim == 2 && g.p1;
     const int di = g.dim == 1 ? 0 : (p1 ? 2 : 1);
+    if (g.dim == 2 && !w.r2) return (int)cudaErrorInvalidValue;
     void (*kern)(CG) = g.dim == 1 ? k_cheb<1, 0> : (p1 ? k_cheb<2, 1> : k_cheb<2, 0>);
     const ll need = (g.ncell + 255) / 256;
     const int grid = clamp_grid(persistent_grid(6 + di, (const void *)kern, 4), need, w);
