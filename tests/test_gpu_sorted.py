@@ -1,7 +1,9 @@
 """Delta interpolation at the particles of the context's last sort, in sorted
 order (pm_interpolate_sorted): slot s equals, bit for bit, pm_interpolate at
 caller particle perm[s], for every field width, in 1D and 2D, on bilinear and
-P1 meshes; and it is refused before any sort or with a different count."""
+P1 meshes; with particles so sparse that a block's cells overrun the staged
+mesh windows (the corners beyond them read from the mesh directly); and it is
+refused before any sort or with a different count."""
 import numpy as np
 import pytest
 
@@ -31,6 +33,19 @@ def test_sorted_interpolation_matches_caller_order(built, dim, F, mesh_kind):
     c.assign_mass(px, py, dv, info=False)  # sorts the particles
     got = c.interpolate_sorted(mesh, inst.np).clone()
     perm, _ = c.sort(px, py)
+    want = c.interpolate(mesh, px, py)
+    assert torch.equal(got, want[:, perm.long()])
+
+
+@pytest.mark.parametrize("n,ppc,F", [(200, 0.05, 4), (300, 0.02, 2), (64, 0.5, 6), (4, 30, 3), (5, 0.4, 4)])
+def test_sorted_interpolation_sparse_and_tiny(built, n, ppc, F):
+    from paper_1610_05258_gb300 import Context
+    inst = W.uniform_instance(n, ppc, F=F, seed=720 + n)
+    c = Context(2, n, inst.L, inst.np, F)
+    px, py, dv = to_dev(torch, inst.px, inst.py, inst.vals)
+    mesh = to_dev(torch, W.mesh_field(2, n, inst.L, F=F, seed=11, kind="noise").astype(np.float32))[0]
+    perm, _ = c.sort(px, py)
+    got = c.interpolate_sorted(mesh, inst.np).clone()
     want = c.interpolate(mesh, px, py)
     assert torch.equal(got, want[:, perm.long()])
 
